@@ -1,0 +1,133 @@
+/*
+ * hdconv.h -- C ABI of libhdconv.so: dealiased linear convolutions of two
+ * equal-size real FP32 arrays in 1D, 2D and 3D on one NVIDIA B300 (sm_103a),
+ * by hybrid dealiasing (Murasko & Bowman, "Hybrid Dealiasing and Implicit
+ * Packing for Real Convolutions").
+ *
+ * Problem (Sec. 2, statement before Eq. forwardr; Sec. 6): given real arrays
+ * f and g of extent L per dimension, compute
+ *       h_k = sum_j f_j g_{k-j},   0 <= k_i < L_i in every dimension,
+ * i.e. the first L outputs per dimension of the linear convolution, which a
+ * DFT method reproduces exactly (up to rounding) once every dimension is padded
+ * to at least 2L-1.  Results are normalised (the 1/(qm) factor of
+ * Eqs. accumulation and real-accumulation is applied inside the last pass).
+ *
+ * Algorithms (Sec. 6):
+ *   HD_EXPLICIT      zero padding materialised to 2L per dimension, real DFT,
+ *                    pointwise product, inverse, crop (the standard method).
+ *   HD_EXPLICIT_RCM  explicit padding with implicit packing: pack, complex DFT
+ *                    of half length, the RCM operator (Eq. RCM, Alg. 4),
+ *                    inverse, unpack (Algs. 3 and 5).
+ *   HD_HYBRID_CS     hybrid dealiasing with conjugate symmetries (Sec. 3).
+ *   HD_HYBRID_RCM    hybrid dealiasing with implicit packing (Sec. 4).
+ *
+ * Memory: every array argument of a compute call is a DEVICE pointer owned
+ * by the caller (row-major, last dimension contiguous, FP32).  h may equal f
+ * or g (in place, as the paper times it); partial overlap is not allowed.
+ * Calls are asynchronous on the given CUDA stream (NULL = legacy default).
+ * The context owns twiddle tables and scratch; the first call for a new size
+ * allocates them (cudaMalloc) and uploads tables, so capture a call in a CUDA
+ * graph only after one uncaptured call of the same shape.  A context is not
+ * thread-safe: use one per host thread.
+ *
+ * Errors: HD_EINVAL for invalid arguments (null pointer, L < 1, hybrid
+ * parameters that do not dealias, see hd_dim_params), HD_EUNSUPPORTED for a
+ * valid request this build cannot run (e.g. shared memory too small for the
+ * requested m), HD_ECUDA when a CUDA call fails (the message is kept and can be
+ * read with hd_last_error_string), HD_ENOMEM when an allocation fails.
+ * Nothing is launched when an error is returned before launch.
+ */
+#ifndef HDCONV_H
+#define HDCONV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hd_ctx hd_ctx;
+typedef struct hd_batch_plan hd_batch_plan;
+
+typedef enum {
+  HD_OK = 0,
+  HD_EINVAL = 1,
+  HD_ENOMEM = 2,
+  HD_ECUDA = 3,
+  HD_ETIMEOUT = 4,
+  HD_EUNSUPPORTED = 5
+} hd_status;
+
+typedef enum { HD_EXPLICIT = 0, HD_EXPLICIT_RCM = 1, HD_HYBRID_CS = 2, HD_HYBRID_RCM = 3 } hd_algo;
+
+/* Arithmetic of the DFT stages.  HD_FP32 everywhere; HD_SPLIT_BF16 runs the
+ * radix-16 stages of the 3D path on tensor cores with hi/lo bfloat16 operands
+ * and FP32 accumulation (returns HD_EUNSUPPORTED where not available). */
+typedef enum { HD_FP32 = 0, HD_SPLIT_BF16 = 1 } hd_prec;
+
+/* Hybrid parameters of one dimension (Sec. 2: p = ceil(L/m), q = ceil(M/m)).
+ * m = 0 lets the planner choose (m, q).  For HD_HYBRID_CS the data are real
+ * of length L and q m >= 2L-1 is required, with m even when q is even
+ * (Sec. 3.1.3).  For HD_HYBRID_RCM the packed dimension (the last one) has
+ * length ceil(L/2) and needs q m >= L; outer dimensions of a 2D/3D call are
+ * complex and need q m >= 2L-1.  Explicit algorithms ignore the parameters. */
+typedef struct {
+  int32_t m;
+  int32_t q;
+} hd_dim_params;
+
+/* Context on a CUDA device (the device becomes current for each call). */
+hd_status hd_create(hd_ctx** ctx, int device);
+hd_status hd_destroy(hd_ctx* ctx);
+
+/* 1D: f, g, h hold L floats.  prm may be NULL (planner). */
+hd_status hd_conv1d(hd_ctx* ctx, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h,
+                    int64_t L, const hd_dim_params* prm, void* stream);
+
+/* 2D: L1 x L2 (L2 contiguous).  prm: 2 entries or NULL. */
+hd_status hd_conv2d(hd_ctx* ctx, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h,
+                    int64_t L1, int64_t L2, const hd_dim_params* prm, void* stream);
+
+/* 3D: L1 x L2 x L3 (L3 contiguous).  prm: 3 entries or NULL. */
+hd_status hd_conv3d(hd_ctx* ctx, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h,
+                    int64_t L1, int64_t L2, int64_t L3, const hd_dim_params* prm, void* stream);
+
+/* Batched 1D convolutions of uneven lengths.  A plan is built on the host
+ * from HOST arrays: item i occupies floats [offsets[i], offsets[i] + L[i]) of
+ * f, g and h (items must not overlap).  The planner picks (m, q) per length
+ * and uploads the item table; hd_conv1d_batched then enqueues a fixed set of
+ * launches with no allocation and no host-to-device copy, so it can be
+ * captured in a CUDA graph.  The plan must outlive every launch that uses it. */
+hd_status hd_batch_plan_create(hd_ctx* ctx, hd_algo algo, int32_t n, const int64_t* offsets, const int32_t* L,
+                               hd_batch_plan** plan);
+hd_status hd_batch_plan_destroy(hd_batch_plan* plan);
+hd_status hd_conv1d_batched(hd_ctx* ctx, const hd_batch_plan* plan, const float* f, const float* g, float* h,
+                            void* stream);
+
+/* Adjoint of h = conv(f, g) (first L outputs per dimension) for `batch`
+ * independent problems of extents Ls[0..ndim) stored back to back: given
+ * grad_h, grad_f[j] = sum_k grad_h[k] g[k-j] and grad_g[j] = sum_k grad_h[k]
+ * f[k-j], computed as rev(conv(rev(grad_h), g)) on every axis (the adjoint of
+ * a truncated convolution is a reversed truncated convolution).  grad_f or
+ * grad_g may be NULL to skip it. */
+hd_status hd_conv_adjoint(hd_ctx* ctx, hd_algo algo, int ndim, const int64_t* Ls, int32_t batch,
+                          const float* grad_h, const float* f, const float* g, float* grad_f, float* grad_g,
+                          void* stream);
+
+/* The planner's (m, q) for one dimension of real length L and `algo`
+ * (HD_HYBRID_RCM reports packed lengths). */
+hd_status hd_plan(hd_ctx* ctx, hd_algo algo, int64_t L, hd_dim_params* out);
+
+/* Status of device-side checks since the last call (bounded waits that gave
+ * up report HD_ETIMEOUT); reading it synchronises the context's device and
+ * clears the word. */
+hd_status hd_last_device_error(hd_ctx* ctx);
+
+const char* hd_strerror(hd_status s);
+const char* hd_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HDCONV_H */

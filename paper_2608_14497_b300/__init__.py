@@ -1,0 +1,218 @@
+"""Python binding of libhdconv.so: hybrid-dealiased real convolutions on a B300.
+
+The binding only marshals arguments: every step of a convolution runs in the
+CUDA kernels of ``libhdconv.so`` (built in-tree by ``build.py``).  PyTorch is
+used for device memory and streams.  There is no CPU fallback: if the library
+cannot be loaded, or no CUDA device is present, calls raise.
+
+Low-level names mirror the C ABI of ``include/hdconv.h`` (``hd_conv1d`` ...),
+taking raw device pointers; the ``conv1d`` / ``conv2d`` / ``conv3d`` /
+``conv1d_batched`` helpers take torch CUDA tensors.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhdconv.so")
+
+HD_OK, HD_EINVAL, HD_ENOMEM, HD_ECUDA, HD_ETIMEOUT, HD_EUNSUPPORTED = range(6)
+HD_EXPLICIT, HD_EXPLICIT_RCM, HD_HYBRID_CS, HD_HYBRID_RCM = range(4)
+HD_FP32, HD_SPLIT_BF16 = range(2)
+
+ALGOS = {"explicit": HD_EXPLICIT, "explicitRCM": HD_EXPLICIT_RCM, "hybridCS": HD_HYBRID_CS,
+         "hybridRCM": HD_HYBRID_RCM}
+PRECS = {"fp32": HD_FP32, "split_bf16": HD_SPLIT_BF16}
+
+# Every symbol include/hdconv.h declares.
+EXPORTS = ("hd_create", "hd_destroy", "hd_conv1d", "hd_conv2d", "hd_conv3d", "hd_batch_plan_create",
+           "hd_batch_plan_destroy", "hd_conv1d_batched", "hd_conv_adjoint", "hd_plan", "hd_last_device_error",
+           "hd_strerror", "hd_last_error_string")
+
+
+class HDError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.hd_last_error_string().decode() if _lib is not None else ""
+        strerr = _lib.hd_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {strerr} ({status}) {msg}")
+
+
+class DimParams(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("q", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(build_if_missing=False):
+    """Load libhdconv.so (optionally building it first); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        from . import build as _b
+        _b.build()
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libhdconv.so not built ({LIB_PATH}); run paper_2608_14497_b300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+    DP = ctypes.POINTER(DimParams)
+    sig = {
+        "hd_create": ([ctypes.POINTER(P), I], I),
+        "hd_destroy": ([P], I),
+        "hd_conv1d": ([P, I, I, P, P, P, I64, DP, P], I),
+        "hd_conv2d": ([P, I, I, P, P, P, I64, I64, DP, P], I),
+        "hd_conv3d": ([P, I, I, P, P, P, I64, I64, I64, DP, P], I),
+        "hd_batch_plan_create": ([P, I, I32, P, P, ctypes.POINTER(P)], I),
+        "hd_batch_plan_destroy": ([P], I),
+        "hd_conv1d_batched": ([P, P, P, P, P, P], I),
+        "hd_conv_adjoint": ([P, I, I, P, I32, P, P, P, P, P, P], I),
+        "hd_plan": ([P, I, I64, DP], I),
+        "hd_last_device_error": ([P], I),
+        "hd_strerror": ([I], ctypes.c_char_p),
+        "hd_last_error_string": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status, where):
+    if status != HD_OK:
+        raise HDError(status, where)
+
+
+# --- thin wrappers with the C names (raw pointers) -------------------------------
+def hd_create(device=0):
+    lib = load()
+    ctx = ctypes.c_void_p()
+    _check(lib.hd_create(ctypes.byref(ctx), device), "hd_create")
+    return ctx
+
+
+def hd_destroy(ctx):
+    return load().hd_destroy(ctx)
+
+
+def _params(prm, n):
+    if prm is None:
+        return None
+    arr = (DimParams * n)()
+    for i, (m, q) in enumerate(prm):
+        arr[i].m, arr[i].q = int(m), int(q)
+    return arr
+
+
+def hd_conv1d(ctx, algo, prec, f_ptr, g_ptr, h_ptr, L, prm=None, stream=0):
+    return load().hd_conv1d(ctx, algo, prec, f_ptr, g_ptr, h_ptr, L, _params(prm, 1), stream)
+
+
+def hd_conv2d(ctx, algo, prec, f_ptr, g_ptr, h_ptr, L1, L2, prm=None, stream=0):
+    return load().hd_conv2d(ctx, algo, prec, f_ptr, g_ptr, h_ptr, L1, L2, _params(prm, 2), stream)
+
+
+def hd_conv3d(ctx, algo, prec, f_ptr, g_ptr, h_ptr, L1, L2, L3, prm=None, stream=0):
+    return load().hd_conv3d(ctx, algo, prec, f_ptr, g_ptr, h_ptr, L1, L2, L3, _params(prm, 3), stream)
+
+
+def hd_plan(ctx, algo, L):
+    out = DimParams()
+    _check(load().hd_plan(ctx, algo, L, ctypes.byref(out)), "hd_plan")
+    return out.m, out.q
+
+
+def hd_batch_plan_create(ctx, algo, offsets, lengths):
+    import numpy as np
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    Ls = np.ascontiguousarray(lengths, dtype=np.int32)
+    plan = ctypes.c_void_p()
+    _check(load().hd_batch_plan_create(ctx, algo, len(Ls), off.ctypes.data, Ls.ctypes.data, ctypes.byref(plan)),
+           "hd_batch_plan_create")
+    return plan
+
+
+def hd_batch_plan_destroy(plan):
+    return load().hd_batch_plan_destroy(plan)
+
+
+def hd_conv1d_batched(ctx, plan, f_ptr, g_ptr, h_ptr, stream=0):
+    return load().hd_conv1d_batched(ctx, plan, f_ptr, g_ptr, h_ptr, stream)
+
+
+def hd_conv_adjoint(ctx, algo, Ls, batch, gh_ptr, f_ptr, g_ptr, gf_ptr, gg_ptr, stream=0):
+    arr = (ctypes.c_int64 * len(Ls))(*[int(x) for x in Ls])
+    return load().hd_conv_adjoint(ctx, algo, len(Ls), arr, batch, gh_ptr, f_ptr, g_ptr, gf_ptr, gg_ptr, stream)
+
+
+def hd_last_device_error(ctx):
+    return load().hd_last_device_error(ctx)
+
+
+# --- torch helpers ---------------------------------------------------------------
+_ctx = {}
+
+
+def context(device=None):
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+    if dev not in _ctx:
+        _ctx[dev] = hd_create(dev)
+    return _ctx[dev]
+
+
+def _stream_ptr():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _check_tensor(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+
+
+def conv(f, g, algo="hybridRCM", params=None, out=None, prec="fp32"):
+    """h = first L per dimension of the linear convolution of f and g (1D/2D/3D)."""
+    import torch
+    _check_tensor(f, "f")
+    _check_tensor(g, "g")
+    if f.shape != g.shape or f.dim() not in (1, 2, 3):
+        raise ValueError("f and g must share a 1D/2D/3D shape")
+    h = torch.empty_like(f) if out is None else out
+    _check_tensor(h, "out")
+    ctx = context(f.device.index)
+    a, p = ALGOS[algo], PRECS[prec]
+    if f.dim() == 1:
+        st = hd_conv1d(ctx, a, p, f.data_ptr(), g.data_ptr(), h.data_ptr(), f.shape[0], params, _stream_ptr())
+    elif f.dim() == 2:
+        st = hd_conv2d(ctx, a, p, f.data_ptr(), g.data_ptr(), h.data_ptr(), *f.shape, params, _stream_ptr())
+    else:
+        st = hd_conv3d(ctx, a, p, f.data_ptr(), g.data_ptr(), h.data_ptr(), *f.shape, params, _stream_ptr())
+    _check(st, f"conv{f.dim()}d[{algo}]")
+    return h
+
+
+class BatchPlan:
+    """Host-built plan of many 1D convolutions of uneven lengths on flat arrays."""
+
+    def __init__(self, offsets, lengths, algo="hybridRCM", device=None):
+        self.ctx = context(device)
+        self.algo = algo
+        self.handle = hd_batch_plan_create(self.ctx, ALGOS[algo], offsets, lengths)
+
+    def __call__(self, f, g, out=None):
+        import torch
+        _check_tensor(f, "f")
+        _check_tensor(g, "g")
+        h = torch.empty_like(f) if out is None else out
+        _check(hd_conv1d_batched(self.ctx, self.handle, f.data_ptr(), g.data_ptr(), h.data_ptr(), _stream_ptr()),
+               "conv1d_batched")
+        return h
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            hd_batch_plan_destroy(self.handle)
+            self.handle = None

@@ -1,0 +1,255 @@
+// hd_api.cu -- the C ABI of libhdconv.so (declared in include/hdconv.h):
+// argument validation, the planner that picks the hybrid parameters (m, q) of
+// Sec. 2 for a length, and dispatch to the kernels.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "hd_conv1d.cuh"
+#include "hd_internal.h"
+#include "hd_nd.cuh"
+
+namespace {
+thread_local std::string g_last_error;
+
+hd_status fail(hd_status s, const char* what) {
+  g_last_error = what;
+  return s;
+}
+
+hd_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return HD_ECUDA;
+}
+}  // namespace
+
+namespace hd {
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Largest 2,3,5-smooth number <= n (n >= 1).
+static int64_t prev_smooth(int64_t n) {
+  while (n > 1 && !smooth235(n)) --n;
+  return n < 1 ? 1 : n;
+}
+
+static int64_t next_smooth_even(int64_t n) {
+  int64_t m = next_smooth(n < 2 ? 2 : n);
+  while (m % 2) m = next_smooth(m + 1);
+  return m;
+}
+
+// Parameters of one 1D convolution, resolved against the kernel limits.
+struct Params1D {
+  int m = 0, q = 0, p = 0;
+  bool gacc = false;
+  int threads = 0;
+  size_t smem = 0;
+};
+
+// hybridRCM: packed length Lp = ceil(L/2) must satisfy p m >= Lp (p =
+// ceil(Lp/m)) and q m >= L (real padded length 2qm >= 2L-1).  The planner
+// prefers p = 1, q = 2 (a single explicit block, residues 0 and 1, both
+// self-paired) with the smallest 2,3,5-smooth m >= Lp; when 4m exceeds what one
+// CTA transforms at once it lowers m and raises p and q.
+hd_status resolve_rcm1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D* out) {
+  const int64_t Lp = ceil_div(L, 2);
+  int64_t m, q;
+  const int64_t mmax = (int64_t)kPts * 1024 / 4;
+  if (prm && prm->m > 0) {
+    m = prm->m;
+    q = prm->q > 0 ? prm->q : ceil_div(L, m);
+    if (q * m < L) return fail(HD_EINVAL, "hybridRCM needs q m >= L (packed)");
+    if (m > mmax) return fail(HD_EUNSUPPORTED, "hybridRCM: m too large for one CTA (m <= 4096)");
+  } else {
+    m = next_smooth(Lp);
+    q = 2;
+    if (m > mmax) {
+      for (int64_t k = 2;; ++k) {
+        m = next_smooth(ceil_div(Lp, k));
+        if (m <= mmax) break;
+      }
+      q = ceil_div(L, m);
+    }
+  }
+  if (q * m > (int64_t)1 << 30) return fail(HD_EUNSUPPORTED, "padded length too large");
+  out->m = (int)m;
+  out->q = (int)q;
+  out->p = (int)ceil_div(Lp, m);
+  out->smem = rcm1d_smem_bytes((int)L, (int)m, false);
+  out->gacc = out->smem > (size_t)c->max_smem;
+  if (out->gacc) out->smem = rcm1d_smem_bytes((int)L, (int)m, true);
+  if (out->smem > (size_t)c->max_smem) return fail(HD_EUNSUPPORTED, "hybridRCM: shared memory too small");
+  out->threads = threads_for_points(4 * m, kPts);
+  return HD_OK;
+}
+
+// hybridCS: real length L, q m >= 2L-1, m even when q is even (Sec. 3.1.3).
+// The planner prefers q = 2 and the smallest even 2,3,5-smooth m >= L.
+hd_status resolve_cs1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D* out) {
+  int64_t m, q;
+  const int64_t mmax = (int64_t)kPts * 1024 / 2;
+  if (prm && prm->m > 0) {
+    m = prm->m;
+    q = prm->q > 0 ? prm->q : ceil_div(2 * L - 1, m);
+    if (q * m < 2 * L - 1) return fail(HD_EINVAL, "hybridCS needs q m >= 2L-1");
+    if (q % 2 == 0 && m % 2 == 1) return fail(HD_EINVAL, "hybridCS needs m even when q is even");
+    if (m > mmax) return fail(HD_EUNSUPPORTED, "hybridCS: m too large for one CTA (m <= 8192)");
+  } else {
+    m = next_smooth_even(L);
+    q = 2;
+    if (m > mmax) {
+      for (int64_t k = 2;; ++k) {
+        m = next_smooth_even(ceil_div(L, k));
+        if (m <= mmax) break;
+      }
+      q = ceil_div(2 * L - 1, m);
+      if (q % 2 == 1) ++q;  // keep q even so residue q/2 uses the half-length DFT
+    }
+  }
+  if (q * m > (int64_t)1 << 30) return fail(HD_EUNSUPPORTED, "padded length too large");
+  out->m = (int)m;
+  out->q = (int)q;
+  out->p = (int)ceil_div(L, m);
+  out->smem = cs1d_smem_bytes((int)L, (int)m, false);
+  out->gacc = out->smem > (size_t)c->max_smem;
+  if (out->gacc) out->smem = cs1d_smem_bytes((int)L, (int)m, true);
+  if (out->smem > (size_t)c->max_smem) return fail(HD_EUNSUPPORTED, "hybridCS: shared memory too small");
+  out->threads = threads_for_points(2 * m, kPts);
+  return HD_OK;
+}
+
+static hd_status conv1d_hybrid(hd_ctx* c, hd_algo algo, const float* f, const float* g, float* h, int64_t L,
+                               const hd_dim_params* prm, cudaStream_t st) {
+  Params1D P;
+  hd_status s = (algo == HD_HYBRID_RCM) ? resolve_rcm1d(c, L, prm, &P) : resolve_cs1d(c, L, prm, &P);
+  if (s != HD_OK) return s;
+  hd_status terr = HD_OK;
+  const float2* tw = c->tables.get((int64_t)P.q * P.m, st, &terr);
+  if (!tw) return fail(terr, "twiddle table allocation failed");
+  Launch1D la;
+  std::memset(&la, 0, sizeof(la));
+  la.one.off = 0;
+  la.one.L = (int32_t)L;
+  la.one.m = P.m;
+  la.one.q = P.q;
+  la.one.p = P.p;
+  la.one.plan = 0;
+  la.one.plan_half = (P.m % 2 == 0) ? 1 : -1;
+  la.one.tw = tw;
+  factor_radices(P.m, &la.plan_m);
+  if (P.m % 2 == 0) factor_radices(P.m / 2, &la.plan_half);
+  if (P.gacc) {
+    const size_t bytes = (algo == HD_HYBRID_RCM) ? sizeof(float2) * (size_t)ceil_div(L, 2) : sizeof(float) * (size_t)L;
+    if (ensure_ws(c, bytes) != HD_OK) return fail(HD_ENOMEM, "workspace allocation failed");
+    la.one.gacc = c->ws;
+  }
+  cudaError_t e = (algo == HD_HYBRID_RCM) ? launch_rcm1d(la, 1, P.threads, P.smem, f, g, h, st)
+                                          : launch_cs1d(la, 1, P.threads, P.smem, f, g, h, st);
+  if (e != cudaSuccess) return cuda_fail(e, "conv1d launch");
+  return HD_OK;
+}
+
+}  // namespace hd
+
+using namespace hd;
+
+extern "C" {
+
+const char* hd_strerror(hd_status s) {
+  switch (s) {
+    case HD_OK: return "ok";
+    case HD_EINVAL: return "invalid argument";
+    case HD_ENOMEM: return "out of memory";
+    case HD_ECUDA: return "CUDA error";
+    case HD_ETIMEOUT: return "device wait timed out";
+    case HD_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* hd_last_error_string(void) { return g_last_error.c_str(); }
+
+hd_status hd_create(hd_ctx** out, int device) {
+  if (!out) return fail(HD_EINVAL, "null ctx pointer");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(HD_EINVAL, "no such device");
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  hd_ctx* c = new hd_ctx();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  // keep a little room for the kernels' static shared memory (plans)
+  c->max_smem -= 1024;
+  e = cudaMalloc(&c->dev_err, sizeof(int));
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaMalloc");
+  }
+  cudaMemset(c->dev_err, 0, sizeof(int));
+  *out = c;
+  return HD_OK;
+}
+
+hd_status hd_destroy(hd_ctx* c) {
+  if (!c) return HD_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  c->tables.clear();
+  if (c->ws) cudaFree(c->ws);
+  if (c->dev_err) cudaFree(c->dev_err);
+  delete c;
+  return HD_OK;
+}
+
+hd_status hd_plan(hd_ctx* c, hd_algo algo, int64_t L, hd_dim_params* out) {
+  if (!c || !out) return fail(HD_EINVAL, "null argument");
+  if (L < 1) return fail(HD_EINVAL, "L < 1");
+  Params1D P;
+  hd_status s;
+  switch (algo) {
+    case HD_HYBRID_RCM: s = resolve_rcm1d(c, L, nullptr, &P); break;
+    case HD_HYBRID_CS: s = resolve_cs1d(c, L, nullptr, &P); break;
+    default: return fail(HD_EINVAL, "hd_plan: hybrid algorithms only");
+  }
+  if (s != HD_OK) return s;
+  out->m = P.m;
+  out->q = P.q;
+  return HD_OK;
+}
+
+hd_status hd_conv1d(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h, int64_t L,
+                    const hd_dim_params* prm, void* stream) {
+  if (!c || !f || !g || !h) return fail(HD_EINVAL, "null argument");
+  if (L < 1) return fail(HD_EINVAL, "L < 1");
+  if (L > ((int64_t)1 << 28)) return fail(HD_EUNSUPPORTED, "L too large");
+  if (prec != HD_FP32) return fail(HD_EUNSUPPORTED, "1D path is FP32 only");
+  if (prm && (prm->m < 0 || prm->q < 0)) return fail(HD_EINVAL, "negative m or q");
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (algo) {
+    case HD_HYBRID_RCM:
+    case HD_HYBRID_CS: return conv1d_hybrid(c, algo, f, g, h, L, prm, st);
+    case HD_EXPLICIT:
+    case HD_EXPLICIT_RCM: return explicit_nd(c, algo, 1, &L, f, g, h, st);
+  }
+  return fail(HD_EINVAL, "unknown algorithm");
+}
+
+hd_status hd_last_device_error(hd_ctx* c) {
+  if (!c) return fail(HD_EINVAL, "null ctx");
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "device");
+  int w = 0;
+  cudaMemcpy(&w, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemset(c->dev_err, 0, sizeof(int));
+  return (hd_status)w;
+}
+
+}  // extern "C"

@@ -1,0 +1,34 @@
+// hd_conv1d.cuh -- launch descriptors of the 1D kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "hd_internal.h"
+
+namespace hd {
+
+// Points per thread of the shared-memory FFT passes (register budget).
+constexpr int kPts = 16;
+
+// Launch descriptor: either a device table of items (batched) or one item
+// passed by value (single call, nothing uploaded).
+struct Launch1D {
+  const Item1D* items;  // nullptr: use `one`
+  const FftPlan* plans; // nullptr: use plan_m / plan_half
+  Item1D one;
+  FftPlan plan_m;
+  FftPlan plan_half;
+};
+
+// Shared-memory float2 slots taken by an accumulator of `nf2` float2 values,
+// rounded to an even count so the buffers behind it stay 16-byte aligned.
+__host__ __device__ __forceinline__ int acc_slots(int nf2) { return (nf2 + 1) & ~1; }
+
+size_t rcm1d_smem_bytes(int L, int m, bool gacc);
+size_t cs1d_smem_bytes(int L, int m, bool gacc);
+int threads_for_points(int64_t points, int pts);
+cudaError_t launch_rcm1d(const Launch1D& la, int nitems, int threads, size_t smem, const float* f,
+                         const float* g, float* h, cudaStream_t st);
+cudaError_t launch_cs1d(const Launch1D& la, int nitems, int threads, size_t smem, const float* f,
+                        const float* g, float* h, cudaStream_t st);
+
+}  // namespace hd

@@ -1,0 +1,275 @@
+// hd_fft.cuh -- CTA-level mixed-radix Stockham FFT in shared memory (sm_103a).
+//
+// Every residue transform of the hybrid method (Sec. 2, Eqs. forwardr and
+// accumulator) needs DFTs of length m of data held on chip.  This header holds
+// the building blocks: complex helpers, register butterflies of radix
+// 2/3/4/5/8/16 plus a generic radix for any other prime factor, and a stage
+// loop that runs a Stockham autosort pass in place (all loads of a stage go to
+// registers, a barrier, then the stores), so no ping-pong buffer is needed.
+//
+// Sign convention (Sec. 2): zeta_N = exp(+2 pi i / N); SIGN = +1 computes
+// sum_j x_j zeta_n^{jk} (the forward transform of the paper), SIGN = -1 the
+// backward transform.  No scaling.
+//
+// Twiddles come from one table tw[k] = zeta_N^k (k < N) per padded length N,
+// generated in FP64 and rounded once to FP32; a length-n DFT with n | N reads
+// zeta_n^x = tw[x * (N / n)].
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hd {
+
+constexpr int kMaxStages = 24;
+
+// Radix sequence of one DFT length; the product of radix[0..nst) equals n.
+struct FftPlan {
+  int n;
+  int nst;
+  int radix[kMaxStages];
+};
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// i * sign * a
+template <int SIGN>
+__device__ __forceinline__ float2 cmul_i(float2 a) {
+  return SIGN > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// zeta_N^{SIGN * k} from the table (k already reduced into [0, N)).
+template <int SIGN>
+__device__ __forceinline__ float2 tw_get(const float2* __restrict__ tw, int k) {
+  float2 w = __ldg(tw + k);
+  if (SIGN < 0) w.y = -w.y;
+  return w;
+}
+
+// ---------------------------------------------------------------------------
+// register butterflies: y_k = sum_j a_j zeta_R^{SIGN jk}
+// ---------------------------------------------------------------------------
+template <int SIGN>
+__device__ __forceinline__ void dft2(float2& a0, float2& a1) {
+  float2 t = a0;
+  a0 = cadd(t, a1);
+  a1 = csub(t, a1);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft3(float2& a0, float2& a1, float2& a2) {
+  const float c = -0.5f;
+  const float s = 0.86602540378443864676f;  // sin(2 pi / 3)
+  float2 t1 = cadd(a1, a2);
+  float2 t2 = csub(a1, a2);
+  float2 y0 = cadd(a0, t1);
+  float2 b = make_float2(fmaf(c, t1.x, a0.x), fmaf(c, t1.y, a0.y));
+  float2 rot = cscale(cmul_i<SIGN>(t2), s);
+  a0 = y0;
+  a1 = cadd(b, rot);
+  a2 = csub(b, rot);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  float2 s13 = cadd(a1, a3), d13 = cmul_i<SIGN>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft5(float2& a0, float2& a1, float2& a2, float2& a3, float2& a4) {
+  const float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
+  const float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
+  const float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
+  const float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
+  float2 p14 = cadd(a1, a4), m14 = csub(a1, a4);
+  float2 p23 = cadd(a2, a3), m23 = csub(a2, a3);
+  float2 y0 = cadd(a0, cadd(p14, p23));
+  float2 b1 = make_float2(a0.x + c1 * p14.x + c2 * p23.x, a0.y + c1 * p14.y + c2 * p23.y);
+  float2 b2 = make_float2(a0.x + c2 * p14.x + c1 * p23.x, a0.y + c2 * p14.y + c1 * p23.y);
+  float2 r1 = cmul_i<SIGN>(make_float2(s1 * m14.x + s2 * m23.x, s1 * m14.y + s2 * m23.y));
+  float2 r2 = cmul_i<SIGN>(make_float2(s2 * m14.x - s1 * m23.x, s2 * m14.y - s1 * m23.y));
+  a0 = y0;
+  a1 = cadd(b1, r1);
+  a4 = csub(b1, r1);
+  a2 = cadd(b2, r2);
+  a3 = csub(b2, r2);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft8(float2* a) {
+  const float r = 0.70710678118654752440f;
+  float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+  float2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+  dft4<SIGN>(e0, e1, e2, e3);
+  dft4<SIGN>(o0, o1, o2, o3);
+  // o_k *= zeta_8^{SIGN k}
+  o1 = make_float2(r * (o1.x - SIGN * o1.y), r * (o1.y + SIGN * o1.x));
+  o2 = cmul_i<SIGN>(o2);
+  o3 = make_float2(r * (-o3.x - SIGN * o3.y), r * (-o3.y + SIGN * o3.x));
+  a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
+  a[1] = cadd(e1, o1); a[5] = csub(e1, o1);
+  a[2] = cadd(e2, o2); a[6] = csub(e2, o2);
+  a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft16(float2* a) {
+  // cos(k pi / 8), sin(k pi / 8), k = 0..7
+  const float C[8] = {1.0f, 0.92387953251128675613f, 0.70710678118654752440f, 0.38268343236508977173f,
+                      0.0f, -0.38268343236508977173f, -0.70710678118654752440f, -0.92387953251128675613f};
+  const float S[8] = {0.0f, 0.38268343236508977173f, 0.70710678118654752440f, 0.92387953251128675613f,
+                      1.0f, 0.92387953251128675613f, 0.70710678118654752440f, 0.38268343236508977173f};
+  float2 e[8], o[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    e[k] = a[2 * k];
+    o[k] = a[2 * k + 1];
+  }
+  dft8<SIGN>(e);
+  dft8<SIGN>(o);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) o[k] = cmul(o[k], make_float2(C[k], SIGN * S[k]));
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    a[k] = cadd(e[k], o[k]);
+    a[k + 8] = csub(e[k], o[k]);
+  }
+}
+
+template <int R, int SIGN>
+__device__ __forceinline__ void dft_reg(float2* v) {
+  if constexpr (R == 2) dft2<SIGN>(v[0], v[1]);
+  else if constexpr (R == 3) dft3<SIGN>(v[0], v[1], v[2]);
+  else if constexpr (R == 4) dft4<SIGN>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 5) dft5<SIGN>(v[0], v[1], v[2], v[3], v[4]);
+  else if constexpr (R == 8) dft8<SIGN>(v);
+  else if constexpr (R == 16) dft16<SIGN>(v);
+}
+
+// ---------------------------------------------------------------------------
+// One Stockham pass of radix R over `nbuf` arrays of length n, stored at
+// base + a * stride (a < nbuf).  Butterfly j (< n/R) reads x[j + r n/R],
+// multiplies by zeta_{Ns R}^{SIGN r (j mod Ns)}, transforms, and writes
+// y[(j / Ns) Ns R + (j mod Ns) + r Ns].  In place: loads, barrier, stores.
+// Requires nbuf * n <= PTS * blockDim.x (checked by the host planner).
+// ---------------------------------------------------------------------------
+template <int R, int SIGN, int PTS>
+__device__ __forceinline__ void fft_stage(float2* base, int stride, int nbuf, int n, int Ns,
+                                          const float2* __restrict__ tw, int twmul) {
+  constexpr int BPT = (PTS + R - 1) / R;
+  const int nb = n / R;
+  const int total = nb * nbuf;
+  const int T = blockDim.x;
+  const int twstep = twmul * (n / (Ns * R));
+  float2 v[BPT][R];
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    const int idx = threadIdx.x + b * T;
+    if (idx < total) {
+      const int a = idx / nb;
+      const int j = idx - a * nb;
+      const float2* x = base + (size_t)a * stride;
+      const int jm = j % Ns;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = x[j + r * nb];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw_get<SIGN>(tw, r * jm * twstep));
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    const int idx = threadIdx.x + b * T;
+    if (idx < total) {
+      const int a = idx / nb;
+      const int j = idx - a * nb;
+      float2* y = base + (size_t)a * stride;
+      const int jm = j % Ns;
+      dft_reg<R, SIGN>(v[b]);
+      const int o = (j - jm) * R + jm;
+#pragma unroll
+      for (int r = 0; r < R; ++r) y[o + r * Ns] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Generic radix (any R, used for prime factors other than 2, 3, 5): each
+// thread computes whole output points as direct sums over the R inputs of
+// its butterfly, keeps them in registers until the barrier, then stores.
+template <int SIGN, int PTS>
+__device__ __forceinline__ void fft_stage_generic(float2* base, int stride, int nbuf, int n, int R, int Ns,
+                                                  const float2* __restrict__ tw, int twmul) {
+  const int total = n * nbuf;
+  const int T = blockDim.x;
+  const int nb = n / R;
+  const int step_tw = n / (Ns * R);  // zeta_{Ns R} = zeta_n^{step_tw}
+  const int step_r = n / R;          // zeta_R = zeta_n^{step_r}
+  float2 out[PTS];
+#pragma unroll
+  for (int k = 0; k < PTS; ++k) {
+    const int o = threadIdx.x + k * T;
+    if (o < total) {
+      const int a = o / n;
+      const int oo = o - a * n;
+      const int jm = oo % Ns;
+      const int r = (oo / Ns) % R;
+      const int j = (oo / (Ns * R)) * Ns + jm;
+      const float2* x = base + (size_t)a * stride;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int r2 = 0; r2 < R; ++r2) {
+        const int e = (r2 * jm * step_tw + ((r * r2) % R) * step_r) % n;
+        const float2 w = tw_get<SIGN>(tw, e * twmul);
+        const float2 xv = x[j + r2 * nb];
+        acc.x = fmaf(xv.x, w.x, fmaf(-xv.y, w.y, acc.x));
+        acc.y = fmaf(xv.x, w.y, fmaf(xv.y, w.x, acc.y));
+      }
+      out[k] = acc;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < PTS; ++k) {
+    const int o = threadIdx.x + k * T;
+    if (o < total) {
+      const int a = o / n;
+      base[(size_t)a * stride + (o - a * n)] = out[k];
+    }
+  }
+  __syncthreads();
+}
+
+// Whole DFT of length pl.n on nbuf arrays (base + a * stride), in place.
+// Ends with a barrier; the caller must have synchronised before the call.
+template <int SIGN, int PTS>
+__device__ __noinline__ void cta_fft(float2* base, int stride, int nbuf, const FftPlan& pl, const float2* __restrict__ tw,
+                        int twmul) {
+  const int n = pl.n;
+  int Ns = 1;
+  for (int st = 0; st < pl.nst; ++st) {
+    const int R = pl.radix[st];
+    switch (R) {
+      case 2: fft_stage<2, SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul); break;
+      case 3: fft_stage<3, SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul); break;
+      case 4: fft_stage<4, SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul); break;
+      case 5: fft_stage<5, SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul); break;
+      case 8: fft_stage<8, SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul); break;
+      case 16: fft_stage<16, SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul); break;
+      default: fft_stage_generic<SIGN, PTS>(base, stride, nbuf, n, R, Ns, tw, twmul); break;
+    }
+    Ns *= R;
+  }
+}
+
+}  // namespace hd

@@ -1,0 +1,59 @@
+// hd_internal.h -- host-side declarations shared by the library's .cu files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "../../include/hdconv.h"
+#include "hd_fft.cuh"
+
+namespace hd {
+
+// Per-item descriptor of a 1D convolution (one CTA, or one cluster, each).
+struct Item1D {
+  int64_t off;       // offset (in floats) of the item in f, g and h
+  int32_t L;         // real length
+  int32_t m, q, p;   // hybrid parameters (packed lengths for hybridRCM)
+  int32_t plan;      // index of the length-m FFT plan
+  int32_t plan_half; // index of the length-m/2 FFT plan (-1 if unused)
+  int32_t pad;
+  const float2* tw;  // zeta_N^k table, N = q m
+  void* gacc;        // accumulator in global memory, or nullptr for shared memory
+};
+
+// Host planner (hd_plan.cpp).
+bool factor_radices(int n, FftPlan* out);  // false if n < 1
+bool smooth235(int64_t n);
+int64_t next_smooth(int64_t n);
+
+// Twiddle tables: zeta_N^k, k < N, FP64 on the device, rounded to FP32.
+struct TableCache {
+  std::map<int64_t, float2*> tabs;
+  const float2* get(int64_t N, cudaStream_t st, hd_status* err);
+  void clear();
+};
+
+}  // namespace hd
+
+struct hd_ctx {
+  int device = 0;
+  hd::TableCache tables;
+  // reusable device scratch, grown on demand
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // plan/item upload buffers for single calls
+  void* meta = nullptr;
+  size_t meta_bytes = 0;
+  int* dev_err = nullptr;  // device error word (bounded waits, bad launches)
+  int max_smem = 0;        // opt-in shared memory per block
+  int num_sms = 0;
+  std::mutex mu;
+};
+
+namespace hd {
+hd_status ensure_ws(hd_ctx* c, size_t bytes);
+hd_status ensure_meta(hd_ctx* c, size_t bytes);
+}  // namespace hd

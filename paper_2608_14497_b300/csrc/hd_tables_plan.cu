@@ -1,0 +1,106 @@
+// hd_tables_plan.cu -- roots-of-unity tables (FP64 -> FP32) and FFT radix plans.
+//
+// Tables: tw[k] = zeta_N^k = exp(2 pi i k / N), k < N (Sec. 2 notation), for
+// each padded length N = q m in use.  They are evaluated in FP64 on the GPU
+// (sincospi of the exact rational 2k/N) and rounded once to FP32, so every
+// twiddle the FP32 kernels use is correctly rounded to within 1 ulp.  One table
+// serves all DFT lengths dividing N: zeta_n^x = tw[x N / n].
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "hd_internal.h"
+
+namespace hd {
+
+__global__ void k_roots_fp64(float2* __restrict__ tw, int64_t N) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+    double s, c;
+    // 2k/N in [0, 2): reduce to [-1, 1] to keep the argument small
+    double x = (2.0 * (double)k) / (double)N;
+    if (x > 1.0) x -= 2.0;
+    sincospi(x, &s, &c);
+    tw[k] = make_float2((float)c, (float)s);
+  }
+}
+
+const float2* TableCache::get(int64_t N, cudaStream_t st, hd_status* err) {
+  auto it = tabs.find(N);
+  if (it != tabs.end()) return it->second;
+  float2* p = nullptr;
+  if (cudaMalloc(&p, sizeof(float2) * (size_t)N) != cudaSuccess) {
+    *err = HD_ENOMEM;
+    return nullptr;
+  }
+  int threads = 256;
+  int64_t blocks64 = (N + threads - 1) / threads;
+  int blocks = (int)(blocks64 < 4096 ? blocks64 : 4096);
+  k_roots_fp64<<<blocks, threads, 0, st>>>(p, N);
+  if (cudaGetLastError() != cudaSuccess) {
+    cudaFree(p);
+    *err = HD_ECUDA;
+    return nullptr;
+  }
+  tabs[N] = p;
+  return p;
+}
+
+void TableCache::clear() {
+  for (auto& kv : tabs) cudaFree(kv.second);
+  tabs.clear();
+}
+
+// Radix sequence for a DFT of length n: radix 16, 8, 4, 2 for the power of
+// two, then 5 and 3, then any remaining prime as a generic stage.
+bool factor_radices(int n, FftPlan* out) {
+  if (n < 1) return false;
+  std::memset(out, 0, sizeof(*out));
+  out->n = n;
+  int v = n, k = 0;
+  auto push = [&](int r) {
+    if (k >= kMaxStages) return false;
+    out->radix[k++] = r;
+    return true;
+  };
+  while (v % 16 == 0) { if (!push(16)) return false; v /= 16; }
+  if (v % 8 == 0) { if (!push(8)) return false; v /= 8; }
+  if (v % 4 == 0) { if (!push(4)) return false; v /= 4; }
+  if (v % 2 == 0) { if (!push(2)) return false; v /= 2; }
+  while (v % 5 == 0) { if (!push(5)) return false; v /= 5; }
+  while (v % 3 == 0) { if (!push(3)) return false; v /= 3; }
+  for (int pr = 7; v > 1; pr += 2) {
+    while (v % pr == 0) { if (!push(pr)) return false; v /= pr; }
+    if ((int64_t)pr * pr > v && v > 1) { if (!push(v)) return false; v = 1; }
+  }
+  out->nst = k;
+  return true;
+}
+
+bool smooth235(int64_t n) {
+  if (n < 1) return false;
+  for (int p : {2, 3, 5})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+int64_t next_smooth(int64_t n) {
+  if (n < 1) n = 1;
+  while (!smooth235(n)) ++n;
+  return n;
+}
+
+hd_status ensure_ws(hd_ctx* c, size_t bytes) {
+  if (bytes <= c->ws_bytes) return HD_OK;
+  if (c->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+  }
+  if (cudaMalloc(&c->ws, bytes) != cudaSuccess) return HD_ENOMEM;
+  c->ws_bytes = bytes;
+  return HD_OK;
+}
+
+}  // namespace hd

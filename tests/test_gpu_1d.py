@@ -1,0 +1,138 @@
+"""GPU parity of the 1D paths against the FP64 oracle (relL2 <= 1e-5, FP32)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import steps
+from paper_2608_14497_b300 import inputs
+from tests.conftest import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+HYBRID = ("hybridRCM", "hybridCS")
+ALL = ("hybridRCM", "hybridCS", "explicit", "explicitRCM")
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import paper_2608_14497_b300 as m
+    m.load()
+    assert torch.cuda.is_available()
+    return m
+
+
+def run(hd, f, g, algo, params=None):
+    tf = torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).cuda()
+    tg = torch.from_numpy(np.ascontiguousarray(g, dtype=np.float32)).cuda()
+    h = hd.conv(tf, tg, algo=algo, params=params)
+    torch.cuda.synchronize()
+    return h.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("algo", ALL)
+def test_L4096_uniform(hd, algo):
+    f, g = inputs.uniform_pair(4096, seed=1)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    assert rel_l2(run(hd, f, g, algo), ref) <= TOL
+
+
+@pytest.mark.parametrize("algo", ALL)
+def test_L4096_integer_exact(hd, algo):
+    f, g = inputs.integer_pair(4096, seed=7)
+    ref = oracle.direct_conv(f, g)
+    h = run(hd, f, g, algo)
+    assert np.abs(h - ref).max() < 0.5
+    assert np.array_equal(np.rint(h), ref)
+
+
+def kappa(f, g, h):
+    """Normwise condition number of the convolution, ||f|| ||g|| / ||h||."""
+    return np.linalg.norm(f) * np.linalg.norm(g) / np.linalg.norm(h)
+
+
+def fp32_fft_conv_bound(N, kap):
+    """Normwise bound for an FP32 FFT convolution: three transforms of log2 N
+    radix-2-equivalent stages, each adding at most about 6 units of roundoff
+    (Higham, Accuracy and Stability of Numerical Algorithms, Sec. 24.1), scaled
+    by the conditioning ||f|| ||g|| / ||h||."""
+    return 18 * np.log2(N) * np.finfo(np.float32).eps * kap
+
+
+@pytest.mark.parametrize("algo", ALL)
+def test_L4096_geometric_closed_form(hd, algo):
+    """Positive ratios: no cancellation, the FP32 result meets 1e-5."""
+    a, b = 0.9995, 0.999
+    f, g = inputs.geometric_pair(4096, a, b)
+    k = np.arange(4096, dtype=np.float64)
+    ref = (a ** (k + 1) - b ** (k + 1)) / (a - b)
+    assert rel_l2(run(hd, f, g, algo), ref) <= TOL
+
+
+@pytest.mark.parametrize("algo", ALL)
+def test_L4096_geometric_alternating(hd, algo):
+    """a = 0.9995, b = -0.999: heavy cancellation (kappa ~ 43), so the bound
+    is the FP32 FFT-convolution bound scaled by kappa, not 1e-5."""
+    a, b = 0.9995, -0.999
+    f, g = inputs.geometric_pair(4096, a, b)
+    k = np.arange(4096, dtype=np.float64)
+    ref = (a ** (k + 1) - b ** (k + 1)) / (a - b)
+    err = rel_l2(run(hd, f, g, algo), ref)
+    assert err <= fp32_fft_conv_bound(2 * 4096, kappa(f, g, ref))
+
+
+@pytest.mark.parametrize("algo", ALL)
+@pytest.mark.parametrize("L", [1, 2, 3, 5, 17, 100, 127, 1000, 3001, 5000, 8192, 12345, 20000, 70000])
+def test_ragged_lengths_default_plan(hd, algo, L):
+    f, g = inputs.uniform_pair(L, seed=L)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    assert rel_l2(run(hd, f, g, algo), ref) <= TOL
+
+
+@pytest.mark.parametrize("L", list(range(1, 17)))
+def test_brute_force_every_valid_m_q(hd, L):
+    f, g = inputs.uniform_pair(L, seed=200 + L)
+    ref = oracle.direct_conv(f, g)
+    for m in range(1, 2 * L + 1):
+        for q in (-(-(2 * L - 1) // m), -(-(2 * L - 1) // m) + 1):
+            if steps.cs_valid(L, m, q):
+                assert rel_l2(run(hd, f, g, "hybridCS", [(m, q)]), ref) <= TOL, (L, m, q)
+        for q in (-(-L // m), -(-L // m) + 1):
+            if steps.rcm_valid(L, m, q):
+                assert rel_l2(run(hd, f, g, "hybridRCM", [(m, q)]), ref) <= TOL, (L, m, q)
+
+
+@pytest.mark.parametrize("L,m,q,algo", [
+    (5000, 512, 10, "hybridRCM"), (5000, 700, 8, "hybridRCM"), (5000, 625, 9, "hybridRCM"),
+    (4999, 1000, 10, "hybridCS"), (4999, 1001, 11, "hybridCS"), (5000, 768, 14, "hybridCS"),
+    (70000, 4096, 18, "hybridRCM"), (70000, 8000, 18, "hybridCS"), (4096, 7 * 11 * 13, 5, "hybridRCM"),
+])
+def test_explicit_parameters_p_gt_1(hd, L, m, q, algo):
+    f, g = inputs.normal_pair(L, seed=300)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    assert rel_l2(run(hd, f, g, algo, [(m, q)]), ref) <= TOL
+
+
+@pytest.mark.parametrize("algo", ALL)
+def test_in_place(hd, algo):
+    f, g = inputs.uniform_pair(3000, seed=9)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    tf = torch.from_numpy(f).cuda()
+    tg = torch.from_numpy(g).cuda()
+    hd.conv(tf, tg, algo=algo, out=tf)
+    torch.cuda.synchronize()
+    assert rel_l2(tf.cpu().numpy(), ref) <= TOL
+
+
+def test_invalid_parameters_rejected(hd):
+    f = torch.zeros(100, device="cuda")
+    with pytest.raises(hd.HDError) as e:
+        hd.conv(f, f, algo="hybridRCM", params=[(10, 5)])  # qm = 50 < L
+    assert e.value.status == hd.HD_EINVAL
+    with pytest.raises(hd.HDError) as e:
+        hd.conv(f, f, algo="hybridCS", params=[(101, 2)])  # q even, m odd
+    assert e.value.status == hd.HD_EINVAL
+    with pytest.raises(hd.HDError) as e:
+        hd.conv(f, f, algo="hybridCS", params=[(50, 3)])  # qm = 150 < 2L-1
+    assert e.value.status == hd.HD_EINVAL
