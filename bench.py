@@ -1,0 +1,350 @@
+"""Benchmark: batched 1D real convolutions by hybrid dealiasing on one B300.
+
+Workload (one step): 4096 independent real convolutions of lengths drawn
+uniformly from 500..70000 (seed 2), values standard normal (seed 3), FP32,
+first L outputs each, computed by one call of the batched C-ABI entry point
+(one kernel launch), replayed from a CUDA graph.  Inputs and outputs (3 x 0.58
+GB) are larger than the 126 MB L2, so no flush is needed between steps.
+
+Printed: one JSON line (rank 0).  ``value`` is whole-job convolutions/s with
+inputs resident in HBM; ``e2e`` the same metric through the C ABI with pinned
+HOST buffers (host-to-device copies of f and g and the device-to-host copy of
+h inside the timed region); ``roofline`` the dominant kernel's algorithmic HBM
+bytes (12 bytes per real element: read f and g, write h) per launch over its
+measured duration, against the measured copy bandwidth; ``cpu_baseline`` the
+FP64 oracle (padded radix-2 FFT convolution, OpenMP over items) on a bounded
+sample of the same items.
+
+``--impl reference`` times that oracle alone on the host cores for the same
+workload and metric (there is no reference implementation to install).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ITEMS = 4096
+L_LO, L_HI = 500, 70000
+SEED_L, SEED_V = 2, 3
+WORKLOAD = "1D batched: 4096 real convolutions, L ~ U{500..70000} (seed 2), N(0,1) values (seed 3), FP32"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2608_14497_b300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, name), "rb") as fh:
+                h.update(name.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+def recorded_traffic(kernel, algo):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(f"{kernel}:{algo}")
+    if not e or e.get("csrc_hash") != csrc_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sms.append(float(parts[0]))
+                maxes.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxes), "reasons": sorted(reasons)}
+
+
+def workload(n_items=N_ITEMS):
+    from paper_2608_14497_b300 import inputs
+    off, Ls = inputs.batch_lengths(n_items, L_LO, L_HI, SEED_L)
+    total = int(Ls.sum())
+    f, g = inputs.batch_values(total, SEED_V)
+    return off, Ls, f, g
+
+
+def cpu_oracle_sample(off, Ls, f, g, budget_items=None):
+    """Time the FP64 oracle on a bounded sample of the items (every k-th)."""
+    import oracle
+    k = 16 if budget_items is None else max(1, len(Ls) // budget_items)
+    idx = np.arange(0, len(Ls), k)
+    soff = np.zeros(len(idx), dtype=np.int64)
+    sL = Ls[idx]
+    soff[1:] = np.cumsum(sL)[:-1]
+    sf = np.concatenate([f[off[i]:off[i] + Ls[i]] for i in idx]).astype(np.float64)
+    sg = np.concatenate([g[off[i]:off[i] + Ls[i]] for i in idx]).astype(np.float64)
+    oracle.batch_conv1d(sf[:1], sg[:1], soff[:1] * 0, np.array([1]))  # build / load
+    t0 = time.perf_counter()
+    oracle.batch_conv1d(sf, sg, soff, sL, use_fft=True)
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    omp = os.environ.get("OMP_NUM_THREADS")
+    if omp:
+        cores = min(cores, int(omp))
+    return {"value": len(idx) / dt, "unit": "conv/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(idx)} of {len(Ls)} items (every {k}th, sum L = {int(sL.sum())}); FP64 radix-2 FFT "
+                      f"convolution padded to a power of two >= 2L-1, OpenMP over items; {dt:.2f} s"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    off, Ls, f, g = workload()
+    times, last = [], None
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        last = cpu_oracle_sample(off, Ls, f, g, budget_items=128)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = last["value"]
+    line = {"metric": "convolutions/s", "value": value, "unit": "conv/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "items_per_step": "sample of 128", "l2": "inputs > L2"},
+            "impl": "reference", "cpu_baseline": last,
+            "e2e": {"value": value, "unit": "conv/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2608_14497_b300 as hd
+    hd.load()
+    off, Ls, f_np, g_np = workload(args.items)
+    total = int(Ls.sum())
+    n = len(Ls)
+    f = torch.from_numpy(f_np).cuda()
+    g = torch.from_numpy(g_np).cuda()
+    h = torch.empty_like(f)
+    plan = hd.BatchPlan(off, Ls, algo=args.algo)
+
+    def step():
+        plan(f, g, out=h)
+
+    # warm-up and graph capture (the plan launches a fixed set of kernels)
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            step()
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+
+    # parity spot check of the timed configuration on sampled items (FP64 oracle)
+    check = None
+    if rank == 0 and not args.no_check:
+        import oracle
+        hh = h.cpu().numpy()
+        errs = []
+        for i in np.linspace(0, n - 1, 6).astype(int):
+            a, b = off[i], off[i] + Ls[i]
+            ref = oracle.fft_conv(f_np[a:b].astype(np.float64), g_np[a:b].astype(np.float64))
+            errs.append(float(np.linalg.norm(hh[a:b] - ref) / np.linalg.norm(ref)))
+        check = max(errs)
+
+    # timed region: K graph replays, device events on the replay stream
+    launches_per_step = plan_launches(plan)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        cur = torch.cuda.current_stream()
+        ev0.record(cur)
+        for _ in range(args.steps):
+            graph.replay()
+        ev1.record(cur)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_step = ms / args.steps
+    value = world * n * args.steps / (ms / 1e3)
+
+    # dominant kernel: the single batched launch; achieved = 12 B/element / duration
+    kern_ms = ms_step / launches_per_step if launches_per_step == 1 else None
+    peak, peak_kind = measured_peaks()
+    alg_bytes = 12.0 * total
+    achieved = alg_bytes / (ms_step * 1e-3) / 1e9 if kern_ms is not None else None
+    traffic = recorded_traffic("k_" + args.algo, args.algo)
+
+    # end to end: pinned host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hf = torch.from_numpy(f_np).pin_memory()
+        hg = torch.from_numpy(g_np).pin_memory()
+        hh = torch.empty_like(hf).pin_memory()
+        df, dg, dh = torch.empty_like(f), torch.empty_like(g), torch.empty_like(h)
+
+        def e2e_step():
+            df.copy_(hf, non_blocking=True)
+            dg.copy_(hg, non_blocking=True)
+            plan(df, dg, out=dh)
+            hh.copy_(dh, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ksteps = max(1, min(args.steps, 5))
+        ee0.record()
+        for _ in range(ksteps):
+            e2e_step()
+        ee1.record()
+        torch.cuda.synchronize()
+        ems = ee0.elapsed_time(ee1)
+        if dist is not None:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * n * ksteps / (ems / 1e3), "unit": "conv/s", "h2d_bytes_per_step": 8 * total,
+               "d2h_bytes_per_step": 4 * total, "steps": ksteps}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_sample(off, Ls, f_np, g_np)
+    line = {
+        "metric": "convolutions/s", "value": value, "unit": "conv/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if n == N_ITEMS else f"{n} items of the same distribution", "algo": args.algo,
+                   "items": n, "sum_L": total,
+                   "l2": "inputs larger than L2 (1.73 GB per step), no flush", "graph": True,
+                   "parallelism": f"replicas x{world} (independent batches, no collective)"},
+        "relL2_sampled_max": check,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "peak_source": peak_kind, "kernel": "k_rcm1d" if args.algo == "hybridRCM" else "k_cs1d",
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def plan_launches(plan):
+    return 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--algo", default="hybridRCM", choices=["hybridRCM", "hybridCS"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--items", type=int, default=N_ITEMS,
+                    help="batch size; smaller batches are for profiling captures, not for the reported line")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

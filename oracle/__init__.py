@@ -37,6 +37,8 @@ def _load():
             fn = getattr(lib, name)
             fn.argtypes = [ctypes.c_int, P, P, P, P, P]
             fn.restype = ctypes.c_int
+        lib.hd_direct_conv_points.argtypes = [ctypes.c_int, P, ctypes.c_int64, P, P, P, P]
+        lib.hd_direct_conv_points.restype = ctypes.c_int
         lib.hd_batch_conv1d.argtypes = [ctypes.c_int64, P, P, P, P, P, ctypes.c_int]
         lib.hd_batch_conv1d.restype = ctypes.c_int
         _lib = lib
@@ -70,6 +72,19 @@ def direct_conv(f, g, K=None):
     if rc:
         raise ValueError(f"hd_direct_conv failed ({rc})")
     return h
+
+
+def direct_conv_points(f, g, points):
+    """O1 at chosen output multi-indices (rows of ``points``), by direct summation."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    L = np.asarray(f.shape, dtype=np.int64)
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int64).reshape(-1, f.ndim))
+    out = np.empty(len(pts), dtype=np.float64)
+    rc = _load().hd_direct_conv_points(f.ndim, _ptr(L), len(pts), _ptr(pts), _ptr(f), _ptr(g), _ptr(out))
+    if rc:
+        raise ValueError(f"hd_direct_conv_points failed ({rc})")
+    return out
 
 
 def direct_corr(u, g, L=None):

@@ -74,6 +74,33 @@ int hd_direct_conv(int d, const int64_t *L_, const int64_t *K_, const double *f,
   return 0;
 }
 
+/* O1 at chosen output points only: h[k] for the npts multi-indices in
+ * pts[npts][d] (each 0 <= k_i < 2L_i - 1), by the same direct sum.  Used to
+ * check full-size results where computing every output would take too long. */
+int hd_direct_conv_points(int d, const int64_t *L_, int64_t npts, const int64_t *pts, const double *f,
+                          const double *g, double *out) {
+  if (d < 1 || d > 3) return 1;
+  int64_t L[3];
+  shape3(d, L_, L);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < npts; ++i) {
+    int64_t k[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) k[3 - d + a] = pts[i * d + a];
+    double acc = 0.0;
+    const int64_t a0 = k[0] - (L[0] - 1) > 0 ? k[0] - (L[0] - 1) : 0, b0 = k[0] < L[0] - 1 ? k[0] : L[0] - 1;
+    const int64_t a1 = k[1] - (L[1] - 1) > 0 ? k[1] - (L[1] - 1) : 0, b1 = k[1] < L[1] - 1 ? k[1] : L[1] - 1;
+    const int64_t a2 = k[2] - (L[2] - 1) > 0 ? k[2] - (L[2] - 1) : 0, b2 = k[2] < L[2] - 1 ? k[2] : L[2] - 1;
+    for (int64_t j0 = a0; j0 <= b0; ++j0)
+      for (int64_t j1 = a1; j1 <= b1; ++j1) {
+        const double *fr = f + (j0 * L[1] + j1) * L[2];
+        const double *gr = g + ((k[0] - j0) * L[1] + (k[1] - j1)) * L[2];
+        for (int64_t j2 = a2; j2 <= b2; ++j2) acc += fr[j2] * gr[k[2] - j2];
+      }
+    out[i] = acc;
+  }
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* O1': the adjoint of the map f -> h = conv_K(f, g) (K outputs per dim):     */
 /* grad_f[j] = sum over k with 0 <= k_i < K_i and 0 <= k_i - j_i < L_i of     */

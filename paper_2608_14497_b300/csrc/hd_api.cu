@@ -7,6 +7,7 @@
 #include <cstring>
 #include <string>
 
+#include "hd_cluster.cuh"
 #include "hd_conv1d.cuh"
 #include "hd_internal.h"
 #include "hd_nd.cuh"
@@ -29,25 +30,11 @@ namespace hd {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Largest 2,3,5-smooth number <= n (n >= 1).
-static int64_t prev_smooth(int64_t n) {
-  while (n > 1 && !smooth235(n)) --n;
-  return n < 1 ? 1 : n;
-}
-
 static int64_t next_smooth_even(int64_t n) {
   int64_t m = next_smooth(n < 2 ? 2 : n);
   while (m % 2) m = next_smooth(m + 1);
   return m;
 }
-
-// Parameters of one 1D convolution, resolved against the kernel limits.
-struct Params1D {
-  int m = 0, q = 0, p = 0;
-  bool gacc = false;
-  int threads = 0;
-  size_t smem = 0;
-};
 
 // hybridRCM: packed length Lp = ceil(L/2) must satisfy p m >= Lp (p =
 // ceil(Lp/m)) and q m >= L (real padded length 2qm >= 2L-1).  The planner
@@ -121,8 +108,35 @@ hd_status resolve_cs1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D*
   return HD_OK;
 }
 
+// hybridRCM with planner parameters: the cluster kernel, one unit by value.
+static hd_status conv1d_rcm_cluster(hd_ctx* c, const float* f, const float* g, float* h, int64_t L, int C, int m,
+                                    int p, cudaStream_t st) {
+  hd_status terr = HD_OK;
+  const float2* tw = c->tables.get((int64_t)2 * C * m, st, &terr);
+  if (!tw) return fail(terr, "twiddle table allocation failed");
+  ClusterLaunch cl;
+  std::memset(&cl, 0, sizeof(cl));
+  cl.one_unit.first = 0;
+  cl.one_unit.count = 1;
+  cl.one_unit.C = C;
+  cl.one_item.off = 0;
+  cl.one_item.L = (int32_t)L;
+  cl.one_item.m = m;
+  cl.one_item.p = p;
+  cl.one_item.C = C;
+  cl.one_item.tw = tw;
+  factor_radices(m, &cl.one_plan);
+  cudaError_t e = launch_rcm1d_cluster(cl, 1, cluster_smem_bytes(m), f, g, h, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cluster launch");
+  return HD_OK;
+}
+
 static hd_status conv1d_hybrid(hd_ctx* c, hd_algo algo, const float* f, const float* g, float* h, int64_t L,
                                const hd_dim_params* prm, cudaStream_t st) {
+  if (algo == HD_HYBRID_RCM && !(prm && prm->m > 0)) {
+    int C, m, p;
+    if (cluster_params(L, &C, &m, &p)) return conv1d_rcm_cluster(c, f, g, h, L, C, m, p, st);
+  }
   Params1D P;
   hd_status s = (algo == HD_HYBRID_RCM) ? resolve_rcm1d(c, L, prm, &P) : resolve_cs1d(c, L, prm, &P);
   if (s != HD_OK) return s;
@@ -213,7 +227,16 @@ hd_status hd_plan(hd_ctx* c, hd_algo algo, int64_t L, hd_dim_params* out) {
   Params1D P;
   hd_status s;
   switch (algo) {
-    case HD_HYBRID_RCM: s = resolve_rcm1d(c, L, nullptr, &P); break;
+    case HD_HYBRID_RCM: {
+      int C, m, p;
+      if (cluster_params(L, &C, &m, &p)) {
+        out->m = m;
+        out->q = 2 * C;
+        return HD_OK;
+      }
+      s = resolve_rcm1d(c, L, nullptr, &P);
+      break;
+    }
     case HD_HYBRID_CS: s = resolve_cs1d(c, L, nullptr, &P); break;
     default: return fail(HD_EINVAL, "hd_plan: hybrid algorithms only");
   }

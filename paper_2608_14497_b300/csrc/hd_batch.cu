@@ -1,0 +1,233 @@
+// hd_batch.cu -- batched 1D convolutions of uneven lengths.
+//
+// The plan is built once on the host: for every item the planner resolves the
+// hybrid parameters (m, q) of Sec. 2 for its length (the role of the paper's
+// empirical scan over m, Sec. 6), distinct DFT lengths share one radix plan,
+// distinct padded lengths N = qm share one twiddle table, and items are grouped
+// into one launch (block size and shared memory of the largest item), ordered
+// longest first so the block scheduler balances the tail.  Everything the kernels read (item table, radix
+// plans, tables, accumulator scratch) is uploaded or allocated here, so a
+// launch of the plan performs no allocation and no host-to-device copy and can
+// be captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "hd_cluster.cuh"
+#include "hd_conv1d.cuh"
+#include "hd_internal.h"
+
+namespace hd {
+struct LaunchClass {
+  int first = 0, count = 0;  // range in the device item table
+  int threads = 0;
+  size_t smem = 0;
+};
+}  // namespace hd
+
+struct hd_batch_plan {
+  hd_algo algo;
+  int n = 0;
+  int device = 0;
+  hd::Item1D* d_items = nullptr;
+  hd::FftPlan* d_plans = nullptr;
+  void* d_acc = nullptr;
+  std::vector<hd::LaunchClass> classes;
+  int64_t total_len = 0;
+  // cluster path (hybridRCM): units of 8 CTAs
+  hd::CUnit* d_units = nullptr;
+  hd::CItem* d_citems = nullptr;
+  int nunits = 0;
+  size_t csmem = 0;
+};
+
+using namespace hd;
+
+extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, const int64_t* offsets,
+                                          const int32_t* Ls, hd_batch_plan** out) {
+  if (!c || !offsets || !Ls || !out || n < 1) return HD_EINVAL;
+  if (algo != HD_HYBRID_RCM && algo != HD_HYBRID_CS) return HD_EUNSUPPORTED;
+  cudaSetDevice(c->device);
+  struct HostItem {
+    Item1D it;
+    Params1D P;
+    int64_t acc_bytes;
+  };
+  std::vector<HostItem> hs;
+  hs.reserve(n);
+  std::vector<FftPlan> plans;
+  std::map<int, int> plan_of;
+  auto plan_index = [&](int len) {
+    auto f = plan_of.find(len);
+    if (f != plan_of.end()) return f->second;
+    FftPlan p;
+    factor_radices(len, &p);
+    plans.push_back(p);
+    return plan_of[len] = (int)plans.size() - 1;
+  };
+  int64_t acc_total = 0;
+  for (int i = 0; i < n; ++i)
+    if (Ls[i] < 1 || offsets[i] < 0) return HD_EINVAL;
+  // hybridRCM: every length the cluster kernel covers goes there
+  std::vector<CItem> citems;
+  std::vector<char> in_cluster(n, 0);
+  int m_max = 1;
+  if (algo == HD_HYBRID_RCM) {
+    for (int i = 0; i < n; ++i) {
+      int C, m, p;
+      if (!cluster_params(Ls[i], &C, &m, &p)) continue;
+      hd_status terr = HD_OK;
+      const float2* tw = c->tables.get((int64_t)2 * C * m, 0, &terr);
+      if (!tw) return terr;
+      CItem ci;
+      std::memset(&ci, 0, sizeof(ci));
+      ci.off = offsets[i];
+      ci.L = Ls[i];
+      ci.m = m;
+      ci.p = p;
+      ci.C = C;
+      ci.plan = plan_index(m);
+      ci.tw = tw;
+      citems.push_back(ci);
+      in_cluster[i] = 1;
+      m_max = std::max(m_max, m);
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    if (in_cluster[i]) continue;
+    Params1D P;
+    hd_status s = (algo == HD_HYBRID_RCM) ? resolve_rcm1d(c, Ls[i], nullptr, &P) : resolve_cs1d(c, Ls[i], nullptr, &P);
+    if (s != HD_OK) return s;
+    hd_status terr = HD_OK;
+    const float2* tw = c->tables.get((int64_t)P.q * P.m, 0, &terr);
+    if (!tw) return terr;
+    Item1D it;
+    std::memset(&it, 0, sizeof(it));
+    it.off = offsets[i];
+    it.L = Ls[i];
+    it.m = P.m;
+    it.q = P.q;
+    it.p = P.p;
+    it.plan = plan_index(P.m);
+    it.plan_half = (P.m % 2 == 0) ? plan_index(P.m / 2) : -1;
+    it.tw = tw;
+    int64_t accb = 0;
+    if (P.gacc) {
+      accb = (algo == HD_HYBRID_RCM) ? (int64_t)sizeof(float2) * ((Ls[i] + 1) / 2) : (int64_t)sizeof(float) * Ls[i];
+      accb = (accb + 255) & ~(int64_t)255;
+    }
+    hs.push_back({it, P, accb});
+    acc_total += accb;
+  }
+  const int ng = (int)hs.size();
+  // Items the cluster kernel does not cover: one launch, longest first.
+  std::stable_sort(hs.begin(), hs.end(), [](const HostItem& a, const HostItem& b) { return a.it.L > b.it.L; });
+  hd_batch_plan* bp = new hd_batch_plan();
+  bp->algo = algo;
+  bp->n = n;
+  bp->device = c->device;
+  if (acc_total > 0 && cudaMalloc(&bp->d_acc, acc_total) != cudaSuccess) {
+    delete bp;
+    return HD_ENOMEM;
+  }
+  int64_t acc_off = 0;
+  std::vector<Item1D> items(ng);
+  for (int i = 0; i < ng; ++i) {
+    items[i] = hs[i].it;
+    if (hs[i].acc_bytes) {
+      items[i].gacc = (char*)bp->d_acc + acc_off;
+      acc_off += hs[i].acc_bytes;
+    }
+    bp->total_len += hs[i].it.L;
+    if (bp->classes.empty()) bp->classes.push_back(LaunchClass());
+    LaunchClass& lc = bp->classes.back();
+    lc.count++;
+    lc.threads = std::max(lc.threads, hs[i].P.threads);
+    lc.smem = std::max(lc.smem, hs[i].P.smem);
+  }
+  // cluster units: by C (largest first), lengths descending, 8/C items per unit
+  std::vector<CUnit> units;
+  if (!citems.empty()) {
+    std::stable_sort(citems.begin(), citems.end(), [](const CItem& a, const CItem& b) {
+      if (a.C != b.C) return a.C > b.C;
+      return a.L > b.L;
+    });
+    for (size_t i = 0; i < citems.size();) {
+      const int C = citems[i].C;
+      const int per = kClusterCtas / C;
+      CUnit u;
+      std::memset(&u, 0, sizeof(u));
+      u.first = (int)i;
+      u.C = C;
+      while (i < citems.size() && citems[i].C == C && u.count < per) {
+        ++u.count;
+        ++i;
+      }
+      units.push_back(u);
+    }
+    for (const CItem& ci : citems) bp->total_len += ci.L;
+    bp->nunits = (int)units.size();
+    bp->csmem = cluster_smem_bytes(m_max);
+    if (cudaMalloc(&bp->d_units, sizeof(CUnit) * units.size()) != cudaSuccess ||
+        cudaMalloc(&bp->d_citems, sizeof(CItem) * citems.size()) != cudaSuccess) {
+      hd_batch_plan_destroy(bp);
+      return HD_ENOMEM;
+    }
+    cudaMemcpy(bp->d_units, units.data(), sizeof(CUnit) * units.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(bp->d_citems, citems.data(), sizeof(CItem) * citems.size(), cudaMemcpyHostToDevice);
+  }
+  if ((ng > 0 && cudaMalloc(&bp->d_items, sizeof(Item1D) * ng) != cudaSuccess) ||
+      cudaMalloc(&bp->d_plans, sizeof(FftPlan) * std::max<size_t>(1, plans.size())) != cudaSuccess) {
+    hd_batch_plan_destroy(bp);
+    return HD_ENOMEM;
+  }
+  if (ng > 0) cudaMemcpy(bp->d_items, items.data(), sizeof(Item1D) * ng, cudaMemcpyHostToDevice);
+  if (!plans.empty()) cudaMemcpy(bp->d_plans, plans.data(), sizeof(FftPlan) * plans.size(), cudaMemcpyHostToDevice);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    hd_batch_plan_destroy(bp);
+    return HD_ECUDA;
+  }
+  *out = bp;
+  return HD_OK;
+}
+
+extern "C" hd_status hd_batch_plan_destroy(hd_batch_plan* bp) {
+  if (!bp) return HD_OK;
+  cudaSetDevice(bp->device);
+  cudaDeviceSynchronize();
+  if (bp->d_items) cudaFree(bp->d_items);
+  if (bp->d_plans) cudaFree(bp->d_plans);
+  if (bp->d_acc) cudaFree(bp->d_acc);
+  if (bp->d_units) cudaFree(bp->d_units);
+  if (bp->d_citems) cudaFree(bp->d_citems);
+  delete bp;
+  return HD_OK;
+}
+
+extern "C" hd_status hd_conv1d_batched(hd_ctx* c, const hd_batch_plan* bp, const float* f, const float* g, float* h,
+                                       void* stream) {
+  if (!c || !bp || !f || !g || !h) return HD_EINVAL;
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (bp->nunits > 0) {
+    ClusterLaunch cl;
+    std::memset(&cl, 0, sizeof(cl));
+    cl.units = bp->d_units;
+    cl.items = bp->d_citems;
+    cl.plans = bp->d_plans;
+    if (launch_rcm1d_cluster(cl, bp->nunits, bp->csmem, f, g, h, st) != cudaSuccess) return HD_ECUDA;
+  }
+  for (const LaunchClass& lc : bp->classes) {
+    Launch1D la;
+    std::memset(&la, 0, sizeof(la));
+    la.items = bp->d_items + lc.first;
+    la.plans = bp->d_plans;
+    cudaError_t e = (bp->algo == HD_HYBRID_RCM) ? launch_rcm1d(la, lc.count, lc.threads, lc.smem, f, g, h, st)
+                                                : launch_cs1d(la, lc.count, lc.threads, lc.smem, f, g, h, st);
+    if (e != cudaSuccess) return HD_ECUDA;
+  }
+  return HD_OK;
+}

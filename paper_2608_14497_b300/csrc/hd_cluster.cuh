@@ -1,0 +1,44 @@
+// hd_cluster.cuh -- descriptors of the cluster hybridRCM kernel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "hd_conv1d.cuh"
+#include "hd_internal.h"
+
+namespace hd {
+
+constexpr int kClusterCtas = 8;       // CTAs per cluster
+constexpr int kClusterThreads = 512;  // threads per CTA
+constexpr int kClusterPts = 32;       // FFT points per thread per pass
+constexpr int kClusterMaxM = 4608;    // largest residue DFT length (shared memory)
+
+// One convolution: q = 2C residues of length m, p = ceil(Lp/m) <= C.
+struct CItem {
+  int64_t off;
+  int32_t L, m, p, C;
+  int32_t plan;
+  int32_t pad_;
+  const float2* tw;  // zeta_N^k, N = 2 C m
+};
+
+// A cluster's work: `count` (<= 8/C) consecutive items starting at `first`.
+struct CUnit {
+  int32_t first, count, C, pad_;
+};
+
+struct ClusterLaunch {
+  const CUnit* units;   // nullptr: one_unit / one_item / one_plan
+  const CItem* items;
+  const FftPlan* plans;
+  CUnit one_unit;
+  CItem one_item;
+  FftPlan one_plan;
+};
+
+bool cluster_params(int64_t L, int* C, int* m, int* p);
+size_t cluster_smem_bytes(int m_max);
+cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int nunits, size_t smem, const float* f, const float* g,
+                                 float* h, cudaStream_t st);
+int cluster_max_active(size_t smem);
+
+}  // namespace hd

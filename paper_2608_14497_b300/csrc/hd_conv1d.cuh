@@ -23,6 +23,17 @@ struct Launch1D {
 // rounded to an even count so the buffers behind it stay 16-byte aligned.
 __host__ __device__ __forceinline__ int acc_slots(int nf2) { return (nf2 + 1) & ~1; }
 
+// Parameters of one 1D convolution, resolved against the kernel limits.
+struct Params1D {
+  int m = 0, q = 0, p = 0;
+  bool gacc = false;  // accumulator in global scratch (does not fit on chip)
+  int threads = 0;
+  size_t smem = 0;
+};
+
+hd_status resolve_rcm1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D* out);
+hd_status resolve_cs1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D* out);
+
 size_t rcm1d_smem_bytes(int L, int m, bool gacc);
 size_t cs1d_smem_bytes(int L, int m, bool gacc);
 int threads_for_points(int64_t points, int pts);

@@ -82,10 +82,27 @@ def test_L4096_geometric_alternating(hd, algo):
     assert err <= fp32_fft_conv_bound(2 * 4096, kappa(f, g, ref))
 
 
+def next_smooth(n):
+    while True:
+        k = n
+        for p in (2, 3, 5):
+            while k % p == 0:
+                k //= p
+        if k == 1:
+            return n
+        n += 1
+
+
 @pytest.mark.parametrize("algo", ALL)
 @pytest.mark.parametrize("L", [1, 2, 3, 5, 17, 100, 127, 1000, 3001, 5000, 8192, 12345, 20000, 70000])
 def test_ragged_lengths_default_plan(hd, algo, L):
     f, g = inputs.uniform_pair(L, seed=L)
+    if algo.startswith("explicit") and next_smooth(L) > 16384:
+        # the explicit baselines transform the padded row in one CTA
+        with pytest.raises(hd.HDError) as e:
+            run(hd, f, g, algo)
+        assert e.value.status == hd.HD_EUNSUPPORTED
+        return
     ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
     assert rel_l2(run(hd, f, g, algo), ref) <= TOL
 
@@ -112,6 +129,14 @@ def test_explicit_parameters_p_gt_1(hd, L, m, q, algo):
     f, g = inputs.normal_pair(L, seed=300)
     ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
     assert rel_l2(run(hd, f, g, algo, [(m, q)]), ref) <= TOL
+
+
+@pytest.mark.parametrize("L", [4096, 9000, 17777, 20000, 40001, 65536, 70000, 73728])
+def test_cluster_path_sizes(hd, L):
+    """Lengths that exercise clusters of 1, 2, 4 and 8 CTAs (planner choice)."""
+    f, g = inputs.normal_pair(L, seed=500 + L)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    assert rel_l2(run(hd, f, g, "hybridRCM"), ref) <= TOL
 
 
 @pytest.mark.parametrize("algo", ALL)

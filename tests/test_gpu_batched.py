@@ -1,0 +1,68 @@
+"""GPU parity of the batched 1D path (one launch over uneven lengths)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_14497_b300 import inputs
+from tests.conftest import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import paper_2608_14497_b300 as m
+    m.load()
+    return m
+
+
+def flat(Ls, seed):
+    off = np.zeros(len(Ls), dtype=np.int64)
+    off[1:] = np.cumsum(Ls)[:-1]
+    f, g = inputs.normal_pair(int(np.sum(Ls)), seed)
+    return off, f, g
+
+
+@pytest.mark.parametrize("algo", ["hybridRCM", "hybridCS"])
+def test_batched_small_every_item(hd, algo):
+    rng = np.random.default_rng(40)
+    Ls = np.concatenate([[1, 2, 3, 4, 5, 16, 17, 255, 256, 257], rng.integers(1, 20000, 54)]).astype(np.int64)
+    off, f, g = flat(Ls, 41)
+    plan = hd.BatchPlan(off, Ls, algo=algo)
+    h = plan(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
+    ref = oracle.batch_conv1d(f, g, off, Ls)
+    for i in range(len(Ls)):
+        a, b = off[i], off[i] + Ls[i]
+        assert rel_l2(h[a:b], ref[a:b]) <= TOL, (i, Ls[i])
+
+
+@pytest.mark.parametrize("algo", ["hybridRCM", "hybridCS"])
+def test_batched_equals_single_calls(hd, algo):
+    Ls = np.array([700, 4096, 9999, 33333, 70000], dtype=np.int64)
+    off, f, g = flat(Ls, 42)
+    tf, tg = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    hb = hd.BatchPlan(off, Ls, algo=algo)(tf, tg).cpu().numpy()
+    for i in range(len(Ls)):
+        a, b = off[i], off[i] + Ls[i]
+        hs = hd.conv(tf[a:b].contiguous(), tg[a:b].contiguous(), algo=algo).cpu().numpy()
+        ref = oracle.fft_conv(f[a:b].astype(np.float64), g[a:b].astype(np.float64))
+        assert rel_l2(hb[a:b], ref) <= TOL
+        assert rel_l2(hs, ref) <= TOL
+
+
+def test_batched_full_workload_sampled(hd):
+    """The benchmark's configuration (4096 items, L ~ U{500..70000}), sampled items."""
+    off, Ls = inputs.batch_lengths(4096, 500, 70000, seed=2)
+    f, g = inputs.batch_values(int(Ls.sum()), seed=3)
+    plan = hd.BatchPlan(off, Ls, algo="hybridRCM")
+    h = plan(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    hh = h.cpu().numpy()
+    for i in [0, 1, 777, 2048, 3000, 4095] + list(np.argsort(Ls)[[0, -1]]):
+        a, b = off[i], off[i] + Ls[i]
+        ref = oracle.fft_conv(f[a:b].astype(np.float64), g[a:b].astype(np.float64))
+        assert rel_l2(hh[a:b], ref) <= TOL, (i, Ls[i])
+    # untouched gaps: nothing outside the items (there are none here) and no NaN
+    assert np.isfinite(hh).all()

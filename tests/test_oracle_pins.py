@@ -332,3 +332,20 @@ def test_planted_dropped_q2_term_is_caught(monkeypatch):
 
     monkeypatch.setattr(steps, "cs_backward", bad)
     assert rel_l2(steps.conv_hybrid_cs(f, g, 6, 4), ref) > 1e-3
+
+
+def test_direct_points_match_full_and_closed_form():
+    rng = np.random.default_rng(28)
+    for shape in [(40,), (9, 11), (5, 6, 7)]:
+        f, g = rng.normal(size=shape), rng.normal(size=shape)
+        full = oracle.direct_conv(f, g)
+        pts = np.stack([rng.integers(0, n, 25) for n in shape], axis=1)
+        assert np.allclose(oracle.direct_conv_points(f, g, pts), full[tuple(pts.T)], rtol=0, atol=1e-12)
+    # separable geometric inputs at a large 3D size: closed form at sampled points
+    L = 64
+    a, b = (0.99, 0.995, 0.98), (-0.97, 0.96, -0.99)
+    f = np.einsum("i,j,k->ijk", *[a[i] ** np.arange(L) for i in range(3)])
+    g = np.einsum("i,j,k->ijk", *[b[i] ** np.arange(L) for i in range(3)])
+    pts = np.stack([rng.integers(0, L, 20) for _ in range(3)], axis=1)
+    ref = np.prod([_geom_1d(a[i], b[i], L)[pts[:, i]] for i in range(3)], axis=0)
+    assert np.allclose(oracle.direct_conv_points(f, g, pts), ref, rtol=1e-11, atol=0)
