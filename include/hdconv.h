@@ -118,6 +118,25 @@ hd_status hd_conv_adjoint(hd_ctx* ctx, hd_algo algo, int ndim, const int64_t* Ls
  * (HD_HYBRID_RCM reports packed lengths). */
 hd_status hd_plan(hd_ctx* ctx, hd_algo algo, int64_t L, hd_dim_params* out);
 
+/* hybridRCM in 1D without any device allocation (no counterpart in the paper).
+ * For callers that may not allocate: code running under an external memory
+ * budget or allocator, loops that must not block (cudaMalloc / cudaFree can
+ * synchronise the device), or hosts calling from a context where allocation
+ * is forbidden.  Same arguments and results as hd_conv1d(HD_HYBRID_RCM, FP32)
+ * except that it takes no context and always runs the one-CTA kernel with its
+ * accumulator in global memory.  Scratch (the twiddle table and the
+ * accumulator, 6.06 MB) is a file-scope device array that every GPU loading
+ * the library holds until the process exits.  Limits: 1 <= L <= 524288, the
+ * DFT length m <= 4096 and q m <= 532480; larger requests return
+ * HD_EUNSUPPORTED.  Runs on the current device and `stream`.  The first call
+ * on a device looks up the array's device address (set-up, no allocation):
+ * make that first call before any stream capture.  All calls share the one
+ * array, so calls that overlap on the GPU (different streams, or concurrent
+ * host threads) race and give wrong results: serialise them.  Each call
+ * rewrites the table and zeroes the accumulator before use. */
+hd_status hd_conv1d_rcm_noalloc(const float* f, const float* g, float* h, int64_t L, const hd_dim_params* prm,
+                                void* stream);
+
 /* Status of device-side checks since the last call (bounded waits that gave
  * up report HD_ETIMEOUT); reading it synchronises the context's device and
  * clears the word. */

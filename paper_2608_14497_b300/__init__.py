@@ -26,7 +26,7 @@ PRECS = {"fp32": HD_FP32, "split_bf16": HD_SPLIT_BF16}
 # Every symbol include/hdconv.h declares.
 EXPORTS = ("hd_create", "hd_destroy", "hd_conv1d", "hd_conv2d", "hd_conv3d", "hd_batch_plan_create",
            "hd_batch_plan_destroy", "hd_conv1d_batched", "hd_conv_adjoint", "hd_plan", "hd_last_device_error",
-           "hd_strerror", "hd_last_error_string")
+           "hd_strerror", "hd_last_error_string", "hd_conv1d_rcm_noalloc")
 
 
 class HDError(RuntimeError):
@@ -71,6 +71,7 @@ def load(build_if_missing=False):
         "hd_last_device_error": ([P], I),
         "hd_strerror": ([I], ctypes.c_char_p),
         "hd_last_error_string": ([], ctypes.c_char_p),
+        "hd_conv1d_rcm_noalloc": ([P, P, P, I64, DP, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -145,6 +146,11 @@ def hd_conv1d_batched(ctx, plan, f_ptr, g_ptr, h_ptr, stream=0):
 def hd_conv_adjoint(ctx, algo, Ls, batch, gh_ptr, f_ptr, g_ptr, gf_ptr, gg_ptr, stream=0):
     arr = (ctypes.c_int64 * len(Ls))(*[int(x) for x in Ls])
     return load().hd_conv_adjoint(ctx, algo, len(Ls), arr, batch, gh_ptr, f_ptr, g_ptr, gf_ptr, gg_ptr, stream)
+
+
+def hd_conv1d_rcm_noalloc(f_ptr, g_ptr, h_ptr, L, prm=None, stream=0):
+    """hybridRCM 1D with no device allocation (scratch in a static device array)."""
+    return load().hd_conv1d_rcm_noalloc(f_ptr, g_ptr, h_ptr, L, _params(prm, 1), stream)
 
 
 def hd_last_device_error(ctx):

@@ -104,3 +104,14 @@ hd_status ensure_ws(hd_ctx* c, size_t bytes) {
 }
 
 }  // namespace hd
+
+namespace hd {
+// Fill tw[0..N) with zeta_N^k on `st` (the same FP64 evaluation as the cache).
+cudaError_t launch_roots_fp64(float2* tw, int64_t N, cudaStream_t st) {
+  int threads = 256;
+  int64_t blocks64 = (N + threads - 1) / threads;
+  int blocks = (int)(blocks64 < 4096 ? blocks64 : 4096);
+  k_roots_fp64<<<blocks, threads, 0, st>>>(tw, N);
+  return cudaGetLastError();
+}
+}  // namespace hd
