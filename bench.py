@@ -316,6 +316,8 @@ def run_gpu(args):
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
+    if args.compare:
+        line["comparisons"] = compare_suite()
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -324,6 +326,61 @@ def run_gpu(args):
 
 def plan_launches(plan):
     return 1
+
+
+def compare_suite(reps=10):
+    """Same-GPU comparison of the four algorithms on the paper-shaped configs
+    (1D L=4096, 2D L in {1024, 2048, 3000}, 3D L in {256, 384}) and the
+    differentiable 2D workload (batch 16 of 1024^2, forward + adjoint): median
+    of `reps` CUDA-event timings per call after warm-up, inputs resident in HBM.
+    Arrays smaller than L2 are timed L2-warm (noted per entry)."""
+    import torch
+    import paper_2608_14497_b300 as hd
+    from paper_2608_14497_b300 import inputs
+    out = {}
+
+    def time_call(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    cases = [("1D L=4096", (4096,), 1), ("2D L=1024", (1024, 1024), 4), ("2D L=2048", (2048, 2048), 4),
+             ("2D L=3000", (3000, 3000), 4), ("3D L=256", (256, 256, 256), 5), ("3D L=384", (384, 384, 384), 5)]
+    for name, shape, seed in cases:
+        f, g = (inputs.uniform_pair if len(shape) < 3 else inputs.normal_pair)(shape, seed)
+        tf, tg = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+        h = torch.empty_like(tf)
+        row = {"l2": "warm" if 12 * f.size < 126e6 else "cold (> L2)"}
+        for algo in ("hybridRCM", "hybridCS", "explicitRCM", "explicit"):
+            try:
+                ms = time_call(lambda: hd.conv(tf, tg, algo=algo, out=h))
+                row[algo] = {"ms": ms, "conv_per_s": 1e3 / ms, "GBps_12B": 12 * f.size / (ms * 1e-3) / 1e9}
+            except Exception as e:  # unsupported size for an algorithm
+                row[algo] = {"error": str(e)[:80]}
+        out[name] = row
+        del tf, tg, h
+        torch.cuda.empty_cache()
+    f, g = inputs.uniform_pair((16, 1024, 1024), 6)
+    tf = torch.from_numpy(f).cuda().requires_grad_(True)
+    tg = torch.from_numpy(g).cuda().requires_grad_(True)
+    u = torch.randn_like(tf)
+
+    def fwd_bwd():
+        tf.grad = None
+        tg.grad = None
+        hd.hd_conv_fn(tf, tg, "hybridRCM").backward(u)
+
+    out["2D adjoint batch16 L=1024 (fwd+bwd)"] = {"ms": time_call(fwd_bwd)}
+    return out
 
 
 def main():
@@ -336,6 +393,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--compare", action="store_true",
+                    help="add same-GPU timings of all algorithms on the 1D/2D/3D configs")
     ap.add_argument("--items", type=int, default=N_ITEMS,
                     help="batch size; smaller batches are for profiling captures, not for the reported line")
     args = ap.parse_args()

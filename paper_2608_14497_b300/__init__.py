@@ -201,6 +201,75 @@ def conv(f, g, algo="hybridRCM", params=None, out=None, prec="fp32"):
     return h
 
 
+def conv_batch(f, g, ndim, algo="hybridRCM", out=None):
+    """Independent convolutions of f[b] with g[b] over a leading batch dimension."""
+    import torch
+    _check_tensor(f, "f")
+    _check_tensor(g, "g")
+    if f.shape != g.shape or f.dim() != ndim + 1:
+        raise ValueError("f and g must be (batch, *extents) with matching shapes")
+    h = torch.empty_like(f) if out is None else out
+    ctx = context(f.device.index)
+    a = ALGOS[algo]
+    n = f[0].numel() * 4
+    L = tuple(f.shape[1:])
+    fn = {1: hd_conv1d, 2: hd_conv2d, 3: hd_conv3d}[ndim]
+    for b in range(f.shape[0]):
+        st = fn(ctx, a, HD_FP32, f.data_ptr() + b * n, g.data_ptr() + b * n, h.data_ptr() + b * n, *L,
+                None, _stream_ptr())
+        _check(st, "conv_batch")
+    return h
+
+
+def adjoint(grad_h, f, g, algo="hybridRCM", need_f=True, need_g=True):
+    """(grad_f, grad_g) of h = conv(f, g) for a batch (leading dimension)."""
+    import torch
+    for t, nme in ((grad_h, "grad_h"), (f, "f"), (g, "g")):
+        _check_tensor(t, nme)
+    gf = torch.empty_like(f) if need_f else None
+    gg = torch.empty_like(g) if need_g else None
+    ctx = context(f.device.index)
+    Ls = tuple(f.shape[1:])
+    st = hd_conv_adjoint(ctx, ALGOS[algo], Ls, f.shape[0], grad_h.data_ptr(), f.data_ptr(), g.data_ptr(),
+                         gf.data_ptr() if gf is not None else None, gg.data_ptr() if gg is not None else None,
+                         _stream_ptr())
+    _check(st, "adjoint")
+    return gf, gg
+
+
+def _autograd_fn():
+    import torch
+
+    class HDConvFn(torch.autograd.Function):
+        """h = conv(f, g) over a leading batch dimension; the backward pass runs
+        the adjoint kernels (spectra are recomputed, nothing is stored)."""
+
+        @staticmethod
+        def forward(ctx, f, g, algo="hybridRCM"):
+            ctx.save_for_backward(f, g)
+            ctx.algo = algo
+            return conv_batch(f.contiguous(), g.contiguous(), f.dim() - 1, algo)
+
+        @staticmethod
+        def backward(ctx, grad_h):
+            f, g = ctx.saved_tensors
+            gf, gg = adjoint(grad_h.contiguous(), f, g, ctx.algo, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+            return gf, gg, None
+
+    return HDConvFn
+
+
+_HDConvFn = None
+
+
+def hd_conv_fn(f, g, algo="hybridRCM"):
+    """Differentiable batched convolution (torch.autograd.Function HDConvFn)."""
+    global _HDConvFn
+    if _HDConvFn is None:
+        _HDConvFn = _autograd_fn()
+    return _HDConvFn.apply(f, g, algo)
+
+
 class BatchPlan:
     """Host-built plan of many 1D convolutions of uneven lengths on flat arrays."""
 

@@ -125,6 +125,8 @@ static hd_status conv1d_rcm_cluster(hd_ctx* c, const float* f, const float* g, f
   cl.one_item.p = p;
   cl.one_item.C = C;
   cl.one_item.tw = tw;
+  cl.one_item.tabm = c->tables.get_pass_table(m, st, &terr);
+  if (!cl.one_item.tabm) return fail(terr, "pass table allocation failed");
   factor_radices(m, &cl.one_plan);
   cudaError_t e = launch_rcm1d_cluster(cl, 1, cluster_smem_bytes(m), f, g, h, st);
   if (e != cudaSuccess) return cuda_fail(e, "cluster launch");
@@ -216,6 +218,7 @@ hd_status hd_destroy(hd_ctx* c) {
   cudaDeviceSynchronize();
   c->tables.clear();
   if (c->ws) cudaFree(c->ws);
+  if (c->ws2) cudaFree(c->ws2);
   if (c->dev_err) cudaFree(c->dev_err);
   delete c;
   return HD_OK;

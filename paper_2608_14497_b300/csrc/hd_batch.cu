@@ -91,6 +91,8 @@ extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, co
       ci.C = C;
       ci.plan = plan_index(m);
       ci.tw = tw;
+      ci.tabm = c->tables.get_pass_table(m, 0, &terr);
+      if (!ci.tabm) return terr;
       citems.push_back(ci);
       in_cluster[i] = 1;
       m_max = std::max(m_max, m);

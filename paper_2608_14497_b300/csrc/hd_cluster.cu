@@ -67,13 +67,12 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
   if (active) it = cl.items ? cl.items[u.first + sub] : cl.one_item;
   const int m = active ? it.m : 1;
   const int q = 2 * C, N = q * m;
-  const int Pm = pad_stride(m);
-  float2* twn = sm;                          // zeta_m^k, k < m
-  float2* arr = sm + ((m + 1) & ~1);         // F_a, F_b, G_a, G_b (stride Pm)
-  if (active) {
-    for (int k = tid; k < m; k += T) twn[k] = __ldg(it.tw + (size_t)k * q);
-  }
-  // every CTA of the cluster is running and has its tables before any
+  const int Sm = swz_stride(m);
+  float2* tws = sm;                 // per-pass twiddles of the length-m DFT (m - 1 entries)
+  float2* arr = sm + swz_stride(m);  // F_a, F_b, G_a, G_b, each Sm long, swizzled
+  const float2* __restrict__ tw = active ? it.tw : nullptr;  // zeta_N^k
+  if (active) fill_pass_twiddles(tws, m, it.tabm);
+  // every CTA of the cluster is running (and has its table) before any
   // distributed-shared-memory traffic
   cluster.sync();
 
@@ -83,13 +82,35 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
   const int chunk = (m + C - 1) / C;
   const int s0 = c * chunk, s1 = min(m, s0 + chunk);
   const int rank0 = sub * C;
-  const float2* __restrict__ tw = active ? it.tw : nullptr;
+
+  // zeta_N^{r s} for r < q from two table reads: zeta_N^{4a + b} s = w4^a w1^b
+  auto residue_twiddles = [&](int s, float2* wr) {
+    const float2 w1 = __ldg(tw + s);
+    float2 p1[4], p4[4];
+    p1[0] = make_float2(1.f, 0.f);
+    p1[1] = w1;
+    p1[2] = cmul(w1, w1);
+    p1[3] = cmul(p1[2], w1);
+    p4[0] = p1[0];
+    if (q > 4) {
+      const float2 w4 = __ldg(tw + 4 * s);
+      p4[1] = w4;
+      p4[2] = cmul(w4, w4);
+      p4[3] = cmul(p4[2], w4);
+    } else {
+      p4[1] = p4[2] = p4[3] = p1[0];
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) wr[r] = (r < 4) ? p1[r] : cmul(p4[r >> 2], p1[r & 3]);
+  };
 
   // ---- phase 1: Eq. forwardr, sum over t and the pre-twiddle, scattered to owners
   if (active) {
-    for (int which = 0; which < 2; ++which) {
-      const float* x = (which ? g : f) + it.off;
-      for (int s = s0 + tid; s < s1; s += T) {
+    for (int s = s0 + tid; s < s1; s += T) {
+      float2 wr[16];
+      residue_twiddles(s, wr);
+      for (int which = 0; which < 2; ++which) {
+        const float* x = (which ? g : f) + it.off;
         float2 e0[8], e1[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -97,16 +118,16 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
           const int j = t * m + s;
           if (t < p && j < Lp) v = make_float2(x[2 * j], (2 * j + 1 < L) ? x[2 * j + 1] : 0.f);
           e0[t] = v;
-          e1[t] = (t < C) ? cmul(v, __ldg(tw + (size_t)t * m)) : v;  // zeta_q^t x_t
+          e1[t] = (t < C && t > 0) ? cmul(v, __ldg(tw + (size_t)t * m)) : v;  // zeta_q^t x_t
         }
         dft_small<1>(e0, C);
         dft_small<1>(e1, C);
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
           if (r < q) {
-            const float2 y = cmul((r & 1) ? e1[r >> 1] : e0[r >> 1], __ldg(tw + r * s));
+            const float2 y = cmul((r & 1) ? e1[r >> 1] : e0[r >> 1], wr[r]);
             float2* dst = cluster.map_shared_rank(arr, rank0 + res_owner(r, C));
-            dst[(which * 2 + res_slot(r, C)) * Pm + pad16(s)] = y;
+            dst[(which * 2 + res_slot(r, C)) * Sm + swz(s)] = y;
           }
         }
       }
@@ -117,46 +138,48 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
   // ---- phase 2: DFTs of the owned residues, RCM product, backward DFTs
   if (active) {
     if (4 * m <= kClusterPts * T) {
-      cta_fft_fast<1, kClusterPts>(arr, Pm, 4, m, twn);
+      cta_fft_fast<1, kClusterPts>(arr, Sm, 4, m, tws);
     } else {
-      cta_fft_fast<1, kClusterPts>(arr, Pm, 2, m, twn);
-      cta_fft_fast<1, kClusterPts>(arr + 2 * Pm, Pm, 2, m, twn);
+      cta_fft_fast<1, kClusterPts>(arr, Sm, 2, m, tws);
+      cta_fft_fast<1, kClusterPts>(arr + 2 * Sm, Sm, 2, m, tws);
     }
     float2* Fa = arr;
-    float2* Fb = arr + Pm;
-    float2* Ga = arr + 2 * Pm;
-    float2* Gb = arr + 3 * Pm;
-    if (c == 0) {
-      // residues 0 (l* = (m - l) mod m) and C = q/2 (l* = m - 1 - l), each self-paired
-      for (int idx = tid; idx < 2 * m; idx += T) {
-        const int slot = idx >= m ? 1 : 0;
-        const int l = idx - slot * m;
-        const int r = slot ? C : 0;
-        const int ls = slot ? (m - 1 - l) : (l == 0 ? 0 : m - l);
+    float2* Fb = arr + Sm;
+    float2* Ga = arr + 2 * Sm;
+    float2* Gb = arr + 3 * Sm;
+    // c = 0: residues 0 (l* = (m - l) mod m) and C = q/2 (l* = m - 1 - l), each
+    // self-paired; c > 0: residue c (l) with residue q - c (l* = m - 1 - l)
+    const int npairs = (c == 0) ? 2 * m : m;
+    for (int idx = tid; idx < npairs; idx += T) {
+      const int slot = idx >= m ? 1 : 0;
+      const int l = idx - slot * m;
+      int r, ls;
+      float2 *Fl, *Gl, *Fs, *Gs;
+      if (c == 0) {
+        r = slot ? C : 0;
+        ls = slot ? (m - 1 - l) : (l == 0 ? 0 : m - l);
         if (l > ls) continue;
-        float2* F = slot ? Fb : Fa;
-        float2* G = slot ? Gb : Ga;
-        const float2 A = F[pad16(l)], B = G[pad16(l)], Ac = F[pad16(ls)], Bc = G[pad16(ls)];
-        const float2 z = __ldg(tw + q * l + r);
-        const float2 Z = make_float2(0.25f * (1.f + z.x), 0.25f * z.y);
-        const float2 alpha = cmul(cmul(csub(A, cconj(Ac)), csub(B, cconj(Bc))), Z);
-        F[pad16(l)] = csub(cmul(A, B), alpha);
-        if (ls != l) F[pad16(ls)] = csub(cmul(Ac, Bc), cconj(alpha));
+        Fl = Fs = slot ? Fb : Fa;
+        Gl = Gs = slot ? Gb : Ga;
+      } else {
+        r = c;
+        ls = m - 1 - l;
+        Fl = Fa;
+        Gl = Ga;
+        Fs = Fb;
+        Gs = Gb;
       }
-    } else {
-      const int ra = c;
-      for (int l = tid; l < m; l += T) {
-        const int ls = m - 1 - l;
-        const float2 A = Fa[pad16(l)], B = Ga[pad16(l)], Ac = Fb[pad16(ls)], Bc = Gb[pad16(ls)];
-        const float2 z = __ldg(tw + q * l + ra);
-        const float2 Z = make_float2(0.25f * (1.f + z.x), 0.25f * z.y);
-        const float2 alpha = cmul(cmul(csub(A, cconj(Ac)), csub(B, cconj(Bc))), Z);
-        Fa[pad16(l)] = csub(cmul(A, B), alpha);
-        Fb[pad16(ls)] = csub(cmul(Ac, Bc), cconj(alpha));
-      }
+      const int il = swz(l), is = swz(ls);
+      const float2 A = Fl[il], B = Gl[il], Ac = Fs[is], Bc = Gs[is];
+      // zeta_N^{q l + r} = zeta_m^l zeta_N^r
+      const float2 z = cmul(__ldg(it.tabm + (m - 1) + l), __ldg(tw + r));
+      const float2 Z = make_float2(0.25f * (1.f + z.x), 0.25f * z.y);  // (1 + zeta_N^k) / 4
+      const float2 alpha = cmul(cmul(csub(A, cconj(Ac)), csub(B, cconj(Bc))), Z);
+      Fl[il] = csub(cmul(A, B), alpha);
+      if (!(c == 0 && ls == l)) Fs[is] = csub(cmul(Ac, Bc), cconj(alpha));
     }
     __syncthreads();
-    cta_fft_fast<-1, kClusterPts>(arr, Pm, 2, m, twn);
+    cta_fft_fast<-1, kClusterPts>(arr, Sm, 2, m, tws);
   }
   cluster.sync();
 
@@ -165,12 +188,14 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
     const float sc = 1.0f / (float)N;
     float* hi = h + it.off;
     for (int s = s0 + tid; s < s1; s += T) {
+      float2 wr[16];
+      residue_twiddles(s, wr);
       float2 e0[8], e1[8];
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
         if (r < q) {
           const float2* src = cluster.map_shared_rank(arr, rank0 + res_owner(r, C));
-          const float2 w = cmul(src[res_slot(r, C) * Pm + pad16(s)], cconj(__ldg(tw + r * s)));
+          const float2 w = cmul(src[res_slot(r, C) * Sm + swz(s)], cconj(wr[r]));
           if (r & 1) e1[r >> 1] = w;
           else e0[r >> 1] = w;
         }
@@ -181,7 +206,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
       for (int t = 0; t < 8; ++t) {
         const int j = t * m + s;
         if (t < p && j < Lp) {
-          const float2 o = cadd(e0[t], cmul(e1[t], cconj(__ldg(tw + (size_t)t * m))));
+          const float2 o = (t > 0) ? cadd(e0[t], cmul(e1[t], cconj(__ldg(tw + (size_t)t * m)))) : cadd(e0[0], e1[0]);
           hi[2 * j] = o.x * sc;
           if (2 * j + 1 < L) hi[2 * j + 1] = o.y * sc;
         }
@@ -225,9 +250,7 @@ bool cluster_params(int64_t L, int* C_out, int* m_out, int* p_out) {
   return false;
 }
 
-size_t cluster_smem_bytes(int m_max) {
-  return sizeof(float2) * ((size_t)((m_max + 1) & ~1) + 4 * (size_t)pad_stride(m_max));
-}
+size_t cluster_smem_bytes(int m_max) { return sizeof(float2) * 5 * (size_t)swz_stride(m_max); }
 
 cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int nunits, size_t smem, const float* f, const float* g,
                                  float* h, cudaStream_t st) {

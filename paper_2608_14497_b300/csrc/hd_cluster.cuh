@@ -9,7 +9,7 @@ namespace hd {
 
 constexpr int kClusterCtas = 8;       // CTAs per cluster
 constexpr int kClusterThreads = 512;  // threads per CTA
-constexpr int kClusterPts = 32;       // FFT points per thread per pass
+constexpr int kClusterPts = 24;       // FFT points per thread per pass
 constexpr int kClusterMaxM = 4608;    // largest residue DFT length (shared memory)
 
 // One convolution: q = 2C residues of length m, p = ceil(Lp/m) <= C.
@@ -18,7 +18,8 @@ struct CItem {
   int32_t L, m, p, C;
   int32_t plan;
   int32_t pad_;
-  const float2* tw;  // zeta_N^k, N = 2 C m
+  const float2* tw;    // zeta_N^k, N = 2 C m
+  const float2* tabm;  // per-length table: pass twiddles, then zeta_m^l (hd_fft_fast.cuh)
 };
 
 // A cluster's work: `count` (<= 8/C) consecutive items starting at `first`.

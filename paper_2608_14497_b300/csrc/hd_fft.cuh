@@ -145,6 +145,35 @@ __device__ __forceinline__ void dft16(float2* a) {
   }
 }
 
+// 9 points as 3 x 3: inner length-3 DFTs over n2 (n = n1 + 3 n2), twiddles
+// zeta_9^{n1 k2}, outer length-3 DFTs over n1; output k = 3 k1 + k2.
+template <int SIGN>
+__device__ __forceinline__ void dft9(float2* a) {
+  const float c1 = 0.76604444311897803520f, s1 = 0.64278760968653932632f;   // zeta_9^1
+  const float c2 = 0.17364817766693034885f, s2 = 0.98480775301220805936f;   // zeta_9^2
+  const float c4 = -0.93969262078590838405f, s4 = 0.34202014332566873304f;  // zeta_9^4
+  float2 y[3][3];
+#pragma unroll
+  for (int n1 = 0; n1 < 3; ++n1) {
+    y[n1][0] = a[n1];
+    y[n1][1] = a[n1 + 3];
+    y[n1][2] = a[n1 + 6];
+    dft3<SIGN>(y[n1][0], y[n1][1], y[n1][2]);
+  }
+  y[1][1] = cmul(y[1][1], make_float2(c1, SIGN * s1));
+  y[1][2] = cmul(y[1][2], make_float2(c2, SIGN * s2));
+  y[2][1] = cmul(y[2][1], make_float2(c2, SIGN * s2));
+  y[2][2] = cmul(y[2][2], make_float2(c4, SIGN * s4));
+#pragma unroll
+  for (int k2 = 0; k2 < 3; ++k2) {
+    float2 z0 = y[0][k2], z1 = y[1][k2], z2 = y[2][k2];
+    dft3<SIGN>(z0, z1, z2);
+    a[k2] = z0;
+    a[3 + k2] = z1;
+    a[6 + k2] = z2;
+  }
+}
+
 template <int R, int SIGN>
 __device__ __forceinline__ void dft_reg(float2* v) {
   if constexpr (R == 2) dft2<SIGN>(v[0], v[1]);
@@ -152,6 +181,7 @@ __device__ __forceinline__ void dft_reg(float2* v) {
   else if constexpr (R == 4) dft4<SIGN>(v[0], v[1], v[2], v[3]);
   else if constexpr (R == 5) dft5<SIGN>(v[0], v[1], v[2], v[3], v[4]);
   else if constexpr (R == 8) dft8<SIGN>(v);
+  else if constexpr (R == 9) dft9<SIGN>(v);
   else if constexpr (R == 16) dft16<SIGN>(v);
 }
 

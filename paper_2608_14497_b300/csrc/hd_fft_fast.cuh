@@ -3,21 +3,25 @@
 //
 // Same arithmetic as hd_fft.cuh (Sec. 2 sign convention, radix-2/3/4/5/8/16
 // butterflies), specialised for speed:
-//   * shared-memory arrays use a padded layout, element i at i + i/16, so the
-//     strided stores of the first passes (stride R elements) hit distinct
-//     banks;
-//   * the twiddles of the length-n DFT come from a table zeta_n^k in shared
-//     memory (k < n);
-//   * index splits use a float reciprocal with one integer correction instead
-//     of integer division (exact for the index range used, < 2^17).
+//   * element i of an array is stored at swz(i) = i ^ ((i >> 4) & 15) from the
+//     array's start (arrays start on 16-element boundaries): a permutation
+//     inside each aligned block of 16 float2 (128 bytes), so contiguous runs
+//     stay in one 128-byte row and the stride-R stores of the first passes land
+//     in distinct banks;
+//   * twiddles come from a per-pass table in shared memory: pass (R, Ns) reads
+//     zeta_{Ns R}^{r jm} at tws[(Ns - 1) + (r - 1) Ns + jm] (r = 1..R-1, jm < Ns),
+//     contiguous in jm; the passes' offsets telescope to a total of n - 1;
+//   * index splits use a float reciprocal with one integer correction (exact
+//     below 2^17) instead of integer division (recomputed after the barrier:
+//     keeping the addresses in registers costs more than the few instructions).
 #pragma once
 #include "hd_fft.cuh"
 
 namespace hd {
 
-__host__ __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
-// padded stride of an array of n elements, rounded to an even count (16 B)
-__host__ __device__ __forceinline__ int pad_stride(int n) { return (pad16(n > 0 ? n - 1 : 0) + 2) & ~1; }
+__host__ __device__ __forceinline__ int swz(int k) { return k ^ ((k >> 4) & 15); }
+// array stride: a whole number of 16-element blocks, so swz stays inside the array
+__host__ __device__ __forceinline__ int swz_stride(int n) { return (n + 15) & ~15; }
 
 struct DivF {
   float rcp;
@@ -32,15 +36,18 @@ __device__ __forceinline__ int fdiv(int n, DivF v) {
   return q;
 }
 
+// One Stockham pass of radix R on nbuf arrays of length n at base + a*stride
+// (stride a multiple of 16, indices swizzled per array), twiddles tws (per-pass
+// table).
 template <int R, int SIGN, int PTS>
 __device__ __forceinline__ void fstage(float2* base, int stride, int nbuf, int n, int Ns,
-                                       const float2* __restrict__ twn) {
+                                       const float2* __restrict__ tws) {
   constexpr int BPT = (PTS + R - 1) / R;
   const int nb = n / R;
   const DivF dnb = make_div(nb), dNs = make_div(Ns);
   const int total = nb * nbuf;
   const int T = blockDim.x;
-  const int twstep = n / (Ns * R);
+  const float2* tw_pass = tws + (Ns - 1);
   float2 v[BPT][R];
 #pragma unroll
   for (int b = 0; b < BPT; ++b) {
@@ -51,12 +58,11 @@ __device__ __forceinline__ void fstage(float2* base, int stride, int nbuf, int n
       const int jm = j - fdiv(j, dNs) * Ns;
       const float2* x = base + a * stride;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = x[pad16(j + r * nb)];
+      for (int r = 0; r < R; ++r) v[b][r] = x[swz(j + r * nb)];
       if (Ns > 1) {
-        const int e = jm * twstep;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          float2 w = twn[r * e];
+          float2 w = tw_pass[(r - 1) * Ns + jm];
           if (SIGN < 0) w.y = -w.y;
           v[b][r] = cmul(v[b][r], w);
         }
@@ -71,53 +77,73 @@ __device__ __forceinline__ void fstage(float2* base, int stride, int nbuf, int n
       const int a = fdiv(idx, dnb);
       const int j = idx - a * nb;
       const int jm = j - fdiv(j, dNs) * Ns;
-      float2* y = base + a * stride;
       dft_reg<R, SIGN>(v[b]);
+      float2* y = base + a * stride;
       const int o = (j - jm) * R + jm;
 #pragma unroll
-      for (int r = 0; r < R; ++r) y[pad16(o + r * Ns)] = v[b][r];
+      for (int r = 0; r < R; ++r) y[swz(o + r * Ns)] = v[b][r];
     }
   }
   __syncthreads();
 }
 
-// Whole DFT of length n = odd * 2^a, odd in {1, 3, 5, 9}, on nbuf padded
-// arrays (base + a * stride), in place; twn[k] = zeta_n^k in shared memory.
-// Passes: radix 16 while 16 divides the power of two, one radix-8/4/2 pass for
-// the rest of it, then radix 3, 3 x 3 or 5.  (A loop over a runtime radix
-// table makes the register allocator spill; this fixed sequence does not.)
+// Pass radices of a length n = odd * 2^a, odd in {1, 3, 5, 9}, in the order
+// cta_fft_fast runs them: radix 16 while 16 divides the power of two, one
+// radix-8/4/2 pass for the rest of it, then one radix-3/5/9 pass.
+__host__ __device__ __forceinline__ int fast_passes(int n, int* Rs) {
+  int a2 = 0;
+  while (a2 < 30 && ((n >> a2) & 1) == 0) ++a2;
+  const int odd = n >> a2;
+  int k = 0;
+  for (int i = 0; i < (a2 >> 2); ++i) Rs[k++] = 16;
+  if (a2 & 3) Rs[k++] = 1 << (a2 & 3);
+  if (odd > 1) Rs[k++] = odd;
+  return k;
+}
+
+// Per-length table (built once per length, FP64 on the device, see
+// hd_tables_plan.cu): entries [0, n-1) are the per-pass twiddles
+// zeta_{Ns R}^{r jm} at (Ns - 1) + (r - 1) Ns + jm; entries [n-1, 2n-1) are
+// zeta_n^l.  Copy the first part into shared memory (coalesced; no barrier).
+__device__ __forceinline__ void fill_pass_twiddles(float2* tws, int n, const float2* __restrict__ tabm) {
+  for (int i = threadIdx.x; i < n - 1; i += blockDim.x) tws[i] = __ldg(tabm + i);
+}
+
+// Whole DFT of length n on nbuf arrays (base + a * stride, swizzled), in place,
+// passes as fast_passes lists them.  (A loop over a runtime radix table
+// makes the register allocator spill; this fixed sequence does not.)
 // Requires nbuf * n <= PTS * T.
 template <int SIGN, int PTS>
 __device__ __forceinline__ void cta_fft_fast(float2* base, int stride, int nbuf, int n,
-                                             const float2* __restrict__ twn) {
-  const int a2 = __ffs(n) - 1;  // power of two in n
+                                             const float2* __restrict__ tws) {
+  const int a2 = __ffs(n) - 1;
   const int odd = n >> a2;
   int Ns = 1;
   for (int i = 0; i < (a2 >> 2); ++i) {
-    fstage<16, SIGN, PTS>(base, stride, nbuf, n, Ns, twn);
+    fstage<16, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
     Ns *= 16;
   }
   const int rem = a2 & 3;
   if (rem == 3) {
-    fstage<8, SIGN, PTS>(base, stride, nbuf, n, Ns, twn);
+    fstage<8, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
     Ns *= 8;
   } else if (rem == 2) {
-    fstage<4, SIGN, PTS>(base, stride, nbuf, n, Ns, twn);
+    fstage<4, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
     Ns *= 4;
   } else if (rem == 1) {
-    fstage<2, SIGN, PTS>(base, stride, nbuf, n, Ns, twn);
+    fstage<2, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
     Ns *= 2;
   }
-  if (odd == 3 || odd == 9) {
-    fstage<3, SIGN, PTS>(base, stride, nbuf, n, Ns, twn);
+  if (odd == 3) {
+    fstage<3, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
     Ns *= 3;
   }
   if (odd == 9) {
-    fstage<3, SIGN, PTS>(base, stride, nbuf, n, Ns, twn);
-    Ns *= 3;
+    fstage<9, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
+    Ns *= 9;
   }
   if (odd == 5) {
-    fstage<5, SIGN, PTS>(base, stride, nbuf, n, Ns, twn);
+    fstage<5, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
     Ns *= 5;
   }
 }

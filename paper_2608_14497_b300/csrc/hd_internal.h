@@ -33,6 +33,7 @@ int64_t next_smooth(int64_t n);
 struct TableCache {
   std::map<int64_t, float2*> tabs;
   const float2* get(int64_t N, cudaStream_t st, hd_status* err);
+  const float2* get_pass_table(int n, cudaStream_t st, hd_status* err);
   void clear();
 };
 
@@ -44,6 +45,8 @@ struct hd_ctx {
   // reusable device scratch, grown on demand
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  void* ws2 = nullptr;  // the adjoint's reversed gradient and temporary
+  size_t ws2_bytes = 0;
   // plan/item upload buffers for single calls
   void* meta = nullptr;
   size_t meta_bytes = 0;
@@ -55,5 +58,6 @@ struct hd_ctx {
 
 namespace hd {
 hd_status ensure_ws(hd_ctx* c, size_t bytes);
+hd_status ensure_ws2(hd_ctx* c, size_t bytes);
 hd_status ensure_meta(hd_ctx* c, size_t bytes);
 }  // namespace hd

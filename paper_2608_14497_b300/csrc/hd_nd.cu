@@ -1087,8 +1087,4 @@ hd_status hd_conv3d(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, const
   const int64_t L[3] = {L1, L2, L3};
   return conv_nd(c, algo, prec, f, g, h, 3, L, prm, stream);
 }
-hd_status hd_conv_adjoint(hd_ctx*, hd_algo, int, const int64_t*, int32_t, const float*, const float*, const float*,
-                          float*, float*, void*) {
-  return HD_EUNSUPPORTED;
-}
 }

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "hd_fft_fast.cuh"
 #include "hd_internal.h"
 
 namespace hd {
@@ -23,6 +24,54 @@ __global__ void k_roots_fp64(float2* __restrict__ tw, int64_t N) {
     sincospi(x, &s, &c);
     tw[k] = make_float2((float)c, (float)s);
   }
+}
+
+// Per-length table of the cluster kernels (layout in hd_fft_fast.cuh): the
+// pass twiddles zeta_{Ns R}^{r jm} followed by zeta_n^l, each evaluated in FP64
+// from its exact rational angle and rounded once.
+__global__ void k_pass_table_fp64(float2* __restrict__ out, int n, int nps, int4 Rs0, int4 Rs1) {
+  const int Rs[8] = {Rs0.x, Rs0.y, Rs0.z, Rs0.w, Rs1.x, Rs1.y, Rs1.z, Rs1.w};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n - 1; i += gridDim.x * blockDim.x) {
+    long long num, den;
+    if (i >= n - 1) {
+      num = i - (n - 1);
+      den = n;
+    } else {
+      int Ns = 1, k = 0;
+      while (k < nps && i >= Ns - 1 + (Rs[k] - 1) * Ns) Ns *= Rs[k++];
+      const int o = i - (Ns - 1);
+      const int r = o / Ns + 1, jm = o - (r - 1) * Ns;
+      num = (long long)r * jm;
+      den = (long long)Ns * Rs[k];
+    }
+    double s, c;
+    double x = (2.0 * (double)(num % den)) / (double)den;
+    if (x > 1.0) x -= 2.0;
+    sincospi(x, &s, &c);
+    out[i] = make_float2((float)c, (float)s);
+  }
+}
+
+// Key space: padded lengths N > 0; per-length pass tables under -n.
+const float2* TableCache::get_pass_table(int n, cudaStream_t st, hd_status* err) {
+  auto it = tabs.find(-(int64_t)n);
+  if (it != tabs.end()) return it->second;
+  float2* p = nullptr;
+  if (cudaMalloc(&p, sizeof(float2) * (size_t)(2 * n)) != cudaSuccess) {
+    *err = HD_ENOMEM;
+    return nullptr;
+  }
+  int Rs[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+  const int nps = fast_passes(n, Rs);
+  k_pass_table_fp64<<<(2 * n + 255) / 256, 256, 0, st>>>(p, n, nps, make_int4(Rs[0], Rs[1], Rs[2], Rs[3]),
+                                                          make_int4(Rs[4], Rs[5], Rs[6], Rs[7]));
+  if (cudaGetLastError() != cudaSuccess) {
+    cudaFree(p);
+    *err = HD_ECUDA;
+    return nullptr;
+  }
+  tabs[-(int64_t)n] = p;
+  return p;
 }
 
 const float2* TableCache::get(int64_t N, cudaStream_t st, hd_status* err) {

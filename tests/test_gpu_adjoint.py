@@ -1,0 +1,90 @@
+"""GPU adjoint (gradients of the truncated convolution) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_14497_b300 import inputs
+from tests.conftest import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+ALGOS = ("hybridRCM", "hybridCS", "explicit", "explicitRCM")
+
+
+@pytest.fixture(scope="module")
+def hd():
+    import paper_2608_14497_b300 as m
+    m.load()
+    return m
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("shape", [(1,), (7,), (64,), (1000,), (5, 7), (33, 40), (4, 5, 6), (9, 8, 7)])
+def test_adjoint_matches_direct_correlation(hd, algo, shape):
+    rng = np.random.default_rng(70)
+    f, g, u = (rng.uniform(-1, 1, (2,) + shape).astype(np.float32) for _ in range(3))
+    gf, gg = hd.adjoint(cuda(u), cuda(f), cuda(g), algo)
+    gf, gg = gf.cpu().numpy(), gg.cpu().numpy()
+    for b in range(2):
+        assert rel_l2(gf[b], oracle.direct_corr(u[b], g[b])) <= TOL
+        assert rel_l2(gg[b], oracle.direct_corr(u[b], f[b])) <= TOL
+
+
+def test_adjoint_finite_differences_L64(hd):
+    """Central differences of the FP64 oracle's <conv(f, g), u> at L = 64."""
+    rng = np.random.default_rng(71)
+    L = 64
+    f, g, u = (rng.uniform(-1, 1, L) for _ in range(3))
+    eps = 1e-3
+    fd_f, fd_g = np.empty(L), np.empty(L)
+    for j in range(L):
+        e = np.zeros(L)
+        e[j] = eps
+        fd_f[j] = (np.sum(oracle.direct_conv(f + e, g) * u) - np.sum(oracle.direct_conv(f - e, g) * u)) / (2 * eps)
+        fd_g[j] = (np.sum(oracle.direct_conv(f, g + e) * u) - np.sum(oracle.direct_conv(f, g - e) * u)) / (2 * eps)
+    gf, gg = hd.adjoint(cuda(u[None]), cuda(f[None]), cuda(g[None]), "hybridRCM")
+    assert rel_l2(gf.cpu().numpy()[0], fd_f) <= TOL
+    assert rel_l2(gg.cpu().numpy()[0], fd_g) <= TOL
+
+
+def test_autograd_function_dot_product(hd):
+    """torch.autograd through HDConvFn: <conv(f,g), u> = <f, grad_f> = <g, grad_g> (FP64 oracle values)."""
+    rng = np.random.default_rng(72)
+    shape = (3, 40, 48)
+    f, g, u = (rng.uniform(-1, 1, shape).astype(np.float32) for _ in range(3))
+    tf = cuda(f).requires_grad_(True)
+    tg = cuda(g).requires_grad_(True)
+    h = hd.hd_conv_fn(tf, tg, "hybridRCM")
+    (h * cuda(u)).sum().backward()
+    for b in range(3):
+        assert rel_l2(h.detach().cpu().numpy()[b], oracle.direct_conv(f[b], g[b])) <= TOL
+        assert rel_l2(tf.grad.cpu().numpy()[b], oracle.direct_corr(u[b], g[b])) <= TOL
+        assert rel_l2(tg.grad.cpu().numpy()[b], oracle.direct_corr(u[b], f[b])) <= TOL
+
+
+def test_adjoint_batch16_1024_sampled(hd):
+    """The differentiable 2D workload: batch 16 of 1024 x 1024, sampled gradients."""
+    B, L = 16, 1024
+    f, g = inputs.uniform_pair((B, L, L), seed=6)
+    rng = np.random.default_rng(73)
+    u = rng.uniform(-1, 1, (B, L, L)).astype(np.float32)
+    tf = cuda(f).requires_grad_(True)
+    tg = cuda(g).requires_grad_(True)
+    h = hd.hd_conv_fn(tf, tg, "hybridRCM")
+    h.backward(cuda(u))
+    gfa, gga = tf.grad.cpu().numpy(), tg.grad.cpu().numpy()
+    for b in (0, 7, 15):
+        pts = np.stack([rng.integers(0, L, 40), rng.integers(0, L, 40)], axis=1)
+        rpts = (L - 1) - pts
+        ur = u[b][::-1, ::-1]
+        ref_f = oracle.direct_conv_points(ur.astype(np.float64), g[b].astype(np.float64), rpts)
+        ref_g = oracle.direct_conv_points(ur.astype(np.float64), f[b].astype(np.float64), rpts)
+        got_f = gfa[b][tuple(pts.T)]
+        got_g = gga[b][tuple(pts.T)]
+        assert np.linalg.norm(got_f - ref_f) / np.linalg.norm(ref_f) <= TOL
+        assert np.linalg.norm(got_g - ref_g) / np.linalg.norm(ref_g) <= TOL
