@@ -15,6 +15,7 @@
 // generated in FP64 and rounded once to FP32; a length-n DFT with n | N reads
 // zeta_n^x = tw[x * (N / n)].
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -280,9 +281,164 @@ __device__ __forceinline__ void fft_stage_generic(float2* base, int stride, int 
   __syncthreads();
 }
 
-// Whole DFT of length pl.n on nbuf arrays (base + a * stride), in place.
-// Ends with a barrier; the caller must have synchronised before the call.
+
+// ---------------------------------------------------------------------------
+// Split-precision radix-16 pass on tensor cores.
+//
+// The 16-point butterflies of a pass are a matrix product: with X the
+// (butterflies x 16) matrix of twiddled inputs and W_kr = zeta_16^{SIGN r k},
+// Y = X W.  In real form, [Re X, Im X] (16 x 32) times
+//   B = [[Re W, Im W], [-Im W, Re W]]  (32 x 32)
+// gives [Re Y, Im Y].  Each operand is split as x = x_hi + x_lo with
+// x_hi = bf16(x), x_lo = bf16(x - x_hi); the product is accumulated in FP32 as
+// hi*hi + hi*lo + lo*hi (the lo*lo term, ~2^-16 relative, is dropped).  One
+// warp computes 16 butterflies (one m16n8k16 row tile) with 4 column tiles x
+// 2 k-steps x 3 products = 24 mma.sync.  Fragment layouts are those of the
+// PTX m16n8k16 bf16 shape (lane = 4 g + t): A rows g, g+8, cols 2t, 2t+1,
+// 2t+8, 2t+9; B rows 2t, 2t+1, 2t+8, 2t+9, col g; C rows g, g+8, cols 2t, 2t+1.
+// In place like fft_stage: all tiles are computed into registers, a barrier,
+// then the stores.  Requires ceil(nbuf n / 256) <= 2 * (blockDim.x / 32).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ void split_bf16(float x, float& h, float& l) {
+  h = __bfloat162float(__float2bfloat16_rn(x));
+  l = x - h;
+}
+__device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// B entry (row K of 32, col c of 32) of the real-form DFT-16 matrix.
+template <int SIGN>
+__device__ __forceinline__ float dft16_real_entry(int K, int c) {
+  // cos / sin of 2 pi j / 16, j = 0..15
+  const float C16[16] = {1.0f, 0.92387953251128675613f, 0.70710678118654752440f, 0.38268343236508977173f,
+                         0.0f, -0.38268343236508977173f, -0.70710678118654752440f, -0.92387953251128675613f,
+                         -1.0f, -0.92387953251128675613f, -0.70710678118654752440f, -0.38268343236508977173f,
+                         0.0f, 0.38268343236508977173f, 0.70710678118654752440f, 0.92387953251128675613f};
+  const int r = K & 15, k = c & 15;
+  const int e = (r * k) & 15;
+  const float cr = C16[e];
+  const float si = SIGN * C16[(e + 12) & 15];  // sin(x) = cos(x - pi/2)
+  if (c < 16) return (K < 16) ? cr : -si;      // Re Y: Re W from Re X, -Im W from Im X
+  return (K < 16) ? si : cr;                   // Im Y: Im W from Re X, Re W from Im X
+}
+
 template <int SIGN, int PTS>
+__device__ __forceinline__ void fft_stage_tc16(float2* base, int stride, int nbuf, int n, int Ns,
+                                               const float2* __restrict__ tw, int twmul) {
+  constexpr int TPW = 2;
+  const int nb = n / 16;
+  const int total = nb * nbuf;
+  const int ntiles = (total + 15) >> 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int twstep = twmul * (n / (Ns * 16));
+  const int rr[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
+  // constant B fragments, hi and lo parts
+  uint32_t bh[4][2][2], bl[4][2][2];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int K0 = 16 * kk + 2 * t + 8 * hh, col = 8 * nt + g;
+        float h0, l0, h1, l1;
+        split_bf16(dft16_real_entry<SIGN>(K0, col), h0, l0);
+        split_bf16(dft16_real_entry<SIGN>(K0 + 1, col), h1, l1);
+        bh[nt][kk][hh] = pack_bf16x2(h0, h1);
+        bl[nt][kk][hh] = pack_bf16x2(l0, l1);
+      }
+  float acc[TPW][4][4];
+  int bid[TPW][2];
+#pragma unroll
+  for (int tt = 0; tt < TPW; ++tt) {
+    const int tile = warp + tt * nwarps;
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[tt][nt][e] = 0.f;
+    bid[tt][0] = bid[tt][1] = -1;
+    if (tile < ntiles) {
+      float2 xv[2][4];
+#pragma unroll
+      for (int row = 0; row < 2; ++row) {
+        const int b = tile * 16 + g + 8 * row;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xv[row][i] = make_float2(0.f, 0.f);
+        if (b < total) {
+          bid[tt][row] = b;
+          const int a = b / nb, j = b - a * nb, jm = j % Ns;
+          const float2* x = base + (size_t)a * stride;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            float2 v = x[j + rr[i] * nb];
+            if (Ns > 1 && rr[i] > 0) v = cmul(v, tw_get<SIGN>(tw, rr[i] * jm * twstep));
+            xv[row][i] = v;
+          }
+        }
+      }
+      uint32_t ah[2][4], al[2][4];
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        float h[2][4], l[2][4];
+#pragma unroll
+        for (int row = 0; row < 2; ++row)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) split_bf16(kk ? xv[row][i].y : xv[row][i].x, h[row][i], l[row][i]);
+        ah[kk][0] = pack_bf16x2(h[0][0], h[0][1]);
+        ah[kk][1] = pack_bf16x2(h[1][0], h[1][1]);
+        ah[kk][2] = pack_bf16x2(h[0][2], h[0][3]);
+        ah[kk][3] = pack_bf16x2(h[1][2], h[1][3]);
+        al[kk][0] = pack_bf16x2(l[0][0], l[0][1]);
+        al[kk][1] = pack_bf16x2(l[1][0], l[1][1]);
+        al[kk][2] = pack_bf16x2(l[0][2], l[0][3]);
+        al[kk][3] = pack_bf16x2(l[1][2], l[1][3]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          mma_bf16_16816(acc[tt][nt], ah[kk], bh[nt][kk]);
+          mma_bf16_16816(acc[tt][nt], ah[kk], bl[nt][kk]);
+          mma_bf16_16816(acc[tt][nt], al[kk], bh[nt][kk]);
+        }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int tt = 0; tt < TPW; ++tt)
+#pragma unroll
+    for (int row = 0; row < 2; ++row) {
+      const int b = bid[tt][row];
+      if (b >= 0) {
+        const int a = b / nb, j = b - a * nb, jm = j % Ns;
+        float2* y = base + (size_t)a * stride;
+        const int o = (j - jm) * 16 + jm;
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int k = 2 * t + 8 * q2 + e;
+            y[o + k * Ns] = make_float2(acc[tt][q2][2 * row + e], acc[tt][2 + q2][2 * row + e]);
+          }
+      }
+    }
+  __syncthreads();
+}
+
+// Whole DFT of length pl.n on nbuf arrays (base + a * stride), in place.
+// TC: radix-16 passes on tensor cores (split_bf16 operands, fft_stage_tc16).
+// Ends with a barrier; the caller must have synchronised before the call.
+template <int SIGN, int PTS, bool TC = false>
 __device__ __noinline__ void cta_fft(float2* base, int stride, int nbuf, const FftPlan& pl, const float2* __restrict__ tw,
                         int twmul) {
   const int n = pl.n;
@@ -295,7 +451,10 @@ __device__ __noinline__ void cta_fft(float2* base, int stride, int nbuf, const F
       case 4: fft_stage<4, SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul); break;
       case 5: fft_stage<5, SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul); break;
       case 8: fft_stage<8, SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul); break;
-      case 16: fft_stage<16, SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul); break;
+      case 16:
+        if (TC) fft_stage_tc16<SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul);
+        else fft_stage<16, SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul);
+        break;
       default: fft_stage_generic<SIGN, PTS>(base, stride, nbuf, n, R, Ns, tw, twmul); break;
     }
     Ns *= R;

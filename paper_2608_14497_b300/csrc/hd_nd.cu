@@ -71,8 +71,8 @@ enum : int { OUT_COMPLEX = 0, OUT_UNPACK_REAL = 1 };
 //      (f[j][2b], f[j][2b+1]) with real row length Lreal), Y: [A][q m][B],
 //   residue-major rows.  Eq. forwardr per column.
 // ---------------------------------------------------------------------------
-template <int PTS>
-__global__ void __launch_bounds__(1024) k_col_fwd(const void* Xv, float2* Y, ColGeom cg,
+template <int PTS, bool TC = false>
+__global__ void __launch_bounds__(TC ? 512 : 1024) k_col_fwd(const void* Xv, float2* Y, ColGeom cg,
                                                   int Lin, int m, int q, int p, int in_mode, int Lreal,
                                                   const float2* __restrict__ tw, FftPlan pl) {
   extern __shared__ float4 smem_raw[];
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(1024) k_col_fwd(const void* Xv, float2* Y, Col
       }
       __syncthreads();
     }
-    cta_fft<1, PTS>(buf, m, W, pl, tw, q);
+    cta_fft<1, PTS, TC>(buf, m, W, pl, tw, q);
     for (int idx = tid; idx < W * m; idx += T) {
       const int l = idx / W, w = idx - l * W;
       const int64_t b = b0 + w;
@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(1024) k_col_fwd(const void* Xv, float2* Y, Col
 //   real array (element (j, b) -> h[j][2b], h[j][2b+1], real row length Lreal).
 //   Eqs. accumulator and accumulation per column, scaled by `scale`.
 // ---------------------------------------------------------------------------
-template <int PTS>
-__global__ void __launch_bounds__(1024) k_col_bwd(const float2* Y, void* Zv, ColGeom cg, int Lout, int m,
+template <int PTS, bool TC = false>
+__global__ void __launch_bounds__(TC ? 512 : 1024) k_col_bwd(const float2* Y, void* Zv, ColGeom cg, int Lout, int m,
                                                   int q, int out_mode, int Lreal, float scale,
                                                   const float2* __restrict__ tw, FftPlan pl) {
   extern __shared__ float4 smem_raw[];
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(1024) k_col_bwd(const float2* Y, void* Zv, Col
       buf[w * m + l] = (b < cg.B) ? Y[(a * (int64_t)N + (int64_t)r * m + l) * cg.B + b] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    cta_fft<-1, PTS>(buf, m, W, pl, tw, q);
+    cta_fft<-1, PTS, TC>(buf, m, W, pl, tw, q);
     if (sep) {
       for (int idx = tid; idx < W * Lout; idx += T) {
         const int w = idx / Lout, j = idx - w * Lout;
@@ -407,8 +407,8 @@ __device__ __forceinline__ int row_partner(int row, const RowGeom& g) {
   return partner_row(r1, g.om[0], g.oq[0]) * M2 + partner_row(r2, g.om[1], g.oq[1]);
 }
 
-template <int PTS>
-__global__ void __launch_bounds__(1024) k_rows_rcm(float2* F, const float2* __restrict__ G, RowGeom rg, float scale,
+template <int PTS, bool TC = false>
+__global__ void __launch_bounds__(TC ? 512 : 1024) k_rows_rcm(float2* F, const float2* __restrict__ G, RowGeom rg, float scale,
                                                    const float2* __restrict__ tw, FftPlan pl) {
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(1024) k_rows_rcm(float2* F, const float2* __re
       buf[idx] = sum;
     }
     __syncthreads();
-    cta_fft<1, PTS>(buf, m, narr, pl, tw, q);
+    cta_fft<1, PTS, TC>(buf, m, narr, pl, tw, q);
     // multiply
     auto arrp = [&](int which, int slot) { return buf + (size_t)(which * nres + slot) * m; };
     if (selfrow) {
@@ -497,9 +497,9 @@ __global__ void __launch_bounds__(1024) k_rows_rcm(float2* F, const float2* __re
     __syncthreads();
     // inverse: A arrays (and C arrays) hold the products
     if (selfrow) {
-      cta_fft<-1, PTS>(buf, m, nres, pl, tw, q);
+      cta_fft<-1, PTS, TC>(buf, m, nres, pl, tw, q);
     } else {
-      cta_fft<-1, PTS>(buf, m, 2 * nres, pl, tw, q);
+      cta_fft<-1, PTS, TC>(buf, m, 2 * nres, pl, tw, q);
     }
     for (int idx = tid; idx < nrow * Lr; idx += T) {
       const int rr = idx / Lr, j = idx - rr * Lr;
@@ -699,9 +699,10 @@ static int elementwise_blocks(int64_t n) {
 
 // Choose W columns per CTA for a column pass: shared memory per column
 // `per_col` bytes and points per column `pts`; W <= 8, W even if `even`.
-static int choose_W(size_t per_col, int pts, int64_t B, size_t max_smem, bool even) {
+static int choose_W(size_t per_col, int pts, int64_t B, size_t max_smem, bool even,
+                    int64_t max_points = (int64_t)kPts * 1024) {
   int W = 8;
-  while (W > 1 && ((size_t)W * per_col > max_smem || (int64_t)W * pts > (int64_t)kPts * 1024)) W >>= 1;
+  while (W > 1 && ((size_t)W * per_col > max_smem || (int64_t)W * pts > max_points)) W >>= 1;
   if (even && W < 2) W = 2;
   if ((int64_t)W > B && !even) W = (int)std::max<int64_t>(1, B);
   return W;
@@ -713,33 +714,49 @@ struct ColPass {
   FftPlan pl;
 };
 
+// Points one CTA may transform at once: kPts per thread up to 1024 threads, or
+// up to 512 threads for the tensor-core instantiation (128 registers).
+static int64_t max_points(bool tc) { return (int64_t)kPts * (tc ? 512 : 1024); }
+
 static hd_status col_fwd(hd_ctx* c, const void* X, int in_mode, int Lreal, float2* Y, int64_t A, int Lin, int64_t B,
-                         const ColPass& cp, cudaStream_t st, int64_t Bp = 0) {
+                         const ColPass& cp, cudaStream_t st, int64_t Bp = 0, bool tc = false) {
   const bool keep = cp.q > 1;
   const size_t per_col = sizeof(float2) * ((keep ? (size_t)Lin : 0) + (size_t)cp.m) + 16;
-  const int W = choose_W(per_col, cp.m, B, (size_t)c->max_smem, false);
+  const int W = choose_W(per_col, cp.m, B, (size_t)c->max_smem, false, max_points(tc));
   ColGeom cg{A, B, W, Bp > 0 ? Bp : B};
   const size_t smem = sizeof(float2) * ((keep ? (size_t)acc_slots(W * Lin) : 0) + (size_t)W * cp.m);
-  if (smem > (size_t)c->max_smem || (int64_t)W * cp.m > (int64_t)kPts * 1024) return HD_EUNSUPPORTED;
+  if (smem > (size_t)c->max_smem || (int64_t)W * cp.m > max_points(tc)) return HD_EUNSUPPORTED;
   const int T = threads_for_points((int64_t)W * cp.m, kPts);
   const int64_t grid = A * ((B + W - 1) / W);
-  if (allow(k_col_fwd<kPts>, smem) != cudaSuccess) return HD_ECUDA;
-  k_col_fwd<kPts><<<(unsigned)grid, T, smem, st>>>(X, Y, cg, Lin, cp.m, cp.q, cp.p, in_mode, Lreal, cp.tw, cp.pl);
+  if (tc) {
+    if (allow(k_col_fwd<kPts, true>, smem) != cudaSuccess) return HD_ECUDA;
+    k_col_fwd<kPts, true><<<(unsigned)grid, T, smem, st>>>(X, Y, cg, Lin, cp.m, cp.q, cp.p, in_mode, Lreal, cp.tw,
+                                                           cp.pl);
+  } else {
+    if (allow(k_col_fwd<kPts>, smem) != cudaSuccess) return HD_ECUDA;
+    k_col_fwd<kPts><<<(unsigned)grid, T, smem, st>>>(X, Y, cg, Lin, cp.m, cp.q, cp.p, in_mode, Lreal, cp.tw, cp.pl);
+  }
   return cudaGetLastError() == cudaSuccess ? HD_OK : HD_ECUDA;
 }
 
 static hd_status col_bwd(hd_ctx* c, const float2* Y, void* Z, int out_mode, int Lreal, int64_t A, int Lout, int64_t B,
-                         const ColPass& cp, float scale, cudaStream_t st, int64_t Bp = 0) {
+                         const ColPass& cp, float scale, cudaStream_t st, int64_t Bp = 0, bool tc = false) {
   const bool sep = cp.q > 1 || Lout > cp.m;
   const size_t per_col = sizeof(float2) * ((sep ? (size_t)Lout : 0) + (size_t)cp.m) + 16;
-  const int W = choose_W(per_col, cp.m, B, (size_t)c->max_smem, false);
+  const int W = choose_W(per_col, cp.m, B, (size_t)c->max_smem, false, max_points(tc));
   ColGeom cg{A, B, W, Bp > 0 ? Bp : B};
   const size_t smem = sizeof(float2) * ((sep ? (size_t)acc_slots(W * Lout) : 0) + (size_t)W * cp.m);
-  if (smem > (size_t)c->max_smem || (int64_t)W * cp.m > (int64_t)kPts * 1024) return HD_EUNSUPPORTED;
+  if (smem > (size_t)c->max_smem || (int64_t)W * cp.m > max_points(tc)) return HD_EUNSUPPORTED;
   const int T = threads_for_points((int64_t)W * cp.m, kPts);
   const int64_t grid = A * ((B + W - 1) / W);
-  if (allow(k_col_bwd<kPts>, smem) != cudaSuccess) return HD_ECUDA;
-  k_col_bwd<kPts><<<(unsigned)grid, T, smem, st>>>(Y, Z, cg, Lout, cp.m, cp.q, out_mode, Lreal, scale, cp.tw, cp.pl);
+  if (tc) {
+    if (allow(k_col_bwd<kPts, true>, smem) != cudaSuccess) return HD_ECUDA;
+    k_col_bwd<kPts, true><<<(unsigned)grid, T, smem, st>>>(Y, Z, cg, Lout, cp.m, cp.q, out_mode, Lreal, scale, cp.tw,
+                                                           cp.pl);
+  } else {
+    if (allow(k_col_bwd<kPts>, smem) != cudaSuccess) return HD_ECUDA;
+    k_col_bwd<kPts><<<(unsigned)grid, T, smem, st>>>(Y, Z, cg, Lout, cp.m, cp.q, out_mode, Lreal, scale, cp.tw, cp.pl);
+  }
   return cudaGetLastError() == cudaSuccess ? HD_OK : HD_ECUDA;
 }
 
@@ -789,7 +806,7 @@ static hd_status row_params(hd_ctx* c, int64_t L, bool packed, const hd_dim_para
 }
 
 static hd_status hybrid_rcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_params* prm, const float* f,
-                               const float* g, float* h, cudaStream_t st) {
+                               const float* g, float* h, cudaStream_t st, bool tc = false) {
   // d = 2: [L0][L1]; d = 3: [L0][L1][L2]; the last dimension is packed
   const int64_t Ln = L[d - 1];
   const int64_t Lp = (Ln + 1) / 2;
@@ -813,13 +830,13 @@ static hd_status hybrid_rcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_
   float2* TG = TF + mid;
   // forward along the outer dimensions
   if (d == 2) {
-    s = col_fwd(c, f, IN_PACKED_REAL, (int)Ln, SF, 1, (int)L[0], Lp, outer[0], st);
-    if (s == HD_OK) s = col_fwd(c, g, IN_PACKED_REAL, (int)Ln, SG, 1, (int)L[0], Lp, outer[0], st);
+    s = col_fwd(c, f, IN_PACKED_REAL, (int)Ln, SF, 1, (int)L[0], Lp, outer[0], st, 0, tc);
+    if (s == HD_OK) s = col_fwd(c, g, IN_PACKED_REAL, (int)Ln, SG, 1, (int)L[0], Lp, outer[0], st, 0, tc);
   } else {
-    s = col_fwd(c, f, IN_PACKED_REAL, (int)Ln, TF, 1, (int)L[0], L[1] * Lp, outer[0], st, Lp);
-    if (s == HD_OK) s = col_fwd(c, g, IN_PACKED_REAL, (int)Ln, TG, 1, (int)L[0], L[1] * Lp, outer[0], st, Lp);
-    if (s == HD_OK) s = col_fwd(c, TF, IN_COMPLEX, 0, SF, M0, (int)L[1], Lp, outer[1], st);
-    if (s == HD_OK) s = col_fwd(c, TG, IN_COMPLEX, 0, SG, M0, (int)L[1], Lp, outer[1], st);
+    s = col_fwd(c, f, IN_PACKED_REAL, (int)Ln, TF, 1, (int)L[0], L[1] * Lp, outer[0], st, Lp, tc);
+    if (s == HD_OK) s = col_fwd(c, g, IN_PACKED_REAL, (int)Ln, TG, 1, (int)L[0], L[1] * Lp, outer[0], st, Lp, tc);
+    if (s == HD_OK) s = col_fwd(c, TF, IN_COMPLEX, 0, SF, M0, (int)L[1], Lp, outer[1], st, 0, tc);
+    if (s == HD_OK) s = col_fwd(c, TG, IN_COMPLEX, 0, SG, M0, (int)L[1], Lp, outer[1], st, 0, tc);
   }
   if (s != HD_OK) return s;
   // rows: C_1 on each row pair
@@ -838,18 +855,24 @@ static hd_status hybrid_rcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_
     rg.oq[1] = outer[1].q;
   }
   const size_t smem = sizeof(float2) * ((size_t)acc_slots(2 * (int)Lp) + 8 * (size_t)row.m);
-  if (smem > (size_t)c->max_smem || 8 * (int64_t)row.m > (int64_t)kPts * 1024) return HD_EUNSUPPORTED;
+  if (smem > (size_t)c->max_smem || 8 * (int64_t)row.m > max_points(tc)) return HD_EUNSUPPORTED;
   const int T = threads_for_points(8 * (int64_t)row.m, kPts);
-  if (allow(k_rows_rcm<kPts>, smem) != cudaSuccess) return HD_ECUDA;
-  k_rows_rcm<kPts><<<rg.nrows, T, smem, st>>>(SF, SG, rg, 1.0f / (float)(row.q * row.m), row.tw, row.pl);
+  if (tc) {
+    if (allow(k_rows_rcm<kPts, true>, smem) != cudaSuccess) return HD_ECUDA;
+    k_rows_rcm<kPts, true><<<rg.nrows, T, smem, st>>>(SF, SG, rg, 1.0f / (float)(row.q * row.m), row.tw, row.pl);
+  } else {
+    if (allow(k_rows_rcm<kPts>, smem) != cudaSuccess) return HD_ECUDA;
+    k_rows_rcm<kPts><<<rg.nrows, T, smem, st>>>(SF, SG, rg, 1.0f / (float)(row.q * row.m), row.tw, row.pl);
+  }
   if (cudaGetLastError() != cudaSuccess) return HD_ECUDA;
   // backward along the outer dimensions, unpacking at the end
   if (d == 2) {
-    s = col_bwd(c, SF, h, OUT_UNPACK_REAL, (int)Ln, 1, (int)L[0], Lp, outer[0], 1.0f / (float)M0, st);
+    s = col_bwd(c, SF, h, OUT_UNPACK_REAL, (int)Ln, 1, (int)L[0], Lp, outer[0], 1.0f / (float)M0, st, 0, tc);
   } else {
-    s = col_bwd(c, SF, TF, OUT_COMPLEX, 0, M0, (int)L[1], Lp, outer[1], 1.0f / (float)M1, st);
+    s = col_bwd(c, SF, TF, OUT_COMPLEX, 0, M0, (int)L[1], Lp, outer[1], 1.0f / (float)M1, st, 0, tc);
     if (s == HD_OK)
-      s = col_bwd(c, TF, h, OUT_UNPACK_REAL, (int)Ln, 1, (int)L[0], L[1] * Lp, outer[0], 1.0f / (float)M0, st, Lp);
+      s = col_bwd(c, TF, h, OUT_UNPACK_REAL, (int)Ln, 1, (int)L[0], L[1] * Lp, outer[0], 1.0f / (float)M0, st, Lp,
+                  tc);
   }
   return s;
 }
@@ -1064,11 +1087,13 @@ static hd_status conv_nd(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, 
   if (!c || !f || !g || !h) return HD_EINVAL;
   for (int i = 0; i < d; ++i)
     if (L[i] < 1 || L[i] > (1 << 20)) return L[i] < 1 ? HD_EINVAL : HD_EUNSUPPORTED;
-  if (prec != HD_FP32) return HD_EUNSUPPORTED;
+  // split precision: the radix-16 passes of hybridRCM's 2D/3D kernels on tensor cores
+  if (prec == HD_SPLIT_BF16 && algo != HD_HYBRID_RCM) return HD_EUNSUPPORTED;
+  if (prec != HD_FP32 && prec != HD_SPLIT_BF16) return HD_EINVAL;
   cudaSetDevice(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   switch (algo) {
-    case HD_HYBRID_RCM: return hybrid_rcm_nd(c, d, L, prm, f, g, h, st);
+    case HD_HYBRID_RCM: return hybrid_rcm_nd(c, d, L, prm, f, g, h, st, prec == HD_SPLIT_BF16);
     case HD_HYBRID_CS: return hybrid_cs_nd(c, d, L, prm, f, g, h, st);
     case HD_EXPLICIT:
     case HD_EXPLICIT_RCM: return explicit_nd(c, algo, d, L, f, g, h, st);
