@@ -118,6 +118,15 @@ hd_status hd_conv_adjoint(hd_ctx* ctx, hd_algo algo, int ndim, const int64_t* Ls
  * (HD_HYBRID_RCM reports packed lengths). */
 hd_status hd_plan(hd_ctx* ctx, hd_algo algo, int64_t L, hd_dim_params* out);
 
+/* The batched planner's autotuner table (filled by the first hybridRCM batch
+ * plan of the context unless the environment sets HD_AUTOTUNE=0): for each
+ * candidate i < *n (at most cap are copied), a cluster of C[i] CTAs with
+ * residue DFT length m[i] took us[i] microseconds per convolution of length
+ * 2 C[i] m[i].  The planner picks, per length, the cheapest candidate among
+ * the three shortest feasible DFT lengths of each cluster size (the role of
+ * the paper's empirical parameter scan, Sec. 6).  *n = 0 before tuning. */
+hd_status hd_tuning_table(hd_ctx* ctx, int32_t cap, int32_t* C, int32_t* m, double* us, int32_t* n);
+
 /* hybridRCM in 1D without any device allocation (no counterpart in the paper).
  * For callers that may not allocate: code running under an external memory
  * budget or allocator, loops that must not block (cudaMalloc / cudaFree can

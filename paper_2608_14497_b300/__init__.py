@@ -26,7 +26,8 @@ PRECS = {"fp32": HD_FP32, "split_bf16": HD_SPLIT_BF16}
 # Every symbol include/hdconv.h declares.
 EXPORTS = ("hd_create", "hd_destroy", "hd_conv1d", "hd_conv2d", "hd_conv3d", "hd_batch_plan_create",
            "hd_batch_plan_destroy", "hd_conv1d_batched", "hd_conv_adjoint", "hd_plan", "hd_last_device_error",
-           "hd_strerror", "hd_last_error_string", "hd_conv1d_rcm_noalloc")
+           "hd_strerror", "hd_last_error_string", "hd_conv1d_rcm_noalloc",
+           "hd_tuning_table")
 
 
 class HDError(RuntimeError):
@@ -72,6 +73,7 @@ def load(build_if_missing=False):
         "hd_strerror": ([I], ctypes.c_char_p),
         "hd_last_error_string": ([], ctypes.c_char_p),
         "hd_conv1d_rcm_noalloc": ([P, P, P, I64, DP, P], I),
+        "hd_tuning_table": ([P, I32, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -151,6 +153,19 @@ def hd_conv_adjoint(ctx, algo, Ls, batch, gh_ptr, f_ptr, g_ptr, gf_ptr, gg_ptr, 
 def hd_conv1d_rcm_noalloc(f_ptr, g_ptr, h_ptr, L, prm=None, stream=0):
     """hybridRCM 1D with no device allocation (scratch in a static device array)."""
     return load().hd_conv1d_rcm_noalloc(f_ptr, g_ptr, h_ptr, L, _params(prm, 1), stream)
+
+
+def hd_tuning_table(ctx):
+    """[(C, m, microseconds per convolution of length 2 C m)] of the autotuner."""
+    import numpy as np
+    n = ctypes.c_int32(0)
+    _check(load().hd_tuning_table(ctx, 0, None, None, None, ctypes.byref(n)), "hd_tuning_table")
+    C = np.zeros(max(1, n.value), np.int32)
+    m = np.zeros(max(1, n.value), np.int32)
+    us = np.zeros(max(1, n.value), np.float64)
+    _check(load().hd_tuning_table(ctx, n.value, C.ctypes.data, m.ctypes.data, us.ctypes.data, ctypes.byref(n)),
+           "hd_tuning_table")
+    return [(int(C[i]), int(m[i]), float(us[i])) for i in range(n.value)]
 
 
 def hd_last_device_error(ctx):

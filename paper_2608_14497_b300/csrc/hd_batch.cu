@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <vector>
@@ -76,9 +77,15 @@ extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, co
   std::vector<char> in_cluster(n, 0);
   int m_max = 1;
   if (algo == HD_HYBRID_RCM) {
+    // autotune the cluster kernel once per context (HD_AUTOTUNE=0 disables it)
+    const char* at = getenv("HD_AUTOTUNE");
+    if (!c->tuning.valid && !(at && at[0] == '0')) {
+      hd_status ts = cluster_autotune(c, &c->tuning);
+      if (ts != HD_OK) c->tuning.valid = false;
+    }
     for (int i = 0; i < n; ++i) {
       int C, m, p;
-      if (!cluster_params(Ls[i], &C, &m, &p)) continue;
+      if (!cluster_params(Ls[i], &C, &m, &p, &c->tuning)) continue;
       hd_status terr = HD_OK;
       const float2* tw = c->tables.get((int64_t)2 * C * m, 0, &terr);
       if (!tw) return terr;
@@ -230,6 +237,18 @@ extern "C" hd_status hd_conv1d_batched(hd_ctx* c, const hd_batch_plan* bp, const
     cudaError_t e = (bp->algo == HD_HYBRID_RCM) ? launch_rcm1d(la, lc.count, lc.threads, lc.smem, f, g, h, st)
                                                 : launch_cs1d(la, lc.count, lc.threads, lc.smem, f, g, h, st);
     if (e != cudaSuccess) return HD_ECUDA;
+  }
+  return HD_OK;
+}
+
+extern "C" hd_status hd_tuning_table(hd_ctx* c, int32_t cap, int32_t* C, int32_t* m, double* us, int32_t* n) {
+  if (!c || !n || cap < 0 || (cap > 0 && (!C || !m || !us))) return HD_EINVAL;
+  const ClusterTuning& t = c->tuning;
+  *n = t.valid ? (int32_t)t.us.size() : 0;
+  for (int32_t i = 0; i < *n && i < cap; ++i) {
+    C[i] = t.C[i];
+    m[i] = t.m[i];
+    us[i] = t.us[i];
   }
   return HD_OK;
 }

@@ -233,9 +233,27 @@ static const std::vector<int>& ladder() {
   return v;
 }
 
-bool cluster_params(int64_t L, int* C_out, int* m_out, int* p_out) {
+bool cluster_params(int64_t L, int* C_out, int* m_out, int* p_out, const ClusterTuning* tun) {
   if (L < 1) return false;
   const int64_t Lp = (L + 1) / 2;
+  if (tun && tun->valid) {
+    // cheapest measured candidate among the three shortest feasible lengths of each C
+    double best = 1e300;
+    int seen[4] = {0, 0, 0, 0};
+    for (size_t i = 0; i < tun->C.size(); ++i) {
+      const int C = tun->C[i], mm = tun->m[i];
+      const int ci = C == 1 ? 0 : C == 2 ? 1 : C == 4 ? 2 : 3;
+      if ((int64_t)2 * C * mm < L || seen[ci] >= 3) continue;
+      ++seen[ci];
+      if (tun->us[i] < best) {
+        best = tun->us[i];
+        *C_out = C;
+        *m_out = mm;
+        *p_out = (int)((Lp + mm - 1) / mm);
+      }
+    }
+    if (best < 1e300) return true;
+  }
   for (int C = 1; C <= 8; C *= 2) {
     const int64_t need = (L + 2 * C - 1) / (2 * C);  // q m >= L, q = 2C
     for (int mm : ladder()) {
@@ -248,6 +266,104 @@ bool cluster_params(int64_t L, int* C_out, int* m_out, int* p_out) {
     }
   }
   return false;
+}
+
+hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out) {
+  // candidates in increasing m per C (cluster_params relies on that order)
+  std::vector<int> Cs, ms;
+  for (int C = 1; C <= 8; C *= 2)
+    for (int mm : ladder())
+      if (mm >= 64) {
+        Cs.push_back(C);
+        ms.push_back(mm);
+      }
+  const int64_t budget = int64_t{1} << 22;  // real elements per timed batch
+  float *f = nullptr, *g = nullptr, *h = nullptr;
+  CUnit* d_units = nullptr;
+  CItem* d_items = nullptr;
+  hd_status st = HD_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaMalloc(&f, sizeof(float) * budget) != cudaSuccess || cudaMalloc(&g, sizeof(float) * budget) != cudaSuccess ||
+      cudaMalloc(&h, sizeof(float) * budget) != cudaSuccess ||
+      cudaMalloc(&d_units, sizeof(CUnit) * 4096) != cudaSuccess ||
+      cudaMalloc(&d_items, sizeof(CItem) * 4096) != cudaSuccess) {
+    st = HD_ENOMEM;
+  }
+  if (st == HD_OK) {
+    cudaMemset(f, 0, sizeof(float) * budget);
+    cudaMemset(g, 0, sizeof(float) * budget);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+  }
+  out->C.clear();
+  out->m.clear();
+  out->us.clear();
+  for (size_t i = 0; i < Cs.size() && st == HD_OK; ++i) {
+    const int C = Cs[i], mm = ms[i];
+    const int64_t L = (int64_t)2 * C * mm;
+    const int per = kClusterCtas / C;
+    int64_t K = budget / L;
+    K = std::max<int64_t>(per, std::min<int64_t>(K, 4096));
+    K = (K / per) * per;
+    if (K * L > budget) continue;
+    hd_status terr = HD_OK;
+    const float2* tw = c->tables.get(L, 0, &terr);
+    const float2* tabm = tw ? c->tables.get_pass_table(mm, 0, &terr) : nullptr;
+    if (!tw || !tabm) {
+      st = terr;
+      break;
+    }
+    std::vector<CItem> items(K);
+    std::vector<CUnit> units(K / per);
+    for (int64_t k = 0; k < K; ++k) {
+      std::memset(&items[k], 0, sizeof(CItem));
+      items[k].off = k * L;
+      items[k].L = (int32_t)L;
+      items[k].m = mm;
+      items[k].p = (int)(((L + 1) / 2 + mm - 1) / mm);
+      items[k].C = C;
+      items[k].tw = tw;
+      items[k].tabm = tabm;
+    }
+    for (size_t u = 0; u < units.size(); ++u) {
+      std::memset(&units[u], 0, sizeof(CUnit));
+      units[u].first = (int)(u * per);
+      units[u].count = per;
+      units[u].C = C;
+    }
+    cudaMemcpy(d_items, items.data(), sizeof(CItem) * K, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_units, units.data(), sizeof(CUnit) * units.size(), cudaMemcpyHostToDevice);
+    ClusterLaunch cl;
+    std::memset(&cl, 0, sizeof(cl));
+    cl.units = d_units;
+    cl.items = d_items;
+    const size_t smem = cluster_smem_bytes(mm);
+    if (launch_rcm1d_cluster(cl, (int)units.size(), smem, f, g, h, 0) != cudaSuccess) {
+      st = HD_ECUDA;
+      break;
+    }
+    cudaEventRecord(e0, 0);
+    for (int rep = 0; rep < 3; ++rep) launch_rcm1d_cluster(cl, (int)units.size(), smem, f, g, h, 0);
+    cudaEventRecord(e1, 0);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = HD_ECUDA;
+      break;
+    }
+    float ms_el = 0.f;
+    cudaEventElapsedTime(&ms_el, e0, e1);
+    out->C.push_back(C);
+    out->m.push_back(mm);
+    out->us.push_back(1e3 * ms_el / (3.0 * (double)K));
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(f);
+  cudaFree(g);
+  cudaFree(h);
+  cudaFree(d_units);
+  cudaFree(d_items);
+  out->valid = (st == HD_OK) && !out->us.empty();
+  return st;
 }
 
 size_t cluster_smem_bytes(int m_max) { return sizeof(float2) * 5 * (size_t)swz_stride(m_max); }

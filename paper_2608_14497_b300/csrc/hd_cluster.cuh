@@ -36,7 +36,12 @@ struct ClusterLaunch {
   FftPlan one_plan;
 };
 
-bool cluster_params(int64_t L, int* C, int* m, int* p);
+// (C, m, p) for a length: the measured cheapest candidate when `tun` holds an
+// autotuner table, else the smallest cluster whose largest ladder length
+// suffices, with the smallest such length.
+bool cluster_params(int64_t L, int* C, int* m, int* p, const ClusterTuning* tun = nullptr);
+// Time every candidate on synthetic batches (device scratch, a few tens of MB).
+hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out);
 size_t cluster_smem_bytes(int m_max);
 cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int nunits, size_t smem, const float* f, const float* g,
                                  float* h, cudaStream_t st);

@@ -19,6 +19,13 @@
 
 namespace hd {
 
+// Largest radix of the power-of-two passes (16, or 8 to fit a pass in 64
+// registers for 1024-thread blocks).
+#ifndef HD_FAST_MAXR
+#define HD_FAST_MAXR 16
+#endif
+constexpr int kFastMaxRadix = HD_FAST_MAXR;
+
 __host__ __device__ __forceinline__ int swz(int k) { return k ^ ((k >> 4) & 15); }
 // array stride: a whole number of 16-element blocks, so swz stays inside the array
 __host__ __device__ __forceinline__ int swz_stride(int n) { return (n + 15) & ~15; }
@@ -95,8 +102,13 @@ __host__ __device__ __forceinline__ int fast_passes(int n, int* Rs) {
   while (a2 < 30 && ((n >> a2) & 1) == 0) ++a2;
   const int odd = n >> a2;
   int k = 0;
-  for (int i = 0; i < (a2 >> 2); ++i) Rs[k++] = 16;
-  if (a2 & 3) Rs[k++] = 1 << (a2 & 3);
+  if (kFastMaxRadix == 8) {
+    for (int i = 0; i < a2 / 3; ++i) Rs[k++] = 8;
+    if (a2 % 3) Rs[k++] = 1 << (a2 % 3);
+  } else {
+    for (int i = 0; i < (a2 >> 2); ++i) Rs[k++] = 16;
+    if (a2 & 3) Rs[k++] = 1 << (a2 & 3);
+  }
   if (odd > 1) Rs[k++] = odd;
   return k;
 }
@@ -113,17 +125,33 @@ __device__ __forceinline__ void fill_pass_twiddles(float2* tws, int n, const flo
 // passes as fast_passes lists them.  (A loop over a runtime radix table
 // makes the register allocator spill; this fixed sequence does not.)
 // Requires nbuf * n <= PTS * T.
-template <int SIGN, int PTS>
+template <int SIGN, int PTS, int MAXR = kFastMaxRadix>
 __device__ __forceinline__ void cta_fft_fast(float2* base, int stride, int nbuf, int n,
                                              const float2* __restrict__ tws) {
   const int a2 = __ffs(n) - 1;
   const int odd = n >> a2;
   int Ns = 1;
-  for (int i = 0; i < (a2 >> 2); ++i) {
-    fstage<16, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
-    Ns *= 16;
+  if (MAXR == 8) {
+    // radix-8 passes while 8 divides the power of two, then one radix-4/2 pass
+    for (int i = 0; i < a2 / 3; ++i) {
+      fstage<8, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
+      Ns *= 8;
+    }
+    const int rem8 = a2 % 3;
+    if (rem8 == 2) {
+      fstage<4, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
+      Ns *= 4;
+    } else if (rem8 == 1) {
+      fstage<2, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
+      Ns *= 2;
+    }
+  } else {
+    for (int i = 0; i < (a2 >> 2); ++i) {
+      fstage<16, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
+      Ns *= 16;
+    }
   }
-  const int rem = a2 & 3;
+  const int rem = (MAXR == 8) ? 0 : (a2 & 3);
   if (rem == 3) {
     fstage<8, SIGN, PTS>(base, stride, nbuf, n, Ns, tws);
     Ns *= 8;

@@ -37,6 +37,15 @@ struct TableCache {
   void clear();
 };
 
+// Autotuner result for the cluster hybridRCM kernel: measured microseconds
+// per convolution for each candidate (C CTAs, residue DFT length m), timed at
+// the largest length the candidate covers, L = 2 C m.
+struct ClusterTuning {
+  bool valid = false;
+  std::vector<int> C, m;
+  std::vector<double> us;
+};
+
 }  // namespace hd
 
 struct hd_ctx {
@@ -51,6 +60,7 @@ struct hd_ctx {
   void* meta = nullptr;
   size_t meta_bytes = 0;
   int* dev_err = nullptr;  // device error word (bounded waits, bad launches)
+  hd::ClusterTuning tuning;  // filled on the first batched hybridRCM plan
   int max_smem = 0;        // opt-in shared memory per block
   int num_sms = 0;
   std::mutex mu;
