@@ -154,6 +154,22 @@ def cpu_oracle_sample(off, Ls, f, g, budget_items=None):
                       f"convolution padded to a power of two >= 2L-1, OpenMP over items; {dt:.2f} s"}
 
 
+def reduce_max_ms(ms, dist, device=None):
+    """Max of a per-rank time over all ranks (one all-reduce; identity alone)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(items_per_rank, world, steps, max_ms):
+    """Weak scaling: every rank processes its own batch; the job's rate is all
+    ranks' items over the slowest rank's time."""
+    return world * items_per_rank * steps / (max_ms / 1e3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -231,14 +247,11 @@ def run_gpu(args):
             graph.replay()
         ev1.record(cur)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+    ms = reduce_max_ms(ev0.elapsed_time(ev1), dist, device="cuda")
     if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     ms_step = ms / args.steps
-    value = world * n * args.steps / (ms / 1e3)
+    value = whole_job_rate(n, world, args.steps, ms)
 
     # dominant kernel: the single batched launch (one launch per step).
     # FP32-ALU roofline: algorithmic flops of the FFT convolutions, 15 L log2 L
@@ -281,12 +294,8 @@ def run_gpu(args):
             e2e_step()
         ee1.record()
         torch.cuda.synchronize()
-        ems = ee0.elapsed_time(ee1)
-        if dist is not None:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * n * ksteps / (ems / 1e3), "unit": "conv/s", "h2d_bytes_per_step": 8 * total,
+        ems = reduce_max_ms(ee0.elapsed_time(ee1), dist, device="cuda")
+        e2e = {"value": whole_job_rate(n, world, ksteps, ems), "unit": "conv/s", "h2d_bytes_per_step": 8 * total,
                "d2h_bytes_per_step": 4 * total, "steps": ksteps}
 
     if rank != 0:
