@@ -461,4 +461,151 @@ __device__ __noinline__ void cta_fft(float2* base, int stride, int nbuf, const F
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Structured engine for ladder lengths n = odd * 2^a (a >= 4, odd in
+// {1, 3, 5, 9}): the passes are a fixed, fully inlined sequence (radix 16
+// while 16 divides the power of two, one radix-8/4/2 pass for the rest of it,
+// then one radix-3/5/9 pass), so no runtime radix switch forces the register
+// allocator to spill.  Arrays enter and leave in natural order; only between
+// the first pass (Ns = 1, whose stores stride by 16) and the second pass are
+// the values kept at swz(i) = i ^ ((i >> 4) & 15), a permutation inside each
+// aligned block of 16 values that sends those stores to distinct banks.
+// Index splits use a float reciprocal with one integer correction (exact for
+// numerators below 2^17), twiddles come from the zeta_N table as in fft_stage.
+// ---------------------------------------------------------------------------
+struct DivF {
+  float rcp;
+  int d;
+};
+__device__ __forceinline__ DivF make_div(int d) { return DivF{1.0f / (float)d, d}; }
+__device__ __forceinline__ int fdiv(int n, DivF v) {
+  int q = __float2int_rz(__fmul_rn((float)n, v.rcp));
+  const int r = n - q * v.d;
+  if (r < 0) --q;
+  else if (r >= v.d) ++q;
+  return q;
+}
+
+__host__ __device__ __forceinline__ int swz(int k) { return k ^ ((k >> 4) & 15); }
+// array stride: a whole number of 16-element blocks, so swz stays inside the array
+__host__ __device__ __forceinline__ int swz_stride(int n) { return (n + 15) & ~15; }
+
+// Lengths cta_fft_struct takes.
+__host__ __device__ inline bool struct_length(int n) {
+  if (n < 16) return false;
+  int a2 = 0;
+  while (((n >> a2) & 1) == 0) ++a2;
+  const int odd = n >> a2;
+  return a2 >= 4 && (odd == 1 || odd == 3 || odd == 5 || odd == 9);
+}
+
+template <int R, int SIGN, int PTS, bool IN_SWZ, bool OUT_SWZ>
+__device__ __forceinline__ void gstage(float2* base, int stride, int nbuf, int n, int Ns,
+                                       const float2* __restrict__ tw, int twmul) {
+  constexpr int BPT = (PTS + R - 1) / R;
+  const int nb = n / R;
+  const DivF dnb = make_div(nb), dNs = make_div(Ns);
+  const int total = nb * nbuf;
+  const int T = blockDim.x;
+  const int twstep = twmul * (n / (Ns * R));
+  float2 v[BPT][R];
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    const int idx = threadIdx.x + b * T;
+    if (idx < total) {
+      const int a = fdiv(idx, dnb);
+      const int j = idx - a * nb;
+      const int jm = j - fdiv(j, dNs) * Ns;
+      const float2* x = base + a * stride;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = x[IN_SWZ ? swz(j + r * nb) : j + r * nb];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw_get<SIGN>(tw, r * jm * twstep));
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < BPT; ++b) {
+    const int idx = threadIdx.x + b * T;
+    if (idx < total) {
+      const int a = fdiv(idx, dnb);
+      const int j = idx - a * nb;
+      const int jm = j - fdiv(j, dNs) * Ns;
+      dft_reg<R, SIGN>(v[b]);
+      float2* y = base + a * stride;
+      const int o = (j - jm) * R + jm;
+#pragma unroll
+      for (int r = 0; r < R; ++r) y[OUT_SWZ ? swz(o + r * Ns) : o + r * Ns] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+// The pass after the radix-16 ones: radix 8/4/2 for the rest of the power of
+// two (rem = a mod 4), else the odd radix; IN_SWZ when it is the second pass.
+template <int SIGN, int PTS, bool IN_SWZ>
+__device__ __forceinline__ void gstage_rem(float2* base, int stride, int nbuf, int n, int& Ns, int rem,
+                                           const float2* __restrict__ tw, int twmul) {
+  if (rem == 3) {
+    gstage<8, SIGN, PTS, IN_SWZ, false>(base, stride, nbuf, n, Ns, tw, twmul);
+    Ns *= 8;
+  } else if (rem == 2) {
+    gstage<4, SIGN, PTS, IN_SWZ, false>(base, stride, nbuf, n, Ns, tw, twmul);
+    Ns *= 4;
+  } else if (rem == 1) {
+    gstage<2, SIGN, PTS, IN_SWZ, false>(base, stride, nbuf, n, Ns, tw, twmul);
+    Ns *= 2;
+  }
+}
+template <int SIGN, int PTS, bool IN_SWZ>
+__device__ __forceinline__ void gstage_odd(float2* base, int stride, int nbuf, int n, int Ns, int odd,
+                                           const float2* __restrict__ tw, int twmul) {
+  if (odd == 3) gstage<3, SIGN, PTS, IN_SWZ, false>(base, stride, nbuf, n, Ns, tw, twmul);
+  else if (odd == 5) gstage<5, SIGN, PTS, IN_SWZ, false>(base, stride, nbuf, n, Ns, tw, twmul);
+  else if (odd == 9) gstage<9, SIGN, PTS, IN_SWZ, false>(base, stride, nbuf, n, Ns, tw, twmul);
+}
+
+// Whole DFT of a struct_length n on nbuf arrays (base + a * stride), in place,
+// natural order in and out.  Requires nbuf * n <= PTS * blockDim.x.
+template <int SIGN, int PTS>
+__device__ __forceinline__ void cta_fft_struct(float2* base, int stride, int nbuf, int n,
+                                               const float2* __restrict__ tw, int twmul) {
+  const int a2 = __ffs(n) - 1;
+  const int odd = n >> a2;
+  const int n16 = a2 >> 2, rem = a2 & 3;
+  if (n == 16) {
+    gstage<16, SIGN, PTS, false, false>(base, stride, nbuf, n, 1, tw, twmul);
+    return;
+  }
+  gstage<16, SIGN, PTS, false, true>(base, stride, nbuf, n, 1, tw, twmul);
+  int Ns = 16;
+  if (n16 >= 2) {
+    gstage<16, SIGN, PTS, true, false>(base, stride, nbuf, n, Ns, tw, twmul);
+    Ns *= 16;
+    for (int i = 2; i < n16; ++i) {
+      gstage<16, SIGN, PTS, false, false>(base, stride, nbuf, n, Ns, tw, twmul);
+      Ns *= 16;
+    }
+    gstage_rem<SIGN, PTS, false>(base, stride, nbuf, n, Ns, rem, tw, twmul);
+    gstage_odd<SIGN, PTS, false>(base, stride, nbuf, n, Ns, odd, tw, twmul);
+  } else if (rem) {
+    gstage_rem<SIGN, PTS, true>(base, stride, nbuf, n, Ns, rem, tw, twmul);
+    gstage_odd<SIGN, PTS, false>(base, stride, nbuf, n, Ns, odd, tw, twmul);
+  } else {
+    gstage_odd<SIGN, PTS, true>(base, stride, nbuf, n, Ns, odd, tw, twmul);
+  }
+}
+
+// DFT dispatch of the nD kernels: SE (struct_length lengths) inlines the
+// structured engine, otherwise the generic plan-driven cta_fft.
+template <int SIGN, int PTS, bool TC, bool SE>
+__device__ __forceinline__ void fft_sel(float2* base, int stride, int nbuf, const FftPlan& pl,
+                                        const float2* __restrict__ tw, int twmul) {
+  if constexpr (SE) cta_fft_struct<SIGN, PTS>(base, stride, nbuf, pl.n, tw, twmul);
+  else cta_fft<SIGN, PTS, TC>(base, stride, nbuf, pl, tw, twmul);
+}
+
 }  // namespace hd

@@ -26,22 +26,7 @@ namespace hd {
 #endif
 constexpr int kFastMaxRadix = HD_FAST_MAXR;
 
-__host__ __device__ __forceinline__ int swz(int k) { return k ^ ((k >> 4) & 15); }
-// array stride: a whole number of 16-element blocks, so swz stays inside the array
-__host__ __device__ __forceinline__ int swz_stride(int n) { return (n + 15) & ~15; }
-
-struct DivF {
-  float rcp;
-  int d;
-};
-__device__ __forceinline__ DivF make_div(int d) { return DivF{1.0f / (float)d, d}; }
-__device__ __forceinline__ int fdiv(int n, DivF v) {
-  int q = __float2int_rz(__fmul_rn((float)n, v.rcp));
-  const int r = n - q * v.d;
-  if (r < 0) --q;
-  else if (r >= v.d) ++q;
-  return q;
-}
+// swz, swz_stride, DivF / fdiv: hd_fft.cuh.
 
 // One Stockham pass of radix R on nbuf arrays of length n at base + a*stride
 // (stride a multiple of 16, indices swizzled per array), twiddles tws (per-pass

@@ -28,6 +28,7 @@ struct Item1D {
 bool factor_radices(int n, FftPlan* out);  // false if n < 1
 bool smooth235(int64_t n);
 int64_t next_smooth(int64_t n);
+int64_t ladder_ceil(int64_t n);  // smallest {1, 3, 5, 9} x 2^a >= n
 
 // Twiddle tables: zeta_N^k, k < N, FP64 on the device, rounded to FP32.
 struct TableCache {

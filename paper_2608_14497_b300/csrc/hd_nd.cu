@@ -25,539 +25,10 @@
 #include <algorithm>
 #include <cstring>
 
-#include "hd_conv1d.cuh"
-#include "hd_internal.h"
 #include "hd_nd.cuh"
+#include "hd_nd_kernels.cuh"
 
 namespace hd {
-
-// ---------------------------------------------------------------------------
-// shared device helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int modmul(int a, int b, int N) { return (int)(((int64_t)a * b) % N); }
-
-// Natural index of storage row r m + l is q l + r; its conjugate partner
-// (M - k) mod M in storage form.
-__device__ __forceinline__ int partner_row(int idx, int m, int q) {
-  const int r = idx / m, l = idx - r * m;
-  if (r == 0) return (l == 0) ? 0 : (m - l);
-  return (q - r) * m + (m - 1 - l);
-}
-
-// Column geometry: the transformed dimension has stride B (elements) inside
-// blocks of A; a CTA owns W consecutive columns b0..b0+W-1 of one block a.
-struct ColGeom {
-  int64_t A, B;   // outer block count, inner (contiguous) extent
-  int W;          // columns per CTA
-  int64_t Bp;     // packed last-dimension length inside B (real packing modes)
-};
-
-// Real offset of packed element (row j of block a, column b): the inner index
-// b runs over (B / Bp) rows of Bp packed pairs, each row Lreal reals long.
-__device__ __forceinline__ int64_t packed_offset(const ColGeom& cg, int64_t a, int64_t Lrows, int64_t j, int64_t b,
-                                                 int Lreal, int64_t* c) {
-  const int64_t sub = b / cg.Bp;
-  *c = 2 * (b - sub * cg.Bp);
-  return ((a * Lrows + j) * (cg.B / cg.Bp) + sub) * (int64_t)Lreal;
-}
-
-// Input element loaders for the column passes.
-enum : int { IN_COMPLEX = 0, IN_PACKED_REAL = 1 };
-enum : int { OUT_COMPLEX = 0, OUT_UNPACK_REAL = 1 };
-
-// ---------------------------------------------------------------------------
-// k_col_fwd: complex hybrid forward transform along a strided dimension.
-//   X: [A][Lin][B] complex (or real packed along B: element (j, b) =
-//      (f[j][2b], f[j][2b+1]) with real row length Lreal), Y: [A][q m][B],
-//   residue-major rows.  Eq. forwardr per column.
-// ---------------------------------------------------------------------------
-template <int PTS, bool TC = false>
-__global__ void __launch_bounds__(TC ? 512 : 1024) k_col_fwd(const void* Xv, float2* Y, ColGeom cg,
-                                                  int Lin, int m, int q, int p, int in_mode, int Lreal,
-                                                  const float2* __restrict__ tw, FftPlan pl) {
-  extern __shared__ float4 smem_raw[];
-  float2* sm = reinterpret_cast<float2*>(smem_raw);
-  const int W = cg.W;
-  const int64_t ncolblk = (cg.B + W - 1) / W;
-  const int64_t a = blockIdx.x / ncolblk;
-  const int64_t b0 = (blockIdx.x - a * ncolblk) * W;
-  const int N = q * m;
-  const int T = blockDim.x, tid = threadIdx.x;
-  const bool keep = (q > 1);  // several residues reuse the loaded columns
-  float2* x = sm;                              // W x Lin (only if keep)
-  float2* buf = keep ? sm + acc_slots(W * Lin) : sm;  // W x m
-  // load columns (zero beyond the input)
-  float2* dst = keep ? x : buf;
-  const int ldst = keep ? Lin : m;
-  for (int idx = tid; idx < W * ldst; idx += T) {
-    const int j = idx / W, w = idx - j * W;
-    const int64_t b = b0 + w;
-    float2 v = make_float2(0.f, 0.f);
-    if (j < Lin && b < cg.B) {
-      const int64_t e = (a * Lin + j) * cg.B + b;
-      if (in_mode == IN_COMPLEX) {
-        v = reinterpret_cast<const float2*>(Xv)[e];
-      } else {
-        int64_t c;
-        const float* fr = reinterpret_cast<const float*>(Xv) + packed_offset(cg, a, Lin, j, b, Lreal, &c);
-        v = make_float2(fr[c], (c + 1 < Lreal) ? fr[c + 1] : 0.f);
-      }
-    }
-    dst[w * ldst + j] = v;
-  }
-  __syncthreads();
-  for (int r = 0; r < q; ++r) {
-    if (keep) {
-      for (int idx = tid; idx < W * m; idx += T) {
-        const int w = idx / m, s = idx - w * m;
-        float2 sum = make_float2(0.f, 0.f);
-        int e = r * s;
-        const int estep = r * m;
-        for (int t = 0; t < p; ++t) {
-          const int j = t * m + s;
-          if (j >= Lin) break;
-          sum = cadd(sum, cmul(x[w * Lin + j], tw_get<1>(tw, e)));
-          e += estep;
-          if (e >= N) e -= N;
-        }
-        buf[idx] = sum;
-      }
-      __syncthreads();
-    }
-    cta_fft<1, PTS, TC>(buf, m, W, pl, tw, q);
-    for (int idx = tid; idx < W * m; idx += T) {
-      const int l = idx / W, w = idx - l * W;
-      const int64_t b = b0 + w;
-      if (b < cg.B) Y[(a * (int64_t)N + (int64_t)r * m + l) * cg.B + b] = buf[w * m + l];
-    }
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// k_col_bwd: complex hybrid backward transform along a strided dimension.
-//   Y: [A][q m][B] residue-major; Z: [A][Lout][B] complex, or the unpacked
-//   real array (element (j, b) -> h[j][2b], h[j][2b+1], real row length Lreal).
-//   Eqs. accumulator and accumulation per column, scaled by `scale`.
-// ---------------------------------------------------------------------------
-template <int PTS, bool TC = false>
-__global__ void __launch_bounds__(TC ? 512 : 1024) k_col_bwd(const float2* Y, void* Zv, ColGeom cg, int Lout, int m,
-                                                  int q, int out_mode, int Lreal, float scale,
-                                                  const float2* __restrict__ tw, FftPlan pl) {
-  extern __shared__ float4 smem_raw[];
-  float2* sm = reinterpret_cast<float2*>(smem_raw);
-  const int W = cg.W;
-  const int64_t ncolblk = (cg.B + W - 1) / W;
-  const int64_t a = blockIdx.x / ncolblk;
-  const int64_t b0 = (blockIdx.x - a * ncolblk) * W;
-  const int N = q * m;
-  const int T = blockDim.x, tid = threadIdx.x;
-  const bool sep = (q > 1) || (Lout > m);
-  float2* acc = sm;                                  // W x Lout (if sep)
-  float2* buf = sep ? sm + acc_slots(W * Lout) : sm;  // W x m
-  if (sep)
-    for (int idx = tid; idx < W * Lout; idx += T) acc[idx] = make_float2(0.f, 0.f);
-  for (int r = 0; r < q; ++r) {
-    for (int idx = tid; idx < W * m; idx += T) {
-      const int l = idx / W, w = idx - l * W;
-      const int64_t b = b0 + w;
-      buf[w * m + l] = (b < cg.B) ? Y[(a * (int64_t)N + (int64_t)r * m + l) * cg.B + b] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    cta_fft<-1, PTS, TC>(buf, m, W, pl, tw, q);
-    if (sep) {
-      for (int idx = tid; idx < W * Lout; idx += T) {
-        const int w = idx / Lout, j = idx - w * Lout;
-        acc[idx] = cadd(acc[idx], cmul(buf[w * m + (j % m)], tw_get<-1>(tw, modmul(r, j, N))));
-      }
-      __syncthreads();
-    }
-  }
-  const float2* res = sep ? acc : buf;
-  const int lres = sep ? Lout : m;
-  for (int idx = tid; idx < W * Lout; idx += T) {
-    const int j = idx / W, w = idx - j * W;
-    const int64_t b = b0 + w;
-    if (b >= cg.B) continue;
-    const float2 v = cscale(res[w * lres + j], scale);
-    if (out_mode == OUT_COMPLEX) {
-      reinterpret_cast<float2*>(Zv)[(a * Lout + j) * cg.B + b] = v;
-    } else {
-      int64_t c;
-      float* hr = reinterpret_cast<float*>(Zv) + packed_offset(cg, a, Lout, j, b, Lreal, &c);
-      hr[c] = v.x;
-      if (c + 1 < Lreal) hr[c + 1] = v.y;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// k_col_fwd_cs: real residues of Sec. 3.1 along the first dimension of a
-// real array X [Lin][B] (B contiguous real).  Output rows (complex, per column):
-//   residue 0:   l = 0..m/2  (m/2 + 1 rows; the columns are transformed two at
-//                a time as the real and imaginary parts of one complex DFT)
-//   residues 1..ceil(q/2)-1: m rows each (Eq. forwardr)
-//   residue q/2 (q even):    m/2 rows (Eq. forwardq2)
-// ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ int cs_rows(int m, int q) {
-  return (m / 2 + 1) + ((q + 1) / 2 - 1) * m + ((q % 2 == 0) ? m / 2 : 0);
-}
-
-template <int PTS>
-__global__ void __launch_bounds__(1024) k_col_fwd_cs(const float* __restrict__ X, float2* __restrict__ Y, int64_t B,
-                                                     int W, int Lin, int m, int q, int p,
-                                                     const float2* __restrict__ tw, FftPlan pl_m, FftPlan pl_h) {
-  extern __shared__ float4 smem_raw[];
-  float2* sm = reinterpret_cast<float2*>(smem_raw);
-  const int64_t b0 = (int64_t)blockIdx.x * W;
-  const int N = q * m;
-  const int R = cs_rows(m, q);
-  const int T = blockDim.x, tid = threadIdx.x;
-  float* x = reinterpret_cast<float*>(sm);          // W x Lin real
-  float2* buf = sm + acc_slots((W * Lin + 1) / 2);  // W x m complex
-  for (int idx = tid; idx < W * Lin; idx += T) {
-    const int j = idx / W, w = idx - j * W;
-    const int64_t b = b0 + w;
-    x[w * Lin + j] = (b < B) ? X[(int64_t)j * B + b] : 0.f;
-  }
-  __syncthreads();
-  auto store = [&](int row, int w, float2 v) {
-    const int64_t b = b0 + w;
-    if (b < B) Y[(int64_t)row * B + b] = v;
-  };
-  // residue 0: pairs of real columns as one complex column
-  {
-    const int npair = W / 2;
-    for (int idx = tid; idx < npair * m; idx += T) {
-      const int pw = idx / m, s = idx - pw * m;
-      float x0 = 0.f, x1 = 0.f;
-      for (int t = 0; t < p; ++t) {
-        const int j = t * m + s;
-        if (j >= Lin) break;
-        x0 += x[(2 * pw) * Lin + j];
-        x1 += x[(2 * pw + 1) * Lin + j];
-      }
-      buf[idx] = make_float2(x0, x1);
-    }
-    __syncthreads();
-    cta_fft<1, PTS>(buf, m, npair, pl_m, tw, q);
-    const int nh = m / 2 + 1;
-    for (int idx = tid; idx < npair * nh; idx += T) {
-      const int l = idx / npair, pw = idx - l * npair;
-      const float2 z = buf[pw * m + l], zc = cconj(buf[pw * m + (l == 0 ? 0 : m - l)]);
-      // X_w = (Z_l + conj Z_{m-l}) / 2, X_{w+1} = (Z_l - conj Z_{m-l}) / (2i)
-      store(l, 2 * pw, cscale(cadd(z, zc), 0.5f));
-      store(l, 2 * pw + 1, cscale(cmul_i<-1>(csub(z, zc)), 0.5f));
-    }
-    __syncthreads();
-  }
-  int row0 = m / 2 + 1;
-  for (int r = 1; r < (q + 1) / 2; ++r) {
-    for (int idx = tid; idx < W * m; idx += T) {
-      const int w = idx / m, s = idx - w * m;
-      float2 sum = make_float2(0.f, 0.f);
-      int e = r * s;
-      for (int t = 0; t < p; ++t) {
-        const int j = t * m + s;
-        if (j >= Lin) break;
-        const float2 z = tw_get<1>(tw, e);
-        const float v = x[w * Lin + j];
-        sum.x = fmaf(v, z.x, sum.x);
-        sum.y = fmaf(v, z.y, sum.y);
-        e += r * m;
-        if (e >= N) e -= N;
-      }
-      buf[idx] = sum;
-    }
-    __syncthreads();
-    cta_fft<1, PTS>(buf, m, W, pl_m, tw, q);
-    for (int idx = tid; idx < W * m; idx += T) {
-      const int l = idx / W, w = idx - l * W;
-      store(row0 + l, w, buf[w * m + l]);
-    }
-    __syncthreads();
-    row0 += m;
-  }
-  if (q % 2 == 0) {
-    const int e = m / 2, qh = q / 2;
-    for (int idx = tid; idx < W * e; idx += T) {
-      const int w = idx / e, bb = idx - w * e;
-      float x0 = 0.f, x1 = 0.f;
-      for (int t = 0; t < p; ++t) {
-        const float sg = (t & 1) ? -1.f : 1.f;
-        const int j = t * m + bb;
-        if (j < Lin) x0 += sg * x[w * Lin + j];
-        if (j + e < Lin) x1 += sg * x[w * Lin + j + e];
-      }
-      buf[idx] = cmul(make_float2(x0, x1), tw_get<1>(tw, bb * qh));
-    }
-    __syncthreads();
-    cta_fft<1, PTS>(buf, e, W, pl_h, tw, 2 * q);
-    for (int idx = tid; idx < W * e; idx += T) {
-      const int c = idx / W, w = idx - c * W;
-      store(row0 + c, w, buf[w * e + c]);
-    }
-  }
-  (void)R;
-}
-
-// k_col_bwd_cs: inverse of k_col_fwd_cs with Eq. real-accumulation; writes the
-// first Lout rows of the real array Z [Lout][B], scaled.
-template <int PTS>
-__global__ void __launch_bounds__(1024) k_col_bwd_cs(const float2* __restrict__ Y, float* __restrict__ Z, int64_t B,
-                                                     int W, int Lout, int m, int q, float scale,
-                                                     const float2* __restrict__ tw, FftPlan pl_m, FftPlan pl_h) {
-  extern __shared__ float4 smem_raw[];
-  float2* sm = reinterpret_cast<float2*>(smem_raw);
-  const int64_t b0 = (int64_t)blockIdx.x * W;
-  const int N = q * m;
-  const int T = blockDim.x, tid = threadIdx.x;
-  float* acc = reinterpret_cast<float*>(sm);          // W x Lout real
-  float2* buf = sm + acc_slots((W * Lout + 1) / 2);  // W x m complex
-  auto load = [&](int row, int w) -> float2 {
-    const int64_t b = b0 + w;
-    return (b < B) ? Y[(int64_t)row * B + b] : make_float2(0.f, 0.f);
-  };
-  for (int idx = tid; idx < W * Lout; idx += T) acc[idx] = 0.f;
-  // residue 0: complex-to-real, two columns per complex DFT: Z_l = H_w[l] + i H_{w+1}[l]
-  {
-    const int npair = W / 2;
-    const int nh = m / 2 + 1;
-    for (int idx = tid; idx < npair * m; idx += T) {
-      const int l = idx / npair, pw = idx - l * npair;
-      float2 a0, a1;
-      if (l < nh) {
-        a0 = load(l, 2 * pw);
-        a1 = load(l, 2 * pw + 1);
-      } else {
-        a0 = cconj(load(m - l, 2 * pw));
-        a1 = cconj(load(m - l, 2 * pw + 1));
-      }
-      buf[pw * m + l] = cadd(a0, cmul_i<1>(a1));
-    }
-    __syncthreads();
-    cta_fft<-1, PTS>(buf, m, npair, pl_m, tw, q);
-    for (int idx = tid; idx < W * Lout; idx += T) {
-      const int w = idx / Lout, j = idx - w * Lout;
-      const float2 v = buf[(w / 2) * m + (j % m)];
-      acc[idx] += (w & 1) ? v.y : v.x;
-    }
-    __syncthreads();
-  }
-  int row0 = m / 2 + 1;
-  for (int r = 1; r < (q + 1) / 2; ++r) {
-    for (int idx = tid; idx < W * m; idx += T) {
-      const int l = idx / W, w = idx - l * W;
-      buf[w * m + l] = load(row0 + l, w);
-    }
-    __syncthreads();
-    cta_fft<-1, PTS>(buf, m, W, pl_m, tw, q);
-    for (int idx = tid; idx < W * Lout; idx += T) {
-      const int w = idx / Lout, j = idx - w * Lout;
-      acc[idx] += 2.f * cmul(buf[w * m + (j % m)], tw_get<-1>(tw, modmul(r, j, N))).x;
-    }
-    __syncthreads();
-    row0 += m;
-  }
-  if (q % 2 == 0) {
-    const int e = m / 2, qh = q / 2;
-    for (int idx = tid; idx < W * e; idx += T) {
-      const int c = idx / W, w = idx - c * W;
-      buf[w * e + c] = load(row0 + c, w);
-    }
-    __syncthreads();
-    cta_fft<-1, PTS>(buf, e, W, pl_h, tw, 2 * q);
-    for (int idx = tid; idx < W * Lout; idx += T) {
-      const int w = idx / Lout, j = idx - w * Lout;
-      const int t = j / m, s = j - t * m;
-      const int bb = s < e ? s : s - e;
-      const float2 v = cmul(buf[w * e + bb], tw_get<-1>(tw, bb * qh));
-      const float val = 2.f * (s < e ? v.x : v.y);
-      acc[idx] += (t & 1) ? -val : val;
-    }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < W * Lout; idx += T) {
-    const int j = idx / W, w = idx - j * W;
-    const int64_t b = b0 + w;
-    if (b < B) Z[(int64_t)j * B + b] = acc[w * Lout + j] * scale;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// k_rows_rcm: one row of the outer spectra and its conjugate partner, a 1D
-// hybrid convolution along the last dimension with the operator C_1 (Sec. 5):
-//   H1_k = A_k B_k - 1/4 (A_k - conj C_k*)(B_k - conj D_k*)(1 + zeta_M^k),
-//   H2_k* = C_k* D_k* - conj(...)   (A, B: rows of F, G; C, D: partner rows).
-// Rows are complex of length Lrow (packed), in place over F's rows.  A row
-// that is its own partner reduces to the 1D RCM of Eqs. Hr / Hr-conj.
-// ---------------------------------------------------------------------------
-struct RowGeom {
-  int nrows;        // rows in the grid
-  int Lrow;         // row length (complex)
-  int m, q, p;      // hybrid parameters along the row
-  int nd;           // number of outer dimensions (1 or 2)
-  int om[2], oq[2]; // outer (m, q) per outer dimension
-};
-
-__device__ __forceinline__ int row_partner(int row, const RowGeom& g) {
-  if (g.nd == 1) return partner_row(row, g.om[0], g.oq[0]);
-  const int M2 = g.om[1] * g.oq[1];
-  const int r1 = row / M2, r2 = row - r1 * M2;
-  return partner_row(r1, g.om[0], g.oq[0]) * M2 + partner_row(r2, g.om[1], g.oq[1]);
-}
-
-template <int PTS, bool TC = false>
-__global__ void __launch_bounds__(TC ? 512 : 1024) k_rows_rcm(float2* F, const float2* __restrict__ G, RowGeom rg, float scale,
-                                                   const float2* __restrict__ tw, FftPlan pl) {
-  extern __shared__ float4 smem_raw[];
-  float2* sm = reinterpret_cast<float2*>(smem_raw);
-  const int row = blockIdx.x;
-  const int prow = row_partner(row, rg);
-  if (prow < row) return;
-  const bool selfrow = (prow == row);
-  const int T = blockDim.x, tid = threadIdx.x;
-  const int Lr = rg.Lrow, m = rg.m, q = rg.q, p = rg.p, N = q * m;
-  const int nrow = selfrow ? 1 : 2;
-  float2* acc = sm;                          // nrow x Lr
-  float2* buf = sm + acc_slots(nrow * Lr);   // arrays of m
-  const float2* src[4] = {F + (int64_t)row * Lr, F + (int64_t)prow * Lr, G + (int64_t)row * Lr,
-                          G + (int64_t)prow * Lr};
-  for (int idx = tid; idx < nrow * Lr; idx += T) acc[idx] = make_float2(0.f, 0.f);
-  __syncthreads();
-  for (int ra = 0; ra <= q / 2; ++ra) {
-    const int rb = (q - ra) % q;
-    const bool selfres = (ra == rb);
-    const int nres = selfres ? 1 : 2;
-    // arrays: index = (which * nres + slot) with which in {A, C, B, D} (C, D only if !selfrow)
-    const int nwhich = selfrow ? 2 : 4;
-    const int narr = nwhich * nres;
-    for (int idx = tid; idx < narr * m; idx += T) {
-      const int arr = idx / m, s = idx - arr * m;
-      const int which = arr / nres, slot = arr - which * nres;
-      const int r = slot ? rb : ra;
-      // which: selfrow {0: A(F row), 1: B(G row)}; else {0: A, 1: C, 2: B, 3: D}
-      const float2* x = selfrow ? src[which == 0 ? 0 : 2] : src[which == 0 ? 0 : (which == 1 ? 1 : (which == 2 ? 2 : 3))];
-      float2 sum = make_float2(0.f, 0.f);
-      int e = r * s;
-      for (int t = 0; t < p; ++t) {
-        const int j = t * m + s;
-        if (j >= Lr) break;
-        sum = cadd(sum, cmul(x[j], tw_get<1>(tw, e)));
-        e += r * m;
-        if (e >= N) e -= N;
-      }
-      buf[idx] = sum;
-    }
-    __syncthreads();
-    cta_fft<1, PTS, TC>(buf, m, narr, pl, tw, q);
-    // multiply
-    auto arrp = [&](int which, int slot) { return buf + (size_t)(which * nres + slot) * m; };
-    if (selfrow) {
-      float2* F0 = arrp(0, 0);
-      float2* Fb = arrp(0, selfres ? 0 : 1);
-      float2* G0 = arrp(1, 0);
-      float2* Gb = arrp(1, selfres ? 0 : 1);
-      for (int l = tid; l < m; l += T) {
-        int ls;
-        if (selfres) {
-          ls = (ra == 0) ? (l == 0 ? 0 : m - l) : (m - 1 - l);
-          if (l > ls) continue;
-        } else {
-          ls = m - 1 - l;
-        }
-        const float2 A = F0[l], B = G0[l], Ac = Fb[ls], Bc = Gb[ls];
-        const float2 z = tw_get<1>(tw, q * l + ra);
-        const float2 Z = make_float2(0.25f * (1.f + z.x), 0.25f * z.y);
-        const float2 alpha = cmul(cmul(csub(A, cconj(Ac)), csub(B, cconj(Bc))), Z);
-        F0[l] = csub(cmul(A, B), alpha);
-        if (!(selfres && ls == l)) Fb[ls] = csub(cmul(Ac, Bc), cconj(alpha));
-      }
-    } else {
-      // every k of residue ra (and of rb when distinct) gives H1_k and H2_{k*}
-      for (int idx = tid; idx < nres * m; idx += T) {
-        const int slot = idx / m, l = idx - slot * m;
-        const int r = slot ? rb : ra;
-        const int pslot = selfres ? 0 : 1 - slot;
-        const int ls = (r == 0) ? (l == 0 ? 0 : m - l) : (m - 1 - l);
-        float2* Ar = arrp(0, slot);
-        float2* Cr = arrp(1, pslot);
-        const float2 A = Ar[l], B = arrp(2, slot)[l], Cs = Cr[ls], Ds = arrp(3, pslot)[ls];
-        const float2 z = tw_get<1>(tw, q * l + r);
-        const float2 Z = make_float2(0.25f * (1.f + z.x), 0.25f * z.y);
-        const float2 alpha = cmul(cmul(csub(A, cconj(Cs)), csub(B, cconj(Ds))), Z);
-        const float2 h1 = csub(cmul(A, B), alpha);
-        const float2 h2 = csub(cmul(Cs, Ds), cconj(alpha));
-        // in place: (slot, l) -> (pslot, ls) is a bijection, so every location
-        // is read and written by exactly one iteration
-        Ar[l] = h1;
-        Cr[ls] = h2;
-      }
-    }
-    __syncthreads();
-    // inverse: A arrays (and C arrays) hold the products
-    if (selfrow) {
-      cta_fft<-1, PTS, TC>(buf, m, nres, pl, tw, q);
-    } else {
-      cta_fft<-1, PTS, TC>(buf, m, 2 * nres, pl, tw, q);
-    }
-    for (int idx = tid; idx < nrow * Lr; idx += T) {
-      const int rr = idx / Lr, j = idx - rr * Lr;
-      const int s = j % m;
-      float2 v = cmul(arrp(rr, 0)[s], tw_get<-1>(tw, modmul(ra, j, N)));
-      if (!selfres) v = cadd(v, cmul(arrp(rr, 1)[s], tw_get<-1>(tw, modmul(rb, j, N))));
-      acc[idx] = cadd(acc[idx], v);
-    }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < nrow * Lr; idx += T) {
-    const int rr = idx / Lr, j = idx - rr * Lr;
-    F[(int64_t)(rr ? prow : row) * Lr + j] = cscale(acc[idx], scale);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// k_rows_cconv: complex hybrid convolution (Sec. 2) of each row of F with the
-// same row of G along the last dimension, pointwise product, in place over F.
-// ---------------------------------------------------------------------------
-template <int PTS>
-__global__ void __launch_bounds__(1024) k_rows_cconv(float2* F, const float2* __restrict__ G, int Lr, int m, int q,
-                                                     int p, float scale, const float2* __restrict__ tw, FftPlan pl) {
-  extern __shared__ float4 smem_raw[];
-  float2* sm = reinterpret_cast<float2*>(smem_raw);
-  const int64_t row = blockIdx.x;
-  const int T = blockDim.x, tid = threadIdx.x;
-  const int N = q * m;
-  float2* acc = sm;
-  float2* buf = sm + acc_slots(Lr);
-  const float2* src[2] = {F + row * Lr, G + row * Lr};
-  for (int j = tid; j < Lr; j += T) acc[j] = make_float2(0.f, 0.f);
-  __syncthreads();
-  for (int r = 0; r < q; ++r) {
-    for (int idx = tid; idx < 2 * m; idx += T) {
-      const int arr = idx / m, s = idx - arr * m;
-      const float2* x = src[arr];
-      float2 sum = make_float2(0.f, 0.f);
-      int e = r * s;
-      for (int t = 0; t < p; ++t) {
-        const int j = t * m + s;
-        if (j >= Lr) break;
-        sum = cadd(sum, cmul(x[j], tw_get<1>(tw, e)));
-        e += r * m;
-        if (e >= N) e -= N;
-      }
-      buf[idx] = sum;
-    }
-    __syncthreads();
-    cta_fft<1, PTS>(buf, m, 2, pl, tw, q);
-    for (int l = tid; l < m; l += T) buf[l] = cmul(buf[l], buf[m + l]);
-    __syncthreads();
-    cta_fft<-1, PTS>(buf, m, 1, pl, tw, q);
-    for (int j = tid; j < Lr; j += T) acc[j] = cadd(acc[j], cmul(buf[j % m], tw_get<-1>(tw, modmul(r, j, N))));
-    __syncthreads();
-  }
-  for (int j = tid; j < Lr; j += T) F[row * Lr + j] = cscale(acc[j], scale);
-}
 
 // ---------------------------------------------------------------------------
 // explicit baselines
@@ -582,78 +53,6 @@ __global__ void k_pad(const float* __restrict__ f, void* P, int d, int64_t L0, i
         if (c0 + 1 < L2) v.y = f[(a * L1 + b) * L2 + c0 + 1];
       }
       reinterpret_cast<float2*>(P)[i] = v;
-    }
-  }
-}
-
-// Row DFTs along the last dimension of length n (complex).  Modes:
-//   0 R2C  : src real row of 2n (padded), pack, DFT(+), unpack U -> n+1 bins
-//   1 C2R  : src n+1 bins, U^{-1}, DFT(-), unpack to 2n reals, keep Lkeep,
-//            scaled; rows with outer index beyond the crop are skipped
-//   2 C2C  : src complex row of n, DFT(+), in place
-//   3 C2RU : src complex row of n, DFT(-), unpack to reals, keep Lkeep, scaled
-struct RowsIO {
-  const void* src;
-  void* dst;
-  int64_t src_stride, dst_stride;  // elements (float for real, float2 for complex)
-  int Lkeep;                       // real outputs kept per row (modes 1, 3)
-  int64_t crop_rows_outer[2];      // outer extents of padded rows (M0, M1) ...
-  int64_t keep_rows_outer[2];      // ... and of the kept rows (L0, L1)
-  float scale;
-};
-
-template <int PTS>
-__global__ void __launch_bounds__(1024) k_rows_fft(RowsIO io, int mode, int n, const float2* __restrict__ tw,
-                                                   int twmul, FftPlan pl) {
-  extern __shared__ float4 smem_raw[];
-  float2* buf = reinterpret_cast<float2*>(smem_raw);
-  const int64_t row = blockIdx.x;
-  const int T = blockDim.x, tid = threadIdx.x;
-  // output row (modes 1, 3 crop the outer dimensions)
-  int64_t orow = row;
-  if (mode == 1 || mode == 3) {
-    const int64_t M1 = io.crop_rows_outer[1];
-    const int64_t a = row / M1, b = row - a * M1;
-    if (a >= io.keep_rows_outer[0] || b >= io.keep_rows_outer[1]) return;
-    orow = a * io.keep_rows_outer[1] + b;
-  }
-  // load
-  if (mode == 0) {
-    const float* s = reinterpret_cast<const float*>(io.src) + row * io.src_stride;
-    for (int j = tid; j < n; j += T) buf[j] = make_float2(s[2 * j], s[2 * j + 1]);
-  } else if (mode == 1) {
-    const float2* s = reinterpret_cast<const float2*>(io.src) + row * io.src_stride;
-    // Eq. fourierPack: Z_k = 1/2 (H_k + conj H_{n-k}) + i/2 (H_k - conj H_{n-k}) zeta_{2n}^{-k}
-    for (int k = tid; k < n; k += T) {
-      const float2 hk = s[k], hc = cconj(s[n - k]);
-      const float2 w = tw_get<-1>(tw, k * twmul / 2);
-      buf[k] = cscale(cadd(cadd(hk, hc), cmul_i<1>(cmul(csub(hk, hc), w))), 0.5f);
-    }
-  } else {
-    const float2* s = reinterpret_cast<const float2*>(io.src) + row * io.src_stride;
-    for (int j = tid; j < n; j += T) buf[j] = s[j];
-  }
-  __syncthreads();
-  if (mode == 0 || mode == 2)
-    cta_fft<1, PTS>(buf, n, 1, pl, tw, twmul);
-  else
-    cta_fft<-1, PTS>(buf, n, 1, pl, tw, twmul);
-  if (mode == 0) {
-    // Eq. fourierUnpack: F_k = 1/2 (Z_k + conj Z_{n-k}) - i/2 (Z_k - conj Z_{n-k}) zeta_{2n}^k, k = 0..n
-    float2* d = reinterpret_cast<float2*>(io.dst) + row * io.dst_stride;
-    for (int k = tid; k <= n; k += T) {
-      const float2 zk = buf[k % n], zc = cconj(buf[(n - k) % n]);
-      const float2 w = tw_get<1>(tw, (k % (2 * n)) * twmul / 2);
-      d[k] = cscale(csub(cadd(zk, zc), cmul_i<1>(cmul(csub(zk, zc), w))), 0.5f);
-    }
-  } else if (mode == 2) {
-    float2* d = reinterpret_cast<float2*>(io.dst) + row * io.dst_stride;
-    for (int j = tid; j < n; j += T) d[j] = buf[j];
-  } else {
-    float* d = reinterpret_cast<float*>(io.dst) + orow * (int64_t)io.Lkeep;
-    for (int j = tid; j < io.Lkeep; j += T) {
-      const float2 v = buf[j >> 1];
-      d[j] = ((j & 1) ? v.y : v.x) * io.scale;
     }
   }
 }
@@ -686,25 +85,28 @@ __global__ void k_rcm_nd(float2* __restrict__ A, const float2* __restrict__ B, i
 // ---------------------------------------------------------------------------
 // host drivers
 // ---------------------------------------------------------------------------
-template <typename K>
-static cudaError_t allow(K kernel, size_t smem) {
-  if (smem <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
+#define HD_TRY(call)                                    \
+  do {                                                  \
+    if ((call) != cudaSuccess) return HD_ECUDA;         \
+  } while (0)
 
 static int elementwise_blocks(int64_t n) {
   int64_t b = (n + 255) / 256;
   return (int)std::min<int64_t>(b, 148 * 32);
 }
 
-// Choose W columns per CTA for a column pass: shared memory per column
-// `per_col` bytes and points per column `pts`; W <= 8, W even if `even`.
-static int choose_W(size_t per_col, int pts, int64_t B, size_t max_smem, bool even,
-                    int64_t max_points = (int64_t)kPts * 1024) {
+// Choose W columns per CTA for a column pass over A blocks of B columns:
+// shared memory per column `per_col` bytes and points per column `pts`;
+// W <= 8, W even if `even`; then halved while the grid is under two CTAs per
+// SM (wide column groups on few SMs leave most of the GPU idle).
+static int choose_W(size_t per_col, int pts, int64_t A, int64_t B, size_t max_smem, bool even, int64_t max_pts,
+                    int num_sms) {
   int W = 8;
-  while (W > 1 && ((size_t)W * per_col > max_smem || (int64_t)W * pts > max_points)) W >>= 1;
+  while (W > 1 && ((size_t)W * per_col > max_smem || (int64_t)W * pts > max_pts)) W >>= 1;
   if (even && W < 2) W = 2;
   if ((int64_t)W > B && !even) W = (int)std::max<int64_t>(1, B);
+  const int wmin = even ? 2 : 1;
+  while (W > wmin && A * ((B + W - 1) / W) < 2 * (int64_t)std::max(num_sms, 1)) W >>= 1;
   return W;
 }
 
@@ -714,50 +116,34 @@ struct ColPass {
   FftPlan pl;
 };
 
-// Points one CTA may transform at once: kPts per thread up to 1024 threads, or
-// up to 512 threads for the tensor-core instantiation (128 registers).
-static int64_t max_points(bool tc) { return (int64_t)kPts * (tc ? 512 : 1024); }
-
 static hd_status col_fwd(hd_ctx* c, const void* X, int in_mode, int Lreal, float2* Y, int64_t A, int Lin, int64_t B,
                          const ColPass& cp, cudaStream_t st, int64_t Bp = 0, bool tc = false) {
   const bool keep = cp.q > 1;
+  const Eng eng = pick_eng(tc, struct_length(cp.m) && cp.q <= 2);
   const size_t per_col = sizeof(float2) * ((keep ? (size_t)Lin : 0) + (size_t)cp.m) + 16;
-  const int W = choose_W(per_col, cp.m, B, (size_t)c->max_smem, false, max_points(tc));
+  const int W = choose_W(per_col, cp.m, A, B, (size_t)c->max_smem, false, max_points(eng), c->num_sms);
   ColGeom cg{A, B, W, Bp > 0 ? Bp : B};
   const size_t smem = sizeof(float2) * ((keep ? (size_t)acc_slots(W * Lin) : 0) + (size_t)W * cp.m);
-  if (smem > (size_t)c->max_smem || (int64_t)W * cp.m > max_points(tc)) return HD_EUNSUPPORTED;
-  const int T = threads_for_points((int64_t)W * cp.m, kPts);
-  const int64_t grid = A * ((B + W - 1) / W);
-  if (tc) {
-    if (allow(k_col_fwd<kPts, true>, smem) != cudaSuccess) return HD_ECUDA;
-    k_col_fwd<kPts, true><<<(unsigned)grid, T, smem, st>>>(X, Y, cg, Lin, cp.m, cp.q, cp.p, in_mode, Lreal, cp.tw,
-                                                           cp.pl);
-  } else {
-    if (allow(k_col_fwd<kPts>, smem) != cudaSuccess) return HD_ECUDA;
-    k_col_fwd<kPts><<<(unsigned)grid, T, smem, st>>>(X, Y, cg, Lin, cp.m, cp.q, cp.p, in_mode, Lreal, cp.tw, cp.pl);
-  }
-  return cudaGetLastError() == cudaSuccess ? HD_OK : HD_ECUDA;
+  if (smem > (size_t)c->max_smem || (int64_t)W * cp.m > max_points(eng)) return HD_EUNSUPPORTED;
+  const int T = eng_threads(eng, (int64_t)W * cp.m);
+  const unsigned grid = (unsigned)(A * ((B + W - 1) / W));
+  HD_TRY(launch_col_fwd(eng, grid, T, smem, st, X, Y, cg, Lin, cp.m, cp.q, cp.p, in_mode, Lreal, cp.tw, cp.pl));
+  return HD_OK;
 }
 
 static hd_status col_bwd(hd_ctx* c, const float2* Y, void* Z, int out_mode, int Lreal, int64_t A, int Lout, int64_t B,
                          const ColPass& cp, float scale, cudaStream_t st, int64_t Bp = 0, bool tc = false) {
   const bool sep = cp.q > 1 || Lout > cp.m;
+  const Eng eng = pick_eng(tc, struct_length(cp.m) && cp.q <= 2);
   const size_t per_col = sizeof(float2) * ((sep ? (size_t)Lout : 0) + (size_t)cp.m) + 16;
-  const int W = choose_W(per_col, cp.m, B, (size_t)c->max_smem, false, max_points(tc));
+  const int W = choose_W(per_col, cp.m, A, B, (size_t)c->max_smem, false, max_points(eng), c->num_sms);
   ColGeom cg{A, B, W, Bp > 0 ? Bp : B};
   const size_t smem = sizeof(float2) * ((sep ? (size_t)acc_slots(W * Lout) : 0) + (size_t)W * cp.m);
-  if (smem > (size_t)c->max_smem || (int64_t)W * cp.m > max_points(tc)) return HD_EUNSUPPORTED;
-  const int T = threads_for_points((int64_t)W * cp.m, kPts);
-  const int64_t grid = A * ((B + W - 1) / W);
-  if (tc) {
-    if (allow(k_col_bwd<kPts, true>, smem) != cudaSuccess) return HD_ECUDA;
-    k_col_bwd<kPts, true><<<(unsigned)grid, T, smem, st>>>(Y, Z, cg, Lout, cp.m, cp.q, out_mode, Lreal, scale, cp.tw,
-                                                           cp.pl);
-  } else {
-    if (allow(k_col_bwd<kPts>, smem) != cudaSuccess) return HD_ECUDA;
-    k_col_bwd<kPts><<<(unsigned)grid, T, smem, st>>>(Y, Z, cg, Lout, cp.m, cp.q, out_mode, Lreal, scale, cp.tw, cp.pl);
-  }
-  return cudaGetLastError() == cudaSuccess ? HD_OK : HD_ECUDA;
+  if (smem > (size_t)c->max_smem || (int64_t)W * cp.m > max_points(eng)) return HD_EUNSUPPORTED;
+  const int T = eng_threads(eng, (int64_t)W * cp.m);
+  const unsigned grid = (unsigned)(A * ((B + W - 1) / W));
+  HD_TRY(launch_col_bwd(eng, grid, T, smem, st, Y, Z, cg, Lout, cp.m, cp.q, out_mode, Lreal, scale, cp.tw, cp.pl));
+  return HD_OK;
 }
 
 // Hybrid parameters of an outer (complex) dimension of real length L.
@@ -768,7 +154,7 @@ static hd_status outer_params(hd_ctx* c, int64_t L, const hd_dim_params* prm, Co
     q = prm->q > 0 ? prm->q : (2 * L - 1 + m - 1) / m;
     if (q * m < 2 * L - 1) return HD_EINVAL;
   } else {
-    m = next_smooth(L);
+    m = ladder_ceil(L);
     q = 2;
   }
   if (m > (int64_t)kPts * 1024) return HD_EUNSUPPORTED;
@@ -793,7 +179,7 @@ static hd_status row_params(hd_ctx* c, int64_t L, bool packed, const hd_dim_para
     q = prm->q > 0 ? prm->q : (need + m - 1) / m;
     if (q * m < need) return HD_EINVAL;
   } else {
-    m = next_smooth(Lr);
+    m = ladder_ceil(Lr);
     q = (need + m - 1) / m;
   }
   cp->m = (int)m;
@@ -854,17 +240,15 @@ static hd_status hybrid_rcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_
     rg.om[1] = outer[1].m;
     rg.oq[1] = outer[1].q;
   }
-  const size_t smem = sizeof(float2) * ((size_t)acc_slots(2 * (int)Lp) + 8 * (size_t)row.m);
-  if (smem > (size_t)c->max_smem || 8 * (int64_t)row.m > max_points(tc)) return HD_EUNSUPPORTED;
-  const int T = threads_for_points(8 * (int64_t)row.m, kPts);
-  if (tc) {
-    if (allow(k_rows_rcm<kPts, true>, smem) != cudaSuccess) return HD_ECUDA;
-    k_rows_rcm<kPts, true><<<rg.nrows, T, smem, st>>>(SF, SG, rg, 1.0f / (float)(row.q * row.m), row.tw, row.pl);
-  } else {
-    if (allow(k_rows_rcm<kPts>, smem) != cudaSuccess) return HD_ECUDA;
-    k_rows_rcm<kPts><<<rg.nrows, T, smem, st>>>(SF, SG, rg, 1.0f / (float)(row.q * row.m), row.tw, row.pl);
-  }
-  if (cudaGetLastError() != cudaSuccess) return HD_ECUDA;
+  // arrays per residue step: {A, C, B, D} x (1 or 2 residues); with q <= 2
+  // every residue is its own partner, so 4
+  const int narr = row.q <= 2 ? 4 : 8;
+  const Eng reng = pick_eng(tc, struct_length(row.m) && row.q <= 2);
+  const size_t smem = sizeof(float2) * ((size_t)acc_slots(2 * (int)Lp) + narr * (size_t)row.m);
+  if (smem > (size_t)c->max_smem || narr * (int64_t)row.m > max_points(reng)) return HD_EUNSUPPORTED;
+  const int T = eng_threads(reng, narr * (int64_t)row.m);
+  HD_TRY(launch_rows_rcm(reng, (unsigned)rg.nrows, T, smem, st, SF, SG, rg, 1.0f / (float)(row.q * row.m), row.tw,
+             row.pl));
   // backward along the outer dimensions, unpacking at the end
   if (d == 2) {
     s = col_bwd(c, SF, h, OUT_UNPACK_REAL, (int)Ln, 1, (int)L[0], Lp, outer[0], 1.0f / (float)M0, st, 0, tc);
@@ -887,8 +271,8 @@ static hd_status hybrid_cs_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_p
     q0 = prm[0].q > 0 ? prm[0].q : (2 * L[0] - 1 + m0 - 1) / m0;
     if (q0 * m0 < 2 * L[0] - 1 || (q0 % 2 == 0 && m0 % 2 == 1)) return HD_EINVAL;
   } else {
-    m0 = next_smooth(L[0]);
-    while (m0 % 2) m0 = next_smooth(m0 + 1);
+    m0 = ladder_ceil(L[0]);
+    while (m0 % 2) m0 = ladder_ceil(m0 + 1);
     q0 = 2;
   }
   if (m0 % 2) return HD_EUNSUPPORTED;  // residue 0 pairs columns through an even-length real DFT
@@ -918,20 +302,22 @@ static hd_status hybrid_cs_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_p
   float2* SG = SF + spec;
   float2* TF = SG + spec;
   float2* TG = TF + tmp;
-  // first dimension: real columns (W even)
+  // first dimension: real columns (W even); the structured engine needs both
+  // the length-m residue-0 DFT and the length-m/2 residue-q/2 DFT on the ladder
+  const Eng eng0 = pick_eng(false, q0 == 2 && struct_length((int)m0) && struct_length((int)(m0 / 2)));
+  const size_t per_col0 = sizeof(float) * (size_t)L[0] + sizeof(float2) * (size_t)m0 + 16;
+  const int W0 = choose_W(per_col0, (int)m0, 1, B0, (size_t)c->max_smem, true, max_points(eng0), c->num_sms);
+  const size_t smem0 = sizeof(float2) * ((size_t)acc_slots((W0 * (int)L[0] + 1) / 2) + (size_t)W0 * m0);
+  if (smem0 > (size_t)c->max_smem || (int64_t)W0 * m0 > max_points(eng0)) return HD_EUNSUPPORTED;
+  const int T0 = eng_threads(eng0, (int64_t)W0 * m0);
+  const unsigned grid0 = (unsigned)((B0 + W0 - 1) / W0);
   {
-    const size_t per_col = sizeof(float) * (size_t)L[0] + sizeof(float2) * (size_t)m0 + 16;
-    const int W = choose_W(per_col, (int)m0, B0, (size_t)c->max_smem, true);
-    const size_t smem = sizeof(float2) * ((size_t)acc_slots((W * (int)L[0] + 1) / 2) + (size_t)W * m0);
-    if (smem > (size_t)c->max_smem || (int64_t)W * m0 > (int64_t)kPts * 1024) return HD_EUNSUPPORTED;
-    const int T = threads_for_points((int64_t)W * m0, kPts);
-    const int64_t grid = (B0 + W - 1) / W;
-    if (allow(k_col_fwd_cs<kPts>, smem) != cudaSuccess) return HD_ECUDA;
     float2* outF = d == 3 ? TF : SF;
     float2* outG = d == 3 ? TG : SG;
-    k_col_fwd_cs<kPts><<<(unsigned)grid, T, smem, st>>>(f, outF, B0, W, (int)L[0], (int)m0, (int)q0, p0, tw0, pm0, ph0);
-    k_col_fwd_cs<kPts><<<(unsigned)grid, T, smem, st>>>(g, outG, B0, W, (int)L[0], (int)m0, (int)q0, p0, tw0, pm0, ph0);
-    if (cudaGetLastError() != cudaSuccess) return HD_ECUDA;
+    HD_TRY(launch_col_fwd_cs(eng0, grid0, T0, smem0, st, f, outF, B0, W0, (int)L[0], (int)m0, (int)q0, p0, tw0, pm0,
+               ph0));
+    HD_TRY(launch_col_fwd_cs(eng0, grid0, T0, smem0, st, g, outG, B0, W0, (int)L[0], (int)m0, (int)q0, p0, tw0, pm0,
+               ph0));
   }
   if (d == 3) {
     s = col_fwd(c, TF, IN_COMPLEX, 0, SF, R0, (int)L[1], Lr, mid, st);
@@ -940,13 +326,12 @@ static hd_status hybrid_cs_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_p
   }
   {
     const int64_t nrows = (int64_t)R0 * (d == 3 ? M1 : 1);
+    const Eng reng = pick_eng(false, struct_length(row.m) && row.q <= 2);
     const size_t smem = sizeof(float2) * ((size_t)acc_slots((int)Lr) + 2 * (size_t)row.m);
-    if (smem > (size_t)c->max_smem || 2 * (int64_t)row.m > (int64_t)kPts * 1024) return HD_EUNSUPPORTED;
-    const int T = threads_for_points(2 * (int64_t)row.m, kPts);
-    if (allow(k_rows_cconv<kPts>, smem) != cudaSuccess) return HD_ECUDA;
-    k_rows_cconv<kPts><<<(unsigned)nrows, T, smem, st>>>(SF, SG, (int)Lr, row.m, row.q, row.p,
-                                                         1.0f / (float)(row.q * row.m), row.tw, row.pl);
-    if (cudaGetLastError() != cudaSuccess) return HD_ECUDA;
+    if (smem > (size_t)c->max_smem || 2 * (int64_t)row.m > max_points(reng)) return HD_EUNSUPPORTED;
+    const int T = eng_threads(reng, 2 * (int64_t)row.m);
+    HD_TRY(launch_rows_cconv(reng, (unsigned)nrows, T, smem, st, SF, SG, (int)Lr, row.m, row.q, row.p,
+               1.0f / (float)(row.q * row.m), row.tw, row.pl));
   }
   if (d == 3) {
     s = col_bwd(c, SF, TF, OUT_COMPLEX, 0, R0, (int)L[1], Lr, mid, 1.0f / (float)M1, st);
@@ -954,16 +339,8 @@ static hd_status hybrid_cs_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_p
   }
   {
     const float2* src = d == 3 ? TF : SF;
-    const size_t per_col = sizeof(float) * (size_t)L[0] + sizeof(float2) * (size_t)m0 + 16;
-    const int W = choose_W(per_col, (int)m0, B0, (size_t)c->max_smem, true);
-    const size_t smem = sizeof(float2) * ((size_t)acc_slots((W * (int)L[0] + 1) / 2) + (size_t)W * m0);
-    if (smem > (size_t)c->max_smem) return HD_EUNSUPPORTED;
-    const int T = threads_for_points((int64_t)W * m0, kPts);
-    const int64_t grid = (B0 + W - 1) / W;
-    if (allow(k_col_bwd_cs<kPts>, smem) != cudaSuccess) return HD_ECUDA;
-    k_col_bwd_cs<kPts><<<(unsigned)grid, T, smem, st>>>(src, h, B0, W, (int)L[0], (int)m0, (int)q0,
-                                                        1.0f / (float)(q0 * m0), tw0, pm0, ph0);
-    if (cudaGetLastError() != cudaSuccess) return HD_ECUDA;
+    HD_TRY(launch_col_bwd_cs(eng0, grid0, T0, smem0, st, src, h, B0, W0, (int)L[0], (int)m0, (int)q0,
+               1.0f / (float)(q0 * m0), tw0, pm0, ph0));
   }
   return HD_OK;
 }
@@ -972,15 +349,15 @@ hd_status explicit_nd(hd_ctx* c, hd_algo algo, int d, const int64_t* Lin, const 
                       cudaStream_t st) {
   // padded extents: 2L per dimension (real); explicitRCM packs the last one to
   // an even packed length (Alg. 4 needs it even)
-  // (each padded length is 2 x the next 2,3,5-smooth size >= L, so every DFT
-  // length factors into the register radices; any length >= 2L-1 dealiases)
+  // (each padded length is 2 x the smallest length {1, 3, 5, 9} x 2^a >= L, so
+  // every DFT runs on the structured engine; any length >= 2L-1 dealiases)
   int64_t L[3] = {1, 1, 1};
   for (int i = 0; i < d; ++i) L[3 - d + i] = Lin[i];
   const bool rcm = (algo == HD_EXPLICIT_RCM);
-  const int64_t Mo0 = d >= 3 ? 2 * next_smooth(L[0]) : 1, Mo1 = d >= 2 ? 2 * next_smooth(L[1]) : 1;
-  int64_t n = next_smooth(L[2]);  // complex length of the last-dim DFT (real padded length 2n)
+  const int64_t Mo0 = d >= 3 ? 2 * ladder_ceil(L[0]) : 1, Mo1 = d >= 2 ? 2 * ladder_ceil(L[1]) : 1;
+  int64_t n = ladder_ceil(L[2]);  // complex length of the last-dim DFT (real padded length 2n)
   if (rcm)
-    while (n % 2) n = next_smooth(n + 1);
+    while (n % 2) n = ladder_ceil(n + 1);
   const int64_t rows = Mo0 * Mo1;
   if (n > (int64_t)kPts * 1024) return HD_EUNSUPPORTED;
   const int64_t bins = rcm ? n : n + 1;                 // complex per row after the last-dim pass
@@ -1005,9 +382,9 @@ hd_status explicit_nd(hd_ctx* c, hd_algo algo, int d, const int64_t* Lin, const 
     k_pad<<<elementwise_blocks(tot), 256, 0, st>>>(g, PG, 3, L[0], L[1], L[2], Mo0, Mo1, rcm ? n : 2 * n, rcm ? 1 : 0);
   }
   // 2) last dimension
-  const int T = threads_for_points(n, kPts);
+  const Eng reng = pick_eng(false, struct_length((int)n));
+  const int T = eng_threads(reng, n);
   const size_t smem = sizeof(float2) * (size_t)n;
-  if (allow(k_rows_fft<kPts>, smem) != cudaSuccess) return HD_ECUDA;
   for (int a = 0; a < 2; ++a) {
     RowsIO io;
     std::memset(&io, 0, sizeof(io));
@@ -1015,9 +392,8 @@ hd_status explicit_nd(hd_ctx* c, hd_algo algo, int d, const int64_t* Lin, const 
     io.dst = a ? SG : SF;
     io.src_stride = rcm ? n : 2 * n;
     io.dst_stride = bins;
-    k_rows_fft<kPts><<<(unsigned)rows, T, smem, st>>>(io, rcm ? 2 : 0, (int)n, twl, 2, pln);
+    HD_TRY(launch_rows_fft(reng, (unsigned)rows, T, smem, st, io, rcm ? 2 : 0, (int)n, twl, 2, pln));
   }
-  if (cudaGetLastError() != cudaSuccess) return HD_ECUDA;
   // 3) outer dimensions: full-length complex DFTs (q = 1, m = 2L)
   ColPass cp[2];
   const int nouter = d - 1;
@@ -1073,9 +449,9 @@ hd_status explicit_nd(hd_ctx* c, hd_algo algo, int d, const int64_t* Lin, const 
     // the unnormalised inverse returns n Mo0 Mo1 times the convolution, for
     // both the real (pack after U^{-1}) and the packed (RCM) forms
     io.scale = (float)(1.0 / ((double)Mo0 * (double)Mo1 * (double)n));
-    k_rows_fft<kPts><<<(unsigned)rows, T, smem, st>>>(io, rcm ? 3 : 1, (int)n, twl, 2, pln);
+    HD_TRY(launch_rows_fft(reng, (unsigned)rows, T, smem, st, io, rcm ? 3 : 1, (int)n, twl, 2, pln));
   }
-  return cudaGetLastError() == cudaSuccess ? HD_OK : HD_ECUDA;
+  return HD_OK;
 }
 
 }  // namespace hd

@@ -7,6 +7,8 @@
 // serves all DFT lengths dividing N: zeta_n^x = tw[x N / n].
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 
@@ -137,6 +139,19 @@ int64_t next_smooth(int64_t n) {
   if (n < 1) n = 1;
   while (!smooth235(n)) ++n;
   return n;
+}
+
+// Smallest length {1, 3, 5, 9} x 2^a >= n: every such length factors into the
+// register radices 16/8/4/2 and one of 3, 5, 9 (the structured FFT engine).
+int64_t ladder_ceil(int64_t n) {
+  if (n < 1) n = 1;
+  int64_t best = INT64_MAX;
+  for (int64_t base : {1, 3, 5, 9}) {
+    int64_t x = base;
+    while (x < n) x *= 2;
+    best = std::min(best, x);
+  }
+  return best;
 }
 
 hd_status ensure_ws(hd_ctx* c, size_t bytes) {

@@ -28,9 +28,9 @@ def run(hd, f, g, prec):
     return h.cpu().numpy().astype(np.float64)
 
 
-# (shape, whether some DFT length of the default plan is a multiple of 16, so a
+# (shape, whether some DFT length of the default plan (ladder lengths) is a multiple of 16, so a
 # tensor-core pass runs)
-@pytest.mark.parametrize("shape,tc", [((16, 16), True), ((64, 64), True), ((100, 37), False), ((256, 256), True),
+@pytest.mark.parametrize("shape,tc", [((16, 16), True), ((64, 64), True), ((100, 37), True), ((256, 256), True),
                                       ((32, 32, 32), True), ((48, 40, 64), True), ((5, 6, 7), False)])
 def test_split_precision_small(hd, shape, tc):
     f, g = inputs.normal_pair(shape, seed=80 + len(shape))
