@@ -38,14 +38,19 @@ SEED_L, SEED_V = 2, 3
 WORKLOAD = "1D batched: 4096 real convolutions, L ~ U{500..70000} (seed 2), N(0,1) values (seed 3), FP32"
 
 
-def csrc_hash():
+# Sources compiled into the batched kernel's translation unit (the DRAM-traffic
+# record is valid only for these exact files).
+CLUSTER_SOURCES = ("hd_cluster.cu", "hd_cluster.cuh", "hd_fft_fast.cuh", "hd_fft.cuh", "hd_conv1d.cuh",
+                   "hd_internal.h")
+
+
+def csrc_hash(names=CLUSTER_SOURCES):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2608_14497_b300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(d, name), "rb") as fh:
-                h.update(name.encode())
-                h.update(fh.read())
+    for name in sorted(names):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

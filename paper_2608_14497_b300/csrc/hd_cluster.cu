@@ -41,16 +41,183 @@ namespace cg = cooperative_groups;
 
 namespace hd {
 
-// length-C DFT (C in {1, 2, 4, 8}) of v[0..C), in place.
-template <int SIGN>
-__device__ __forceinline__ void dft_small(float2* v, int C) {
-  if (C == 2) dft2<SIGN>(v[0], v[1]);
-  else if (C == 4) dft4<SIGN>(v[0], v[1], v[2], v[3]);
-  else if (C == 8) dft8<SIGN>(v);
-}
-
 __device__ __forceinline__ int res_owner(int r, int C) { return r < C ? r : (r == C ? 0 : 2 * C - r); }
 __device__ __forceinline__ int res_slot(int r, int C) { return r < C ? 0 : 1; }
+
+// Distributed shared memory through 32-bit shared::cluster addresses: the
+// address of `local` (a shared::cta address) in the shared memory of CTA
+// `rank` of the cluster, and 8-byte stores / loads there.
+__device__ __forceinline__ unsigned map_rank_u32(unsigned local, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster_f2(unsigned addr, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ float2 ld_cluster_f2(unsigned addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+
+// What the exchange phases of one CTA need.
+struct XCtx {
+  const float* f;
+  const float* g;
+  float* h;
+  int64_t off;
+  int L, Lp, m, p, Sm, s0, s1, rank0;
+  unsigned arr_local;     // shared::cta address of this CTA's F_a
+  const float2* tw;       // zeta_N^k, N = 2 C m
+};
+
+// zeta_N^{r s} for r < Q from two table reads: zeta_N^{(4a + b) s} = w4^a w1^b
+template <int Q>
+__device__ __forceinline__ void residue_twiddles_q(const float2* __restrict__ tw, int s, float2* wr) {
+  const float2 w1 = __ldg(tw + s);
+  float2 p1[4];
+  p1[0] = make_float2(1.f, 0.f);
+  p1[1] = w1;
+  p1[2] = cmul(w1, w1);
+  p1[3] = cmul(p1[2], w1);
+  if constexpr (Q <= 4) {
+#pragma unroll
+    for (int r = 0; r < Q; ++r) wr[r] = p1[r];
+  } else {
+    const float2 w4 = __ldg(tw + 4 * s);
+    float2 p4[4];
+    p4[0] = p1[0];
+    p4[1] = w4;
+    p4[2] = cmul(w4, w4);
+    p4[3] = cmul(p4[2], w4);
+#pragma unroll
+    for (int r = 0; r < Q; ++r) wr[r] = (r < 4) ? p1[r] : cmul(p4[r >> 2], p1[r & 3]);
+  }
+}
+
+template <int SIGN, int CC>
+__device__ __forceinline__ void dft_c(float2* v) {
+  if constexpr (CC == 2) dft2<SIGN>(v[0], v[1]);
+  else if constexpr (CC == 4) dft4<SIGN>(v[0], v[1], v[2], v[3]);
+  else if constexpr (CC == 8) dft8<SIGN>(v);
+}
+
+// s values each thread keeps in flight in the exchange phases (their loads
+// are all issued before any arithmetic): 8 / C, so p <= C inputs per array
+// and s stay within 16 loads.  C = 8 loads one array at a time (registers).
+template <int CC>
+constexpr int kSPerThread = CC >= 8 ? 1 : 8 / CC;
+
+// Phase 1 (Eq. forwardr, sum over t and the pre-twiddle) for C = CC: for each
+// s of this CTA's slice, the p packed inputs f~_{tm+s} (t < p <= C; zero for
+// C <= t < q) of f and of g, the q-point DFT over t as two length-C DFTs
+// (even and odd residues), times zeta_N^{rs}, stored into residue r's owner.
+template <int CC>
+__device__ __forceinline__ void scatter_phase(const XCtx& x) {
+  constexpr int Q = 2 * CC;
+  constexpr int U = kSPerThread<CC>;
+  constexpr bool PRE = CC < 8;  // load both arrays before the arithmetic
+  const int T = blockDim.x;
+  auto load = [&](int s, int which, float2* v) {
+    const float* src = (which ? x.g : x.f) + x.off;
+#pragma unroll
+    for (int t = 0; t < CC; ++t) {
+      const int j = t * x.m + s;
+      v[t] = make_float2(0.f, 0.f);
+      if (s < x.s1 && t < x.p && j < x.Lp)
+        v[t] = make_float2(__ldg(src + 2 * j), (2 * j + 1 < x.L) ? __ldg(src + 2 * j + 1) : 0.f);
+    }
+  };
+  for (int sb = x.s0 + (int)threadIdx.x; sb < x.s1; sb += U * T) {
+    float2 xv[U][PRE ? 2 : 1][CC];
+    if constexpr (PRE) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        load(sb + u * T, 0, xv[u][0]);
+        load(sb + u * T, 1, xv[u][1]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = sb + u * T;
+      if (s < x.s1) {
+        float2 wr[Q];
+        residue_twiddles_q<Q>(x.tw, s, wr);
+#pragma unroll
+        for (int which = 0; which < 2; ++which) {
+          float2* v = xv[u][PRE ? which : 0];
+          if constexpr (!PRE) load(s, which, v);
+          float2 e0[CC], e1[CC];
+#pragma unroll
+          for (int t = 0; t < CC; ++t) {
+            e0[t] = v[t];
+            e1[t] = (t > 0) ? cmul(v[t], __ldg(x.tw + (size_t)t * x.m)) : v[t];  // zeta_q^t x_t
+          }
+          dft_c<1, CC>(e0);
+          dft_c<1, CC>(e1);
+          const unsigned loc = x.arr_local + (unsigned)((which * 2 * x.Sm + s) * sizeof(float2));
+#pragma unroll
+          for (int r = 0; r < Q; ++r)
+            st_cluster_f2(map_rank_u32(loc + (unsigned)(res_slot(r, CC) * x.Sm * sizeof(float2)),
+                                       (unsigned)(x.rank0 + res_owner(r, CC))),
+                          cmul((r & 1) ? e1[r >> 1] : e0[r >> 1], wr[r]));
+        }
+      }
+    }
+  }
+}
+
+// Phase 3 (Eq. accumulation) for C = CC: w_r[s] of every residue from its
+// owner, times zeta_N^{-rs}, the backward q-point sum over r for the p needed
+// blocks t (two length-C DFTs), scaled by 1/N, unpacked to the real output.
+template <int CC>
+__device__ __forceinline__ void gather_phase(const XCtx& x) {
+  constexpr int Q = 2 * CC;
+  constexpr int U = kSPerThread<CC>;
+  const int T = blockDim.x;
+  const float sc = 1.0f / (float)(Q * x.m);
+  float* hi = x.h + x.off;
+  for (int sb = x.s0 + (int)threadIdx.x; sb < x.s1; sb += U * T) {
+    float2 yv[U][Q];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = sb + u * T;
+      const unsigned loc = x.arr_local + (unsigned)(s * sizeof(float2));
+#pragma unroll
+      for (int r = 0; r < Q; ++r)
+        yv[u][r] = (s < x.s1) ? ld_cluster_f2(map_rank_u32(loc + (unsigned)(res_slot(r, CC) * x.Sm * sizeof(float2)),
+                                                           (unsigned)(x.rank0 + res_owner(r, CC))))
+                              : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = sb + u * T;
+      if (s < x.s1) {
+        float2 wr[Q];
+        residue_twiddles_q<Q>(x.tw, s, wr);
+        float2 e0[CC], e1[CC];
+#pragma unroll
+        for (int r = 0; r < Q; ++r) {
+          const float2 w = cmul(yv[u][r], cconj(wr[r]));
+          if (r & 1) e1[r >> 1] = w;
+          else e0[r >> 1] = w;
+        }
+        dft_c<-1, CC>(e0);
+        dft_c<-1, CC>(e1);
+#pragma unroll
+        for (int t = 0; t < CC; ++t) {
+          const int j = t * x.m + s;
+          if (t < x.p && j < x.Lp) {
+            const float2 o = (t > 0) ? cadd(e0[t], cmul(e1[t], cconj(__ldg(x.tw + (size_t)t * x.m)))) : cadd(e0[0], e1[0]);
+            hi[2 * j] = o.x * sc;
+            if (2 * j + 1 < x.L) hi[2 * j + 1] = o.y * sc;
+          }
+        }
+      }
+    }
+  }
+}
 
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads, 1)
     k_rcm1d_cluster(ClusterLaunch cl, const float* f, const float* g, float* h) {
@@ -66,14 +233,14 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
   CItem it;
   if (active) it = cl.items ? cl.items[u.first + sub] : cl.one_item;
   const int m = active ? it.m : 1;
-  const int q = 2 * C, N = q * m;
+  const int q = 2 * C;
   const int Sm = swz_stride(m);
   float2* tws = sm;                 // per-pass twiddles of the length-m DFT (m - 1 entries)
-  float2* arr = sm + swz_stride(m);  // F_a, F_b, G_a, G_b, each Sm long, swizzled
+  float2* arr = sm + swz_stride(m);  // F_a, F_b, G_a, G_b, each Sm long, natural order
   const float2* __restrict__ tw = active ? it.tw : nullptr;  // zeta_N^k
-  if (active) fill_pass_twiddles(tws, m, it.tabm);
-  // every CTA of the cluster is running (and has its table) before any
-  // distributed-shared-memory traffic
+  // the table copy overlaps phase 1 (waited for before the phase-2 barrier)
+  if (active) fill_pass_twiddles_async(tws, m, it.tabm);
+  // every CTA of the cluster is running before any distributed-shared-memory traffic
   cluster.sync();
 
   const int L = active ? it.L : 0;
@@ -82,66 +249,41 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
   const int chunk = (m + C - 1) / C;
   const int s0 = c * chunk, s1 = min(m, s0 + chunk);
   const int rank0 = sub * C;
-
-  // zeta_N^{r s} for r < q from two table reads: zeta_N^{4a + b} s = w4^a w1^b
-  auto residue_twiddles = [&](int s, float2* wr) {
-    const float2 w1 = __ldg(tw + s);
-    float2 p1[4], p4[4];
-    p1[0] = make_float2(1.f, 0.f);
-    p1[1] = w1;
-    p1[2] = cmul(w1, w1);
-    p1[3] = cmul(p1[2], w1);
-    p4[0] = p1[0];
-    if (q > 4) {
-      const float2 w4 = __ldg(tw + 4 * s);
-      p4[1] = w4;
-      p4[2] = cmul(w4, w4);
-      p4[3] = cmul(p4[2], w4);
-    } else {
-      p4[1] = p4[2] = p4[3] = p1[0];
-    }
-#pragma unroll
-    for (int r = 0; r < 16; ++r) wr[r] = (r < 4) ? p1[r] : cmul(p4[r >> 2], p1[r & 3]);
-  };
+  XCtx xc;
+  xc.f = f;
+  xc.g = g;
+  xc.h = h;
+  xc.off = active ? it.off : 0;
+  xc.L = L;
+  xc.Lp = Lp;
+  xc.m = m;
+  xc.p = p;
+  xc.Sm = Sm;
+  xc.s0 = s0;
+  xc.s1 = s1;
+  xc.rank0 = rank0;
+  xc.arr_local = (unsigned)__cvta_generic_to_shared(arr);
+  xc.tw = tw;
 
   // ---- phase 1: Eq. forwardr, sum over t and the pre-twiddle, scattered to owners
   if (active) {
-    for (int s = s0 + tid; s < s1; s += T) {
-      float2 wr[16];
-      residue_twiddles(s, wr);
-      for (int which = 0; which < 2; ++which) {
-        const float* x = (which ? g : f) + it.off;
-        float2 e0[8], e1[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          float2 v = make_float2(0.f, 0.f);
-          const int j = t * m + s;
-          if (t < p && j < Lp) v = make_float2(x[2 * j], (2 * j + 1 < L) ? x[2 * j + 1] : 0.f);
-          e0[t] = v;
-          e1[t] = (t < C && t > 0) ? cmul(v, __ldg(tw + (size_t)t * m)) : v;  // zeta_q^t x_t
-        }
-        dft_small<1>(e0, C);
-        dft_small<1>(e1, C);
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          if (r < q) {
-            const float2 y = cmul((r & 1) ? e1[r >> 1] : e0[r >> 1], wr[r]);
-            float2* dst = cluster.map_shared_rank(arr, rank0 + res_owner(r, C));
-            dst[(which * 2 + res_slot(r, C)) * Sm + swz(s)] = y;
-          }
-        }
-      }
+    switch (C) {
+      case 1: scatter_phase<1>(xc); break;
+      case 2: scatter_phase<2>(xc); break;
+      case 4: scatter_phase<4>(xc); break;
+      default: scatter_phase<8>(xc); break;
     }
   }
+  cp_async_wait_all();
   cluster.sync();
 
   // ---- phase 2: DFTs of the owned residues, RCM product, backward DFTs
   if (active) {
     if (4 * m <= kClusterPts * T) {
-      cta_fft_fast<1, kClusterPts>(arr, Sm, 4, m, tws);
+      cta_fft_struct<1, kClusterPts, true>(arr, Sm, 4, m, tws, 0);
     } else {
-      cta_fft_fast<1, kClusterPts>(arr, Sm, 2, m, tws);
-      cta_fft_fast<1, kClusterPts>(arr + 2 * Sm, Sm, 2, m, tws);
+      cta_fft_struct<1, kClusterPts, true>(arr, Sm, 2, m, tws, 0);
+      cta_fft_struct<1, kClusterPts, true>(arr + 2 * Sm, Sm, 2, m, tws, 0);
     }
     float2* Fa = arr;
     float2* Fb = arr + Sm;
@@ -169,48 +311,26 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
         Fs = Fb;
         Gs = Gb;
       }
-      const int il = swz(l), is = swz(ls);
-      const float2 A = Fl[il], B = Gl[il], Ac = Fs[is], Bc = Gs[is];
+      const float2 A = Fl[l], B = Gl[l], Ac = Fs[ls], Bc = Gs[ls];
       // zeta_N^{q l + r} = zeta_m^l zeta_N^r
       const float2 z = cmul(__ldg(it.tabm + (m - 1) + l), __ldg(tw + r));
       const float2 Z = make_float2(0.25f * (1.f + z.x), 0.25f * z.y);  // (1 + zeta_N^k) / 4
       const float2 alpha = cmul(cmul(csub(A, cconj(Ac)), csub(B, cconj(Bc))), Z);
-      Fl[il] = csub(cmul(A, B), alpha);
-      if (!(c == 0 && ls == l)) Fs[is] = csub(cmul(Ac, Bc), cconj(alpha));
+      Fl[l] = csub(cmul(A, B), alpha);
+      if (!(c == 0 && ls == l)) Fs[ls] = csub(cmul(Ac, Bc), cconj(alpha));
     }
     __syncthreads();
-    cta_fft_fast<-1, kClusterPts>(arr, Sm, 2, m, tws);
+    cta_fft_struct<-1, kClusterPts, true>(arr, Sm, 2, m, tws, 0);
   }
   cluster.sync();
 
   // ---- phase 3: Eq. accumulation, gathered from the owners
   if (active) {
-    const float sc = 1.0f / (float)N;
-    float* hi = h + it.off;
-    for (int s = s0 + tid; s < s1; s += T) {
-      float2 wr[16];
-      residue_twiddles(s, wr);
-      float2 e0[8], e1[8];
-#pragma unroll
-      for (int r = 0; r < 16; ++r) {
-        if (r < q) {
-          const float2* src = cluster.map_shared_rank(arr, rank0 + res_owner(r, C));
-          const float2 w = cmul(src[res_slot(r, C) * Sm + swz(s)], cconj(wr[r]));
-          if (r & 1) e1[r >> 1] = w;
-          else e0[r >> 1] = w;
-        }
-      }
-      dft_small<-1>(e0, C);
-      dft_small<-1>(e1, C);
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int j = t * m + s;
-        if (t < p && j < Lp) {
-          const float2 o = (t > 0) ? cadd(e0[t], cmul(e1[t], cconj(__ldg(tw + (size_t)t * m)))) : cadd(e0[0], e1[0]);
-          hi[2 * j] = o.x * sc;
-          if (2 * j + 1 < L) hi[2 * j + 1] = o.y * sc;
-        }
-      }
+    switch (C) {
+      case 1: gather_phase<1>(xc); break;
+      case 2: gather_phase<2>(xc); break;
+      case 4: gather_phase<4>(xc); break;
+      default: gather_phase<8>(xc); break;
     }
   }
   // no CTA leaves while others may still read its shared memory
@@ -220,13 +340,14 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// Candidate DFT lengths: {1, 3, 5, 9} x 2^a up to the cap (few distinct
-// lengths, so twiddle tables are shared across a batch and stay in L2).
+// Candidate DFT lengths: {1, 3, 5, 9} x 2^a with a >= 4 (the lengths of the
+// structured engine, cta_fft_struct) up to the cap (few distinct lengths, so
+// twiddle tables are shared across a batch and stay in L2).
 static const std::vector<int>& ladder() {
   static std::vector<int> v;
   if (v.empty()) {
     for (int base : {1, 3, 5, 9})
-      for (int x = base; x <= kClusterMaxM; x *= 2) v.push_back(x);
+      for (int x = 16 * base; x <= kClusterMaxM; x *= 2) v.push_back(x);
     std::sort(v.begin(), v.end());
     v.erase(std::unique(v.begin(), v.end()), v.end());
   }

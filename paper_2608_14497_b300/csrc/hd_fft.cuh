@@ -472,7 +472,12 @@ __device__ __noinline__ void cta_fft(float2* base, int stride, int nbuf, const F
 // the values kept at swz(i) = i ^ ((i >> 4) & 15), a permutation inside each
 // aligned block of 16 values that sends those stores to distinct banks.
 // Index splits use a float reciprocal with one integer correction (exact for
-// numerators below 2^17), twiddles come from the zeta_N table as in fft_stage.
+// numerators below 2^17).  Twiddles: PASS_TW = false reads the zeta_N table
+// `tw` as fft_stage does (zeta_m^x = tw[x * twmul]); PASS_TW = true reads a
+// per-pass table (in shared memory) where pass (R, Ns) finds zeta_{Ns R}^{r jm}
+// at tw[(Ns - 1) + (r - 1) Ns + jm] (r = 1..R-1, jm < Ns; the offsets of the
+// passes telescope to a table of n - 1 entries, built by hd_tables_plan.cu in
+// the pass order of cta_fft_struct).
 // ---------------------------------------------------------------------------
 struct DivF {
   float rcp;
@@ -500,7 +505,7 @@ __host__ __device__ inline bool struct_length(int n) {
   return a2 >= 4 && (odd == 1 || odd == 3 || odd == 5 || odd == 9);
 }
 
-template <int R, int SIGN, int PTS, bool IN_SWZ, bool OUT_SWZ>
+template <int R, int SIGN, int PTS, bool IN_SWZ, bool OUT_SWZ, bool PASS_TW>
 __device__ __forceinline__ void gstage(float2* base, int stride, int nbuf, int n, int Ns,
                                        const float2* __restrict__ tw, int twmul) {
   constexpr int BPT = (PTS + R - 1) / R;
@@ -522,7 +527,16 @@ __device__ __forceinline__ void gstage(float2* base, int stride, int nbuf, int n
       for (int r = 0; r < R; ++r) v[b][r] = x[IN_SWZ ? swz(j + r * nb) : j + r * nb];
       if (Ns > 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw_get<SIGN>(tw, r * jm * twstep));
+        for (int r = 1; r < R; ++r) {
+          float2 w;
+          if constexpr (PASS_TW) {
+            w = tw[(Ns - 1) + (r - 1) * Ns + jm];
+            if (SIGN < 0) w.y = -w.y;
+          } else {
+            w = tw_get<SIGN>(tw, r * jm * twstep);
+          }
+          v[b][r] = cmul(v[b][r], w);
+        }
       }
     }
   }
@@ -546,56 +560,56 @@ __device__ __forceinline__ void gstage(float2* base, int stride, int nbuf, int n
 
 // The pass after the radix-16 ones: radix 8/4/2 for the rest of the power of
 // two (rem = a mod 4), else the odd radix; IN_SWZ when it is the second pass.
-template <int SIGN, int PTS, bool IN_SWZ>
+template <int SIGN, int PTS, bool IN_SWZ, bool PASS_TW>
 __device__ __forceinline__ void gstage_rem(float2* base, int stride, int nbuf, int n, int& Ns, int rem,
                                            const float2* __restrict__ tw, int twmul) {
   if (rem == 3) {
-    gstage<8, SIGN, PTS, IN_SWZ, false>(base, stride, nbuf, n, Ns, tw, twmul);
+    gstage<8, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul);
     Ns *= 8;
   } else if (rem == 2) {
-    gstage<4, SIGN, PTS, IN_SWZ, false>(base, stride, nbuf, n, Ns, tw, twmul);
+    gstage<4, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul);
     Ns *= 4;
   } else if (rem == 1) {
-    gstage<2, SIGN, PTS, IN_SWZ, false>(base, stride, nbuf, n, Ns, tw, twmul);
+    gstage<2, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul);
     Ns *= 2;
   }
 }
-template <int SIGN, int PTS, bool IN_SWZ>
+template <int SIGN, int PTS, bool IN_SWZ, bool PASS_TW>
 __device__ __forceinline__ void gstage_odd(float2* base, int stride, int nbuf, int n, int Ns, int odd,
                                            const float2* __restrict__ tw, int twmul) {
-  if (odd == 3) gstage<3, SIGN, PTS, IN_SWZ, false>(base, stride, nbuf, n, Ns, tw, twmul);
-  else if (odd == 5) gstage<5, SIGN, PTS, IN_SWZ, false>(base, stride, nbuf, n, Ns, tw, twmul);
-  else if (odd == 9) gstage<9, SIGN, PTS, IN_SWZ, false>(base, stride, nbuf, n, Ns, tw, twmul);
+  if (odd == 3) gstage<3, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul);
+  else if (odd == 5) gstage<5, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul);
+  else if (odd == 9) gstage<9, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul);
 }
 
 // Whole DFT of a struct_length n on nbuf arrays (base + a * stride), in place,
 // natural order in and out.  Requires nbuf * n <= PTS * blockDim.x.
-template <int SIGN, int PTS>
+template <int SIGN, int PTS, bool PASS_TW = false>
 __device__ __forceinline__ void cta_fft_struct(float2* base, int stride, int nbuf, int n,
                                                const float2* __restrict__ tw, int twmul) {
   const int a2 = __ffs(n) - 1;
   const int odd = n >> a2;
   const int n16 = a2 >> 2, rem = a2 & 3;
   if (n == 16) {
-    gstage<16, SIGN, PTS, false, false>(base, stride, nbuf, n, 1, tw, twmul);
+    gstage<16, SIGN, PTS, false, false, PASS_TW>(base, stride, nbuf, n, 1, tw, twmul);
     return;
   }
-  gstage<16, SIGN, PTS, false, true>(base, stride, nbuf, n, 1, tw, twmul);
+  gstage<16, SIGN, PTS, false, true, PASS_TW>(base, stride, nbuf, n, 1, tw, twmul);
   int Ns = 16;
   if (n16 >= 2) {
-    gstage<16, SIGN, PTS, true, false>(base, stride, nbuf, n, Ns, tw, twmul);
+    gstage<16, SIGN, PTS, true, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul);
     Ns *= 16;
     for (int i = 2; i < n16; ++i) {
-      gstage<16, SIGN, PTS, false, false>(base, stride, nbuf, n, Ns, tw, twmul);
+      gstage<16, SIGN, PTS, false, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul);
       Ns *= 16;
     }
-    gstage_rem<SIGN, PTS, false>(base, stride, nbuf, n, Ns, rem, tw, twmul);
-    gstage_odd<SIGN, PTS, false>(base, stride, nbuf, n, Ns, odd, tw, twmul);
+    gstage_rem<SIGN, PTS, false, PASS_TW>(base, stride, nbuf, n, Ns, rem, tw, twmul);
+    gstage_odd<SIGN, PTS, false, PASS_TW>(base, stride, nbuf, n, Ns, odd, tw, twmul);
   } else if (rem) {
-    gstage_rem<SIGN, PTS, true>(base, stride, nbuf, n, Ns, rem, tw, twmul);
-    gstage_odd<SIGN, PTS, false>(base, stride, nbuf, n, Ns, odd, tw, twmul);
+    gstage_rem<SIGN, PTS, true, PASS_TW>(base, stride, nbuf, n, Ns, rem, tw, twmul);
+    gstage_odd<SIGN, PTS, false, PASS_TW>(base, stride, nbuf, n, Ns, odd, tw, twmul);
   } else {
-    gstage_odd<SIGN, PTS, true>(base, stride, nbuf, n, Ns, odd, tw, twmul);
+    gstage_odd<SIGN, PTS, true, PASS_TW>(base, stride, nbuf, n, Ns, odd, tw, twmul);
   }
 }
 
