@@ -40,7 +40,8 @@ WORKLOAD = "1D batched: 4096 real convolutions, L ~ U{500..70000} (seed 2), N(0,
 
 # Sources compiled into the batched kernel's translation unit (the DRAM-traffic
 # record is valid only for these exact files).
-CLUSTER_SOURCES = ("hd_cluster.cu", "hd_cluster.cuh", "hd_fft_fast.cuh", "hd_fft.cuh", "hd_conv1d.cuh",
+CLUSTER_SOURCES = ("hd_cluster_kernel.cuh", "hd_cluster_c1.cu", "hd_cluster_c2.cu", "hd_cluster_c4.cu",
+                   "hd_cluster_c8.cu", "hd_cluster.cuh", "hd_fft_fast.cuh", "hd_fft.cuh", "hd_conv1d.cuh",
                    "hd_internal.h")
 
 
@@ -339,7 +340,8 @@ def run_gpu(args):
 
 
 def plan_launches(plan):
-    return 1
+    """Kernel launches per step: the plan's own count (one per cluster size in use)."""
+    return plan.launches
 
 
 def compare_suite(reps=10):

@@ -103,6 +103,11 @@ hd_status hd_batch_plan_create(hd_ctx* ctx, hd_algo algo, int32_t n, const int64
 hd_status hd_batch_plan_destroy(hd_batch_plan* plan);
 hd_status hd_conv1d_batched(hd_ctx* ctx, const hd_batch_plan* plan, const float* f, const float* g, float* h,
                             void* stream);
+/* Number of kernel launches one hd_conv1d_batched call of the plan enqueues
+ * (hybridRCM: one per cluster size in use, launched concurrently on streams
+ * forked from and joined back to `stream`; plus one for lengths outside the
+ * cluster kernel's range).  EINVAL on NULL arguments. */
+hd_status hd_batch_plan_launches(const hd_batch_plan* plan, int32_t* n);
 
 /* Adjoint of h = conv(f, g) (first L outputs per dimension) for `batch`
  * independent problems of extents Ls[0..ndim) stored back to back: given

@@ -27,7 +27,7 @@ PRECS = {"fp32": HD_FP32, "split_bf16": HD_SPLIT_BF16}
 EXPORTS = ("hd_create", "hd_destroy", "hd_conv1d", "hd_conv2d", "hd_conv3d", "hd_batch_plan_create",
            "hd_batch_plan_destroy", "hd_conv1d_batched", "hd_conv_adjoint", "hd_plan", "hd_last_device_error",
            "hd_strerror", "hd_last_error_string", "hd_conv1d_rcm_noalloc",
-           "hd_tuning_table")
+           "hd_tuning_table", "hd_batch_plan_launches")
 
 
 class HDError(RuntimeError):
@@ -74,6 +74,7 @@ def load(build_if_missing=False):
         "hd_last_error_string": ([], ctypes.c_char_p),
         "hd_conv1d_rcm_noalloc": ([P, P, P, I64, DP, P], I),
         "hd_tuning_table": ([P, I32, P, P, P, P], I),
+        "hd_batch_plan_launches": ([P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -301,6 +302,13 @@ class BatchPlan:
         _check(hd_conv1d_batched(self.ctx, self.handle, f.data_ptr(), g.data_ptr(), h.data_ptr(), _stream_ptr()),
                "conv1d_batched")
         return h
+
+    @property
+    def launches(self):
+        """Kernel launches one call of the plan enqueues."""
+        n = ctypes.c_int32(0)
+        _check(load().hd_batch_plan_launches(self.handle, ctypes.byref(n)), "hd_batch_plan_launches")
+        return n.value
 
     def __del__(self):
         if getattr(self, "handle", None) is not None and _lib is not None:

@@ -116,9 +116,6 @@ static hd_status conv1d_rcm_cluster(hd_ctx* c, const float* f, const float* g, f
   if (!tw) return fail(terr, "twiddle table allocation failed");
   ClusterLaunch cl;
   std::memset(&cl, 0, sizeof(cl));
-  cl.one_unit.first = 0;
-  cl.one_unit.count = 1;
-  cl.one_unit.C = C;
   cl.one_item.off = 0;
   cl.one_item.L = (int32_t)L;
   cl.one_item.m = m;
@@ -127,8 +124,7 @@ static hd_status conv1d_rcm_cluster(hd_ctx* c, const float* f, const float* g, f
   cl.one_item.tw = tw;
   cl.one_item.tabm = c->tables.get_pass_table(m, st, &terr);
   if (!cl.one_item.tabm) return fail(terr, "pass table allocation failed");
-  factor_radices(m, &cl.one_plan);
-  cudaError_t e = launch_rcm1d_cluster(cl, 1, cluster_smem_bytes(m), f, g, h, st);
+  cudaError_t e = launch_rcm1d_cluster(cl, C, 1, cluster_smem_bytes(m), f, g, h, st);
   if (e != cudaSuccess) return cuda_fail(e, "cluster launch");
   return HD_OK;
 }

@@ -5,10 +5,15 @@
 // empirical scan over m, Sec. 6), distinct DFT lengths share one radix plan,
 // distinct padded lengths N = qm share one twiddle table, and items are grouped
 // into one launch (block size and shared memory of the largest item), ordered
-// longest first so the block scheduler balances the tail.  Everything the kernels read (item table, radix
-// plans, tables, accumulator scratch) is uploaded or allocated here, so a
-// launch of the plan performs no allocation and no host-to-device copy and can
-// be captured in a CUDA graph.
+// longest first so the block scheduler balances the tail.  hybridRCM lengths
+// the cluster kernel covers form one class per cluster size C; the classes run
+// concurrently on streams forked from the caller's stream and joined back
+// (8-CTA clusters pack into the GPCs less densely than smaller ones, so the
+// smaller classes fill the SMs the C = 8 class cannot use; the C = 8 class
+// runs at the higher stream priority).  Everything the kernels read (item
+// table, radix plans, tables, accumulator scratch) is uploaded or allocated
+// here, so a launch of the plan performs no allocation and no host-to-device
+// copy and can be captured in a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +32,12 @@ struct LaunchClass {
   int threads = 0;
   size_t smem = 0;
 };
+struct ClusterClass {
+  int first = 0, count = 0;  // range in the device cluster item table
+  int C = 0;
+  size_t smem = 0;
+};
+constexpr int kMaxClusterClasses = 4;  // C in {8, 4, 2, 1}
 }  // namespace hd
 
 struct hd_batch_plan {
@@ -38,11 +49,12 @@ struct hd_batch_plan {
   void* d_acc = nullptr;
   std::vector<hd::LaunchClass> classes;
   int64_t total_len = 0;
-  // cluster path (hybridRCM): units of 8 CTAs
-  hd::CUnit* d_units = nullptr;
+  // cluster path (hybridRCM): one class per cluster size, concurrent streams
   hd::CItem* d_citems = nullptr;
-  int nunits = 0;
-  size_t csmem = 0;
+  std::vector<hd::ClusterClass> cclasses;
+  cudaStream_t side[hd::kMaxClusterClasses] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[hd::kMaxClusterClasses] = {};
 };
 
 using namespace hd;
@@ -75,7 +87,6 @@ extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, co
   // hybridRCM: every length the cluster kernel covers goes there
   std::vector<CItem> citems;
   std::vector<char> in_cluster(n, 0);
-  int m_max = 1;
   if (algo == HD_HYBRID_RCM) {
     // autotune the cluster kernel once per context (HD_AUTOTUNE=0 disables it)
     const char* at = getenv("HD_AUTOTUNE");
@@ -102,7 +113,6 @@ extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, co
       if (!ci.tabm) return terr;
       citems.push_back(ci);
       in_cluster[i] = 1;
-      m_max = std::max(m_max, m);
     }
   }
   for (int i = 0; i < n; ++i) {
@@ -157,36 +167,42 @@ extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, co
     lc.threads = std::max(lc.threads, hs[i].P.threads);
     lc.smem = std::max(lc.smem, hs[i].P.smem);
   }
-  // cluster units: by C (largest first), lengths descending, 8/C items per unit
-  std::vector<CUnit> units;
+  // cluster classes: by C (largest first), lengths descending within a class
   if (!citems.empty()) {
     std::stable_sort(citems.begin(), citems.end(), [](const CItem& a, const CItem& b) {
       if (a.C != b.C) return a.C > b.C;
       return a.L > b.L;
     });
-    for (size_t i = 0; i < citems.size();) {
-      const int C = citems[i].C;
-      const int per = kClusterCtas / C;
-      CUnit u;
-      std::memset(&u, 0, sizeof(u));
-      u.first = (int)i;
-      u.C = C;
-      while (i < citems.size() && citems[i].C == C && u.count < per) {
-        ++u.count;
-        ++i;
+    for (size_t i = 0; i < citems.size(); ++i) {
+      if (bp->cclasses.empty() || bp->cclasses.back().C != citems[i].C) {
+        ClusterClass k;
+        k.first = (int)i;
+        k.C = citems[i].C;
+        bp->cclasses.push_back(k);
       }
-      units.push_back(u);
+      ClusterClass& k = bp->cclasses.back();
+      ++k.count;
+      k.smem = std::max(k.smem, cluster_smem_bytes(citems[i].m));
+      bp->total_len += citems[i].L;
     }
-    for (const CItem& ci : citems) bp->total_len += ci.L;
-    bp->nunits = (int)units.size();
-    bp->csmem = cluster_smem_bytes(m_max);
-    if (cudaMalloc(&bp->d_units, sizeof(CUnit) * units.size()) != cudaSuccess ||
-        cudaMalloc(&bp->d_citems, sizeof(CItem) * citems.size()) != cudaSuccess) {
+    if (cudaMalloc(&bp->d_citems, sizeof(CItem) * citems.size()) != cudaSuccess) {
       hd_batch_plan_destroy(bp);
       return HD_ENOMEM;
     }
-    cudaMemcpy(bp->d_units, units.data(), sizeof(CUnit) * units.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(bp->d_citems, citems.data(), sizeof(CItem) * citems.size(), cudaMemcpyHostToDevice);
+    if (bp->cclasses.size() > 1) {
+      int lo = 0, hi = 0;
+      cudaDeviceGetStreamPriorityRange(&lo, &hi);
+      bool ok = cudaEventCreateWithFlags(&bp->fork, cudaEventDisableTiming) == cudaSuccess;
+      for (size_t k = 0; k < bp->cclasses.size() && ok; ++k) {
+        ok = cudaStreamCreateWithPriority(&bp->side[k], cudaStreamNonBlocking, k == 0 ? hi : lo) == cudaSuccess &&
+             cudaEventCreateWithFlags(&bp->join[k], cudaEventDisableTiming) == cudaSuccess;
+      }
+      if (!ok) {
+        hd_batch_plan_destroy(bp);
+        return HD_ECUDA;
+      }
+    }
   }
   if ((ng > 0 && cudaMalloc(&bp->d_items, sizeof(Item1D) * ng) != cudaSuccess) ||
       cudaMalloc(&bp->d_plans, sizeof(FftPlan) * std::max<size_t>(1, plans.size())) != cudaSuccess) {
@@ -210,8 +226,12 @@ extern "C" hd_status hd_batch_plan_destroy(hd_batch_plan* bp) {
   if (bp->d_items) cudaFree(bp->d_items);
   if (bp->d_plans) cudaFree(bp->d_plans);
   if (bp->d_acc) cudaFree(bp->d_acc);
-  if (bp->d_units) cudaFree(bp->d_units);
   if (bp->d_citems) cudaFree(bp->d_citems);
+  for (int k = 0; k < kMaxClusterClasses; ++k) {
+    if (bp->side[k]) cudaStreamDestroy(bp->side[k]);
+    if (bp->join[k]) cudaEventDestroy(bp->join[k]);
+  }
+  if (bp->fork) cudaEventDestroy(bp->fork);
   delete bp;
   return HD_OK;
 }
@@ -221,13 +241,28 @@ extern "C" hd_status hd_conv1d_batched(hd_ctx* c, const hd_batch_plan* bp, const
   if (!c || !bp || !f || !g || !h) return HD_EINVAL;
   cudaSetDevice(c->device);
   cudaStream_t st = (cudaStream_t)stream;
-  if (bp->nunits > 0) {
+  const int ncc = (int)bp->cclasses.size();
+  if (ncc == 1) {
+    const ClusterClass& k = bp->cclasses[0];
     ClusterLaunch cl;
     std::memset(&cl, 0, sizeof(cl));
-    cl.units = bp->d_units;
-    cl.items = bp->d_citems;
-    cl.plans = bp->d_plans;
-    if (launch_rcm1d_cluster(cl, bp->nunits, bp->csmem, f, g, h, st) != cudaSuccess) return HD_ECUDA;
+    cl.items = bp->d_citems + k.first;
+    if (launch_rcm1d_cluster(cl, k.C, k.count, k.smem, f, g, h, st) != cudaSuccess) return HD_ECUDA;
+  } else if (ncc > 1) {
+    // fork: every class on its own stream after the work already on `st`; join
+    if (cudaEventRecord(bp->fork, st) != cudaSuccess) return HD_ECUDA;
+    for (int i = 0; i < ncc; ++i) {
+      const ClusterClass& k = bp->cclasses[i];
+      ClusterLaunch cl;
+      std::memset(&cl, 0, sizeof(cl));
+      cl.items = bp->d_citems + k.first;
+      if (cudaStreamWaitEvent(bp->side[i], bp->fork, 0) != cudaSuccess ||
+          launch_rcm1d_cluster(cl, k.C, k.count, k.smem, f, g, h, bp->side[i]) != cudaSuccess ||
+          cudaEventRecord(bp->join[i], bp->side[i]) != cudaSuccess)
+        return HD_ECUDA;
+    }
+    for (int i = 0; i < ncc; ++i)
+      if (cudaStreamWaitEvent(st, bp->join[i], 0) != cudaSuccess) return HD_ECUDA;
   }
   for (const LaunchClass& lc : bp->classes) {
     Launch1D la;
@@ -238,6 +273,12 @@ extern "C" hd_status hd_conv1d_batched(hd_ctx* c, const hd_batch_plan* bp, const
                                                 : launch_cs1d(la, lc.count, lc.threads, lc.smem, f, g, h, st);
     if (e != cudaSuccess) return HD_ECUDA;
   }
+  return HD_OK;
+}
+
+extern "C" hd_status hd_batch_plan_launches(const hd_batch_plan* bp, int32_t* n) {
+  if (!bp || !n) return HD_EINVAL;
+  *n = (int32_t)(bp->cclasses.size() + bp->classes.size());
   return HD_OK;
 }
 

@@ -7,7 +7,7 @@
 
 namespace hd {
 
-constexpr int kClusterCtas = 8;       // CTAs per cluster
+constexpr int kClusterCtas = 8;       // largest cluster (C = 8 CTAs, q = 16 residues)
 constexpr int kClusterThreads = 512;  // threads per CTA
 constexpr int kClusterPts = 24;       // FFT points per thread per pass
 constexpr int kClusterMaxM = 4608;    // largest residue DFT length (shared memory)
@@ -22,18 +22,11 @@ struct CItem {
   const float2* tabm;  // per-length table: pass twiddles, then zeta_m^l (hd_fft_fast.cuh)
 };
 
-// A cluster's work: `count` (<= 8/C) consecutive items starting at `first`.
-struct CUnit {
-  int32_t first, count, C, pad_;
-};
-
+// Items of one launch (all of the same C, one cluster each), or one item by
+// value (items == nullptr).
 struct ClusterLaunch {
-  const CUnit* units;   // nullptr: one_unit / one_item / one_plan
   const CItem* items;
-  const FftPlan* plans;
-  CUnit one_unit;
   CItem one_item;
-  FftPlan one_plan;
 };
 
 // (C, m, p) for a length: the measured cheapest candidate when `tun` holds an
@@ -43,8 +36,16 @@ bool cluster_params(int64_t L, int* C, int* m, int* p, const ClusterTuning* tun 
 // Time every candidate on synthetic batches (device scratch, a few tens of MB).
 hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out);
 size_t cluster_smem_bytes(int m_max);
-cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int nunits, size_t smem, const float* f, const float* g,
-                                 float* h, cudaStream_t st);
-int cluster_max_active(size_t smem);
+// Launch over `nitems` convolutions of the same C (clusters of C CTAs).
+cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int C, int nitems, size_t smem, const float* f,
+                                 const float* g, float* h, cudaStream_t st);
+cudaError_t launch_cluster_c1(const ClusterLaunch& cl, int nitems, size_t smem, const float* f, const float* g,
+                              float* h, cudaStream_t st);
+cudaError_t launch_cluster_c2(const ClusterLaunch& cl, int nitems, size_t smem, const float* f, const float* g,
+                              float* h, cudaStream_t st);
+cudaError_t launch_cluster_c4(const ClusterLaunch& cl, int nitems, size_t smem, const float* f, const float* g,
+                              float* h, cudaStream_t st);
+cudaError_t launch_cluster_c8(const ClusterLaunch& cl, int nitems, size_t smem, const float* f, const float* g,
+                              float* h, cudaStream_t st);
 
 }  // namespace hd

@@ -1,0 +1,11 @@
+// hd_cluster_c1.cu -- instantiation of the cluster hybridRCM kernel for
+// clusters of 1 CTA (q = 2 residues); one file per cluster size so they
+// compile in parallel.
+#include "hd_cluster_kernel.cuh"
+
+namespace hd {
+cudaError_t launch_cluster_c1(const ClusterLaunch& cl, int nitems, size_t smem, const float* f, const float* g,
+                              float* h, cudaStream_t st) {
+  return launch_cluster_c<1>(cl, nitems, smem, f, g, h, st);
+}
+}  // namespace hd

@@ -66,3 +66,40 @@ def test_batched_full_workload_sampled(hd):
         assert rel_l2(hh[a:b], ref) <= TOL, (i, Ls[i])
     # untouched gaps: nothing outside the items (there are none here) and no NaN
     assert np.isfinite(hh).all()
+
+
+def test_autotune_table_matches_direct_timing(hd):
+    """The planner's cost table must describe real launches: the entry it picks
+    for L = 65536 (64 items, about the tuner's batch size) agrees with a CUDA-event
+    timing of the same batch within a factor of two."""
+    L, K = 65536, 64
+    Ls = np.full(K, L, dtype=np.int64)
+    off = np.arange(K, dtype=np.int64) * L
+    f = torch.randn(K * L, device="cuda")
+    g = torch.randn(K * L, device="cuda")
+    h = torch.empty_like(f)
+    plan = hd.BatchPlan(off, Ls, algo="hybridRCM")
+    tab = hd.hd_tuning_table(hd.context())
+    if not tab:
+        pytest.skip("autotuner disabled (HD_AUTOTUNE=0)")
+    assert all(us > 0 for _, _, us in tab)
+    # the planner's rule: cheapest of the three shortest feasible lengths per C
+    seen, best = {}, None
+    for C, m, us in tab:
+        if 2 * C * m < L or seen.get(C, 0) >= 3:
+            continue
+        seen[C] = seen.get(C, 0) + 1
+        if best is None or us < best[2]:
+            best = (C, m, us)
+    assert best is not None
+    for _ in range(3):
+        plan(f, g, out=h)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(10):
+        plan(f, g, out=h)
+    b.record()
+    torch.cuda.synchronize()
+    us_direct = 1e3 * a.elapsed_time(b) / (10 * K)
+    assert 0.5 <= us_direct / best[2] <= 2.0, (best, us_direct)
