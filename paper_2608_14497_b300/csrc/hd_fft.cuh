@@ -176,6 +176,85 @@ __device__ __forceinline__ void dft9(float2* a) {
 }
 
 template <int R, int SIGN>
+__device__ __forceinline__ void dft_reg(float2* v);
+
+// zeta_R^e = (cos, sin)(2 pi e / R), e < R, for the composite radices below
+// (FP32 roundings of the exact values).
+template <int R>
+__device__ __forceinline__ float2 unit_root(int e);
+template <>
+__device__ __forceinline__ float2 unit_root<6>(int e) {
+  const float c[6] = {1.0f, 0.5f, -0.5f, -1.0f, -0.5f, 0.5f};
+  const float s[6] = {0.0f, 0.866025404f, 0.866025404f, 0.0f, -0.866025404f, -0.866025404f};
+  return make_float2(c[e], s[e]);
+}
+template <>
+__device__ __forceinline__ float2 unit_root<10>(int e) {
+  const float c[10] = {1.0f, 0.809016994f, 0.309016994f, -0.309016994f, -0.809016994f, -1.0f, -0.809016994f, -0.309016994f, 0.309016994f, 0.809016994f};
+  const float s[10] = {0.0f, 0.587785252f, 0.951056516f, 0.951056516f, 0.587785252f, 0.0f, -0.587785252f, -0.951056516f, -0.951056516f, -0.587785252f};
+  return make_float2(c[e], s[e]);
+}
+template <>
+__device__ __forceinline__ float2 unit_root<12>(int e) {
+  const float c[12] = {1.0f, 0.866025404f, 0.5f, 0.0f, -0.5f, -0.866025404f, -1.0f, -0.866025404f, -0.5f, 0.0f, 0.5f, 0.866025404f};
+  const float s[12] = {0.0f, 0.5f, 0.866025404f, 1.0f, 0.866025404f, 0.5f, 0.0f, -0.5f, -0.866025404f, -1.0f, -0.866025404f, -0.5f};
+  return make_float2(c[e], s[e]);
+}
+template <>
+__device__ __forceinline__ float2 unit_root<18>(int e) {
+  const float c[18] = {1.0f, 0.939692621f, 0.766044443f, 0.5f, 0.173648178f, -0.173648178f, -0.5f, -0.766044443f, -0.939692621f, -1.0f, -0.939692621f, -0.766044443f, -0.5f, -0.173648178f, 0.173648178f, 0.5f, 0.766044443f, 0.939692621f};
+  const float s[18] = {0.0f, 0.342020143f, 0.64278761f, 0.866025404f, 0.984807753f, 0.984807753f, 0.866025404f, 0.64278761f, 0.342020143f, 0.0f, -0.342020143f, -0.64278761f, -0.866025404f, -0.984807753f, -0.984807753f, -0.866025404f, -0.64278761f, -0.342020143f};
+  return make_float2(c[e], s[e]);
+}
+template <>
+__device__ __forceinline__ float2 unit_root<20>(int e) {
+  const float c[20] = {1.0f, 0.951056516f, 0.809016994f, 0.587785252f, 0.309016994f, 0.0f, -0.309016994f, -0.587785252f, -0.809016994f, -0.951056516f, -1.0f, -0.951056516f, -0.809016994f, -0.587785252f, -0.309016994f, 0.0f, 0.309016994f, 0.587785252f, 0.809016994f, 0.951056516f};
+  const float s[20] = {0.0f, 0.309016994f, 0.587785252f, 0.809016994f, 0.951056516f, 1.0f, 0.951056516f, 0.809016994f, 0.587785252f, 0.309016994f, 0.0f, -0.309016994f, -0.587785252f, -0.809016994f, -0.951056516f, -1.0f, -0.951056516f, -0.809016994f, -0.587785252f, -0.309016994f};
+  return make_float2(c[e], s[e]);
+}
+template <>
+__device__ __forceinline__ float2 unit_root<24>(int e) {
+  const float c[24] = {1.0f, 0.965925826f, 0.866025404f, 0.707106781f, 0.5f, 0.258819045f, 0.0f, -0.258819045f, -0.5f, -0.707106781f, -0.866025404f, -0.965925826f, -1.0f, -0.965925826f, -0.866025404f, -0.707106781f, -0.5f, -0.258819045f, 0.0f, 0.258819045f, 0.5f, 0.707106781f, 0.866025404f, 0.965925826f};
+  const float s[24] = {0.0f, 0.258819045f, 0.5f, 0.707106781f, 0.866025404f, 0.965925826f, 1.0f, 0.965925826f, 0.866025404f, 0.707106781f, 0.5f, 0.258819045f, 0.0f, -0.258819045f, -0.5f, -0.707106781f, -0.866025404f, -0.965925826f, -1.0f, -0.965925826f, -0.866025404f, -0.707106781f, -0.5f, -0.258819045f};
+  return make_float2(c[e], s[e]);
+}
+
+// Composite radix R = R1 R2 in registers: with n = n1 + R1 n2 and
+// k = k2 + R2 k1, X_k = sum_{n1} zeta_{R1}^{n1 k1} zeta_R^{n1 k2}
+// sum_{n2} x_n zeta_{R2}^{n2 k2} (length-R2 DFTs, twiddles, length-R1 DFTs).
+template <int R1, int R2, int SIGN>
+__device__ __forceinline__ void dft_comp(float2* v) {
+  constexpr int R = R1 * R2;
+  float2 t[R];
+#pragma unroll
+  for (int n1 = 0; n1 < R1; ++n1) {
+    float2 a[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) a[n2] = v[n1 + R1 * n2];
+    dft_reg<R2, SIGN>(a);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      if (n1 * k2 == 0) {
+        t[n1 * R2 + k2] = a[k2];
+      } else {
+        float2 w = unit_root<R>(n1 * k2);
+        if (SIGN < 0) w.y = -w.y;
+        t[n1 * R2 + k2] = cmul(a[k2], w);
+      }
+    }
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < R2; ++k2) {
+    float2 b[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) b[n1] = t[n1 * R2 + k2];
+    dft_reg<R1, SIGN>(b);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) v[k2 + R2 * k1] = b[k1];
+  }
+}
+
+template <int R, int SIGN>
 __device__ __forceinline__ void dft_reg(float2* v) {
   if constexpr (R == 2) dft2<SIGN>(v[0], v[1]);
   else if constexpr (R == 3) dft3<SIGN>(v[0], v[1], v[2]);
@@ -184,6 +263,12 @@ __device__ __forceinline__ void dft_reg(float2* v) {
   else if constexpr (R == 8) dft8<SIGN>(v);
   else if constexpr (R == 9) dft9<SIGN>(v);
   else if constexpr (R == 16) dft16<SIGN>(v);
+  else if constexpr (R == 6) dft_comp<2, 3, SIGN>(v);
+  else if constexpr (R == 10) dft_comp<2, 5, SIGN>(v);
+  else if constexpr (R == 12) dft_comp<4, 3, SIGN>(v);
+  else if constexpr (R == 18) dft_comp<2, 9, SIGN>(v);
+  else if constexpr (R == 20) dft_comp<4, 5, SIGN>(v);
+  else if constexpr (R == 24) dft_comp<8, 3, SIGN>(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -496,6 +581,13 @@ __host__ __device__ __forceinline__ int swz(int k) { return k ^ ((k >> 4) & 15);
 // array stride: a whole number of 16-element blocks, so swz stays inside the array
 __host__ __device__ __forceinline__ int swz_stride(int n) { return (n + 15) & ~15; }
 
+// Radix of the last pass of cta_fft_struct when the leftover power of two
+// rem2 (2, 4 or 8) and the odd factor (3, 5 or 9) are merged into one
+// composite butterfly (at most 24 points), else 0 (separate passes).
+__host__ __device__ constexpr int merged_tail(int rem2, int odd) {
+  return (rem2 > 1 && odd > 1 && rem2 * odd <= 24) ? rem2 * odd : 0;
+}
+
 // Lengths cta_fft_struct takes.
 __host__ __device__ inline bool struct_length(int n) {
   if (n < 16) return false;
@@ -582,14 +674,30 @@ __device__ __forceinline__ void gstage_odd(float2* base, int stride, int nbuf, i
   else if (odd == 9) gstage<9, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul);
 }
 
+template <int SIGN, int PTS, bool IN_SWZ, bool PASS_TW>
+__device__ __forceinline__ void gstage_merged(float2* base, int stride, int nbuf, int n, int Ns, int R,
+                                              const float2* __restrict__ tw, int twmul) {
+  switch (R) {
+    case 6: gstage<6, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul); break;
+    case 10: gstage<10, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul); break;
+    case 12: gstage<12, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul); break;
+    case 18: gstage<18, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul); break;
+    case 20: gstage<20, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul); break;
+    default: gstage<24, SIGN, PTS, IN_SWZ, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul); break;
+  }
+}
+
 // Whole DFT of a struct_length n on nbuf arrays (base + a * stride), in place,
-// natural order in and out.  Requires nbuf * n <= PTS * blockDim.x.
+// natural order in and out: radix-16 passes, then the leftover power of two
+// and the odd factor, merged into one composite pass where merged_tail allows.
+// Requires nbuf * n <= PTS * blockDim.x.
 template <int SIGN, int PTS, bool PASS_TW = false>
 __device__ __forceinline__ void cta_fft_struct(float2* base, int stride, int nbuf, int n,
                                                const float2* __restrict__ tw, int twmul) {
   const int a2 = __ffs(n) - 1;
   const int odd = n >> a2;
   const int n16 = a2 >> 2, rem = a2 & 3;
+  const int mt = merged_tail(1 << rem, odd);
   if (n == 16) {
     gstage<16, SIGN, PTS, false, false, PASS_TW>(base, stride, nbuf, n, 1, tw, twmul);
     return;
@@ -603,11 +711,19 @@ __device__ __forceinline__ void cta_fft_struct(float2* base, int stride, int nbu
       gstage<16, SIGN, PTS, false, false, PASS_TW>(base, stride, nbuf, n, Ns, tw, twmul);
       Ns *= 16;
     }
-    gstage_rem<SIGN, PTS, false, PASS_TW>(base, stride, nbuf, n, Ns, rem, tw, twmul);
-    gstage_odd<SIGN, PTS, false, PASS_TW>(base, stride, nbuf, n, Ns, odd, tw, twmul);
+    if (mt) {
+      gstage_merged<SIGN, PTS, false, PASS_TW>(base, stride, nbuf, n, Ns, mt, tw, twmul);
+    } else {
+      gstage_rem<SIGN, PTS, false, PASS_TW>(base, stride, nbuf, n, Ns, rem, tw, twmul);
+      gstage_odd<SIGN, PTS, false, PASS_TW>(base, stride, nbuf, n, Ns, odd, tw, twmul);
+    }
   } else if (rem) {
-    gstage_rem<SIGN, PTS, true, PASS_TW>(base, stride, nbuf, n, Ns, rem, tw, twmul);
-    gstage_odd<SIGN, PTS, false, PASS_TW>(base, stride, nbuf, n, Ns, odd, tw, twmul);
+    if (mt) {
+      gstage_merged<SIGN, PTS, true, PASS_TW>(base, stride, nbuf, n, Ns, mt, tw, twmul);
+    } else {
+      gstage_rem<SIGN, PTS, true, PASS_TW>(base, stride, nbuf, n, Ns, rem, tw, twmul);
+      gstage_odd<SIGN, PTS, false, PASS_TW>(base, stride, nbuf, n, Ns, odd, tw, twmul);
+    }
   } else {
     gstage_odd<SIGN, PTS, true, PASS_TW>(base, stride, nbuf, n, Ns, odd, tw, twmul);
   }

@@ -10,17 +10,24 @@
 
 namespace hd {
 
-// Pass radices of a length n = odd * 2^a, odd in {1, 3, 5, 9}, in the order
-// cta_fft_struct runs them: radix 16 while 16 divides the power of two, one
-// radix-8/4/2 pass for the rest of it, then one radix-3/5/9 pass.
+// Pass radices of a length n = odd * 2^a, odd in {1, 3, 5, 9}, a >= 4, in the
+// order cta_fft_struct runs them: radix 16 while 16 divides the power of two,
+// then the rest of it (8/4/2) and the odd factor (3/5/9), as one composite
+// pass where merged_tail allows, else as two passes.
 __host__ __device__ __forceinline__ int fast_passes(int n, int* Rs) {
   int a2 = 0;
   while (a2 < 30 && ((n >> a2) & 1) == 0) ++a2;
   const int odd = n >> a2;
+  const int rem2 = 1 << (a2 & 3);
   int k = 0;
   for (int i = 0; i < (a2 >> 2); ++i) Rs[k++] = 16;
-  if (a2 & 3) Rs[k++] = 1 << (a2 & 3);
-  if (odd > 1) Rs[k++] = odd;
+  const int mt = merged_tail(rem2, odd);
+  if (mt) {
+    Rs[k++] = mt;
+  } else {
+    if (rem2 > 1) Rs[k++] = rem2;
+    if (odd > 1) Rs[k++] = odd;
+  }
   return k;
 }
 

@@ -161,3 +161,17 @@ def test_invalid_parameters_rejected(hd):
     with pytest.raises(hd.HDError) as e:
         hd.conv(f, f, algo="hybridCS", params=[(50, 3)])  # qm = 150 < 2L-1
     assert e.value.status == hd.HD_EINVAL
+
+
+# DFT lengths whose last pass is a composite butterfly (leftover power of two
+# times the odd factor: radix 6, 10, 12, 18, 20, 24): m in {96, 160, 192, 288,
+# 320, 384, 1536, 2560, 3072, 4608}.  The single-call plan takes the smallest
+# cluster whose largest length suffices (C = 1 up to L = 9216) and the smallest
+# ladder length m with 2 m >= L, so L = 2m and L = 2m - 5 land on these m.
+@pytest.mark.parametrize("m", [96, 160, 192, 288, 320, 384, 1536, 2560, 3072, 4608])
+@pytest.mark.parametrize("delta", [0, 5])
+def test_composite_last_pass_lengths(hd, m, delta):
+    L = 2 * m - delta
+    f, g = inputs.uniform_pair(L, seed=500 + m + delta)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    assert rel_l2(run(hd, f, g, "hybridRCM"), ref) <= TOL

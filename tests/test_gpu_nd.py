@@ -94,3 +94,14 @@ def test_2d_in_place(hd, algo):
     hd.conv(tf, tg, algo=algo, out=tf)
     torch.cuda.synchronize()
     assert rel_l2(tf.cpu().numpy(), ref) <= TOL
+
+
+# Shapes whose default DFT lengths (ladder lengths) end in a composite pass:
+# outer m = 160, 288, 1536 (radix 10, 18, 6), rows m = 96, 192, 320 (packed
+# lengths 96, 191 and 320 for hybridRCM; radix 6, 12, 20), explicit 2 * ladder.
+@pytest.mark.parametrize("algo", ALL)
+@pytest.mark.parametrize("shape", [(160, 192), (288, 381), (1500, 40), (100, 640)])
+def test_2d_composite_last_pass(hd, algo, shape):
+    f, g = inputs.uniform_pair(shape, seed=sum(shape))
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    assert rel_l2(run(hd, f, g, algo), ref) <= TOL
