@@ -265,7 +265,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClusterThreads, 1)
 
   // ---- phase 2: DFTs of the owned residues, RCM product, backward DFTs
   {
-    if (4 * m <= kClusterPts * T) {
+    if (4 * m <= struct_capacity(m, kClusterPts, T)) {
       cta_fft_struct<1, kClusterPts, true>(arr, Sm, 4, m, tws, 0);
     } else {
       cta_fft_struct<1, kClusterPts, true>(arr, Sm, 2, m, tws, 0);

@@ -588,6 +588,26 @@ __host__ __device__ constexpr int merged_tail(int rem2, int odd) {
   return (rem2 > 1 && odd > 1 && rem2 * odd <= 24) ? rem2 * odd : 0;
 }
 
+// Points cta_fft_struct<SIGN, PTS> can transform in one call with T threads
+// for a struct_length n: every pass must hold its butterflies, ceil(PTS / R)
+// per thread, so the capacity is the smallest ceil(PTS / R) R T over the
+// passes (e.g. 32 T for n = 4096 at PTS = 24, whose passes are all radix 16).
+__host__ __device__ inline int struct_capacity(int n, int PTS, int T) {
+  int a2 = 0;
+  while (a2 < 30 && ((n >> a2) & 1) == 0) ++a2;
+  const int odd = n >> a2, rem2 = 1 << (a2 & 3);
+  auto cap = [&](int R) { return ((PTS + R - 1) / R) * R * T; };
+  int c = cap(16);
+  const int mt = merged_tail(rem2, odd);
+  if (mt) {
+    c = c < cap(mt) ? c : cap(mt);
+  } else {
+    if (rem2 > 1) c = c < cap(rem2) ? c : cap(rem2);
+    if (odd > 1) c = c < cap(odd) ? c : cap(odd);
+  }
+  return c;
+}
+
 // Lengths cta_fft_struct takes.
 __host__ __device__ inline bool struct_length(int n) {
   if (n < 16) return false;
