@@ -3,15 +3,18 @@
 Workload (one step): 4096 independent real convolutions of lengths drawn
 uniformly from 500..70000 (seed 2), values standard normal (seed 3), FP32,
 first L outputs each, computed by one call of the batched C-ABI entry point
-(one kernel launch), replayed from a CUDA graph.  Inputs and outputs (3 x 0.58
-GB) are larger than the 126 MB L2, so no flush is needed between steps.
+(one launch of the cluster kernel per cluster size in the plan, on streams
+forked from and joined back to the caller's stream), replayed from a CUDA
+graph.  Inputs and outputs (3 x 0.58 GB) are larger than the 126 MB L2, so no
+flush is needed between steps.
 
 Printed: one JSON line (rank 0).  ``value`` is whole-job convolutions/s with
 inputs resident in HBM; ``e2e`` the same metric through the C ABI with pinned
 HOST buffers (host-to-device copies of f and g and the device-to-host copy of
-h inside the timed region); ``roofline`` the dominant kernel's algorithmic HBM
-bytes (12 bytes per real element: read f and g, write h) per launch over its
-measured duration, against the measured copy bandwidth; ``cpu_baseline`` the
+h inside the timed region); ``roofline`` the batched kernel's algorithmic
+FP32 flops per step over the step's CUDA-event time against the FP32 peak
+("alu"), with the HBM view (12 algorithmic bytes per real element: read f
+and g, write h) against the measured copy bandwidth; ``cpu_baseline`` the
 FP64 oracle (padded radix-2 FFT convolution, OpenMP over items) on a bounded
 sample of the same items.
 
@@ -259,7 +262,8 @@ def run_gpu(args):
     ms_step = ms / args.steps
     value = whole_job_rate(n, world, args.steps, ms)
 
-    # dominant kernel: the single batched launch (one launch per step).
+    # dominant kernel: k_rcm1d_cluster, every launch of the step (one per cluster
+    # size, concurrent; timed together by the events on the joining stream).
     # FP32-ALU roofline: algorithmic flops of the FFT convolutions, 15 L log2 L
     # + 6 L per item (three real transforms of length 2L at 2.5 (2L) log2(2L),
     # i.e. 5 L log2 L each to first order, plus the spectral products), over
@@ -323,7 +327,9 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_alu, "unit": "TFLOP/s",
                      "frac": achieved_tf / peak_alu, "traffic": traffic,
                      "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
-                     "kernel": "k_rcm1d_cluster" if args.algo == "hybridRCM" else "k_cs1d",
+                     "kernel": ("k_rcm1d_cluster<C> (all launches of one step)" if args.algo == "hybridRCM"
+                                else "k_cs1d"),
+                     "traffic_unit": "DRAM bytes per step (all launches of one batched call)",
                      "algorithmic_flops_per_launch": alg_flops, "algorithmic_bytes_per_launch": alg_bytes,
                      "hbm": {"achieved": achieved_gbs, "peak": peak_hbm, "unit": "GB/s",
                              "frac": achieved_gbs / peak_hbm, "peak_source": peak_kind}},
