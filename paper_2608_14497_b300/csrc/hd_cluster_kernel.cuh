@@ -101,19 +101,29 @@ __device__ __forceinline__ void dft_c(float2* v) {
 
 // s values each thread keeps in flight in the exchange phases (their loads
 // are all issued before any arithmetic): 8 / C, so p <= C inputs per array
-// and s stay within 16 loads.  C = 8 loads one array at a time (registers).
+// and s stay within 16 loads per array.
 template <int CC>
 constexpr int kSPerThread = CC >= 8 ? 1 : 8 / CC;
+
+// Cluster barrier split in two: every CTA arrives when it starts (relaxed: no
+// data is published) and waits only before its first store into another
+// CTA's shared memory, so the wait overlaps the first input loads.
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
 
 // Phase 1 (Eq. forwardr, sum over t and the pre-twiddle) for C = CC: for each
 // s of this CTA's slice, the p packed inputs f~_{tm+s} (t < p <= C; zero for
 // C <= t < q) of f and of g, the q-point DFT over t as two length-C DFTs
 // (even and odd residues), times zeta_N^{rs}, stored into residue r's owner.
+// Both arrays' loads are issued before any arithmetic; zeta_N^{rs} is built
+// per residue from zeta_N^{s} and zeta_N^{4s} (few registers held).  Ends the
+// cluster barrier begun by cluster_arrive_relaxed().
 template <int CC>
 __device__ __forceinline__ void scatter_phase(const XCtx& x) {
   constexpr int Q = 2 * CC;
   constexpr int U = kSPerThread<CC>;
-  constexpr bool PRE = CC < 8;  // load both arrays before the arithmetic
   const int T = blockDim.x;
   auto load = [&](int s, int which, float2* v) {
     const float* src = (which ? x.g : x.f) + x.off;
@@ -125,25 +135,39 @@ __device__ __forceinline__ void scatter_phase(const XCtx& x) {
         v[t] = make_float2(__ldg(src + 2 * j), (2 * j + 1 < x.L) ? __ldg(src + 2 * j + 1) : 0.f);
     }
   };
-  for (int sb = x.s0 + (int)threadIdx.x; sb < x.s1; sb += U * T) {
-    float2 xv[U][PRE ? 2 : 1][CC];
-    if constexpr (PRE) {
+  float2 xv[U][2][CC];
+  auto load_batch = [&](int sb) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        load(sb + u * T, 0, xv[u][0]);
-        load(sb + u * T, 1, xv[u][1]);
-      }
+    for (int u = 0; u < U; ++u) {
+      load(sb + u * T, 0, xv[u][0]);
+      load(sb + u * T, 1, xv[u][1]);
     }
+  };
+  const int sb0 = x.s0 + (int)threadIdx.x;
+  load_batch(sb0);
+  cluster_wait();  // every CTA of the cluster is running
+  for (int sb = sb0; sb < x.s1; sb += U * T) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int s = sb + u * T;
       if (s < x.s1) {
-        float2 wr[Q];
-        residue_twiddles_q<Q>(x.tw, s, wr);
+        // zeta_N^{rs} = (zeta_N^{4s})^{r >> 2} (zeta_N^s)^{r & 3}
+        const float2 w1 = __ldg(x.tw + s);
+        float2 p1[4], p4[4];
+        p1[0] = make_float2(1.f, 0.f);
+        p1[1] = w1;
+        p1[2] = cmul(w1, w1);
+        p1[3] = cmul(p1[2], w1);
+        p4[0] = p1[0];
+        if constexpr (Q > 4) {
+          const float2 w4 = __ldg(x.tw + 4 * s);
+          p4[1] = w4;
+          p4[2] = cmul(w4, w4);
+          p4[3] = cmul(p4[2], w4);
+        }
 #pragma unroll
         for (int which = 0; which < 2; ++which) {
-          float2* v = xv[u][PRE ? which : 0];
-          if constexpr (!PRE) load(s, which, v);
+          const float2* v = xv[u][which];
           float2 e0[CC], e1[CC];
 #pragma unroll
           for (int t = 0; t < CC; ++t) {
@@ -154,13 +178,16 @@ __device__ __forceinline__ void scatter_phase(const XCtx& x) {
           dft_c<1, CC>(e1);
           const unsigned loc = x.arr_local + (unsigned)((which * 2 * x.Sm + s) * sizeof(float2));
 #pragma unroll
-          for (int r = 0; r < Q; ++r)
+          for (int r = 0; r < Q; ++r) {
+            const float2 wr = (r < 4) ? p1[r] : cmul(p4[r >> 2], p1[r & 3]);
             st_cluster_f2(map_rank_u32(loc + (unsigned)(res_slot(r, CC) * x.Sm * sizeof(float2)),
                                        (unsigned)(x.rank0 + res_owner(r, CC))),
-                          cmul((r & 1) ? e1[r >> 1] : e0[r >> 1], wr[r]));
+                          cmul((r & 1) ? e1[r >> 1] : e0[r >> 1], wr));
+          }
         }
       }
     }
+    if (sb + U * T < x.s1) load_batch(sb + U * T);
   }
 }
 
@@ -233,8 +260,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClusterThreads, 1)
   const float2* __restrict__ tw = it.tw;  // zeta_N^k
   // the table copy overlaps phase 1 (waited for before the phase-2 barrier)
   fill_pass_twiddles_async(tws, m, it.tabm);
-  // every CTA of the cluster is running before any distributed-shared-memory traffic
-  cluster.sync();
+  // every CTA of the cluster must be running before any distributed-shared-
+  // memory traffic: arrive now, wait in phase 1 after its first loads
+  cluster_arrive_relaxed();
 
   const int L = it.L;
   const int Lp = (L + 1) >> 1;
@@ -259,7 +287,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClusterThreads, 1)
   xc.tw = tw;
 
   // ---- phase 1: Eq. forwardr, sum over t and the pre-twiddle, scattered to owners
-  scatter_phase<C>(xc);
+  scatter_phase<C>(xc);  // completes the barrier begun above
   cp_async_wait_all();
   cluster.sync();
 
