@@ -39,3 +39,7 @@ def test_null_arguments_rejected_without_gpu():
     assert lib.hd_create(None, 0) == hd.HD_EINVAL
     assert lib.hd_conv1d(None, hd.HD_HYBRID_RCM, hd.HD_FP32, None, None, None, 16, None, None) == hd.HD_EINVAL
     assert lib.hd_plan(None, hd.HD_HYBRID_RCM, 16, None) == hd.HD_EINVAL
+    n = ctypes.c_int32(-1)
+    assert lib.hd_batch_plan_launches(None, ctypes.byref(n)) == hd.HD_EINVAL
+    assert lib.hd_batch_plan_launches(None, None) == hd.HD_EINVAL
+    assert lib.hd_tuning_table(None, 0, None, None, None, ctypes.byref(n)) == hd.HD_EINVAL

@@ -103,3 +103,48 @@ def test_autotune_table_matches_direct_timing(hd):
     torch.cuda.synchronize()
     us_direct = 1e3 * a.elapsed_time(b) / (10 * K)
     assert 0.5 <= us_direct / best[2] <= 2.0, (best, us_direct)
+
+
+@pytest.mark.parametrize("algo", ["hybridRCM", "hybridCS"])
+def test_batched_in_place(hd, algo):
+    """h may alias f: every item reads its inputs before writing its outputs."""
+    rng = np.random.default_rng(43)
+    Ls = rng.integers(300, 40000, 48).astype(np.int64)
+    off, f, g = flat(Ls, 44)
+    tf, tg = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    plan = hd.BatchPlan(off, Ls, algo=algo)
+    plan(tf, tg, out=tf)
+    h = tf.cpu().numpy()
+    ref = oracle.batch_conv1d(f, g, off, Ls, use_fft=True)
+    for i in range(len(Ls)):
+        a, b = off[i], off[i] + Ls[i]
+        assert rel_l2(h[a:b], ref[a:b]) <= TOL, (i, Ls[i])
+
+
+def test_batched_graph_replay_matches_eager(hd):
+    """A plan whose items span several cluster sizes launches one kernel per size
+    on streams forked from the caller's stream; captured in a CUDA graph and
+    replayed, it must give the eager result bit for bit."""
+    Ls = np.array([600, 1500, 9000, 17000, 30000, 52000, 69000, 2500, 40000, 12000] * 6, dtype=np.int64)
+    off, f, g = flat(Ls, 45)
+    tf, tg = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    plan = hd.BatchPlan(off, Ls, algo="hybridRCM")
+    assert 1 <= plan.launches <= 5
+    h_eager = plan(tf, tg).clone()
+    h = torch.zeros_like(tf)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        plan(tf, tg, out=h)  # warm-up on the capture stream
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            plan(tf, tg, out=h)
+    h.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(h, h_eager)
+    ref = oracle.batch_conv1d(f, g, off, Ls, use_fft=True)
+    hh = h.cpu().numpy()
+    for i in range(0, len(Ls), 7):
+        a, b = off[i], off[i] + Ls[i]
+        assert rel_l2(hh[a:b], ref[a:b]) <= TOL, (i, Ls[i])
