@@ -292,6 +292,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClusterThreads, 1)
   cluster.sync();
 
   // ---- phase 2: DFTs of the owned residues, RCM product, backward DFTs
+  int bwd_res = 0;
   {
     if (4 * m <= struct_capacity(m, kClusterPts, T)) {
       cta_fft_struct<1, kClusterPts, true>(arr, Sm, 4, m, tws, 0);
@@ -334,9 +335,12 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClusterThreads, 1)
       if (!(c == 0 && ls == l)) Fs[ls] = csub(cmul(Ac, Bc), cconj(alpha));
     }
     __syncthreads();
-    cta_fft_struct<-1, kClusterPts, true>(arr, Sm, 2, m, tws, 0);
+    // G_a, G_b are free after the product: the backward DFTs of F_a, F_b run
+    // out of place between the two pairs of arrays (one barrier per pass)
+    bwd_res = cta_fft_struct_oop<-1, true>(arr, arr + 2 * Sm, Sm, 2, m, tws, 0);
   }
   cluster.sync();
+  xc.arr_local += (unsigned)(bwd_res * 2 * Sm * sizeof(float2));  // where the owners' results are
 
   // ---- phase 3: Eq. accumulation, gathered from the owners
   gather_phase<C>(xc);

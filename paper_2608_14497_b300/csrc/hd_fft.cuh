@@ -749,6 +749,127 @@ __device__ __forceinline__ void cta_fft_struct(float2* base, int stride, int nbu
   }
 }
 
+// ---------------------------------------------------------------------------
+// Out-of-place form of the structured engine: pass k reads one buffer and
+// writes the other, so a pass needs one barrier (after its stores) and holds
+// one butterfly at a time.  Same pass sequence, swizzle and twiddles as
+// cta_fft_struct.
+// ---------------------------------------------------------------------------
+template <int R, int SIGN, bool IN_SWZ, bool OUT_SWZ, bool PASS_TW>
+__device__ __forceinline__ void gstage_oop(const float2* __restrict__ in, float2* __restrict__ out, int stride,
+                                           int nbuf, int n, int Ns, const float2* __restrict__ tw, int twmul) {
+  const int nb = n / R;
+  const DivF dnb = make_div(nb), dNs = make_div(Ns);
+  const int total = nb * nbuf;
+  const int twstep = twmul * (n / (Ns * R));
+  constexpr int UNR = R <= 8 ? 2 : 1;  // two small butterflies in flight; one large one
+#pragma unroll UNR
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int a = fdiv(idx, dnb);
+    const int j = idx - a * nb;
+    const int jm = j - fdiv(j, dNs) * Ns;
+    const float2* x = in + a * stride;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = x[IN_SWZ ? swz(j + r * nb) : j + r * nb];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w;
+        if constexpr (PASS_TW) {
+          w = tw[(Ns - 1) + (r - 1) * Ns + jm];
+          if (SIGN < 0) w.y = -w.y;
+        } else {
+          w = tw_get<SIGN>(tw, r * jm * twstep);
+        }
+        v[r] = cmul(v[r], w);
+      }
+    }
+    dft_reg<R, SIGN>(v);
+    float2* y = out + a * stride;
+    const int o = (j - jm) * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) y[OUT_SWZ ? swz(o + r * Ns) : o + r * Ns] = v[r];
+  }
+  __syncthreads();
+}
+
+template <int SIGN, bool IN_SWZ, bool PASS_TW>
+__device__ __forceinline__ void gstage_oop_tail(const float2* in, float2* out, int stride, int nbuf, int n, int Ns,
+                                                int R, const float2* __restrict__ tw, int twmul) {
+  switch (R) {
+    case 2: gstage_oop<2, SIGN, IN_SWZ, false, PASS_TW>(in, out, stride, nbuf, n, Ns, tw, twmul); break;
+    case 3: gstage_oop<3, SIGN, IN_SWZ, false, PASS_TW>(in, out, stride, nbuf, n, Ns, tw, twmul); break;
+    case 4: gstage_oop<4, SIGN, IN_SWZ, false, PASS_TW>(in, out, stride, nbuf, n, Ns, tw, twmul); break;
+    case 5: gstage_oop<5, SIGN, IN_SWZ, false, PASS_TW>(in, out, stride, nbuf, n, Ns, tw, twmul); break;
+    case 6: gstage_oop<6, SIGN, IN_SWZ, false, PASS_TW>(in, out, stride, nbuf, n, Ns, tw, twmul); break;
+    case 8: gstage_oop<8, SIGN, IN_SWZ, false, PASS_TW>(in, out, stride, nbuf, n, Ns, tw, twmul); break;
+    case 9: gstage_oop<9, SIGN, IN_SWZ, false, PASS_TW>(in, out, stride, nbuf, n, Ns, tw, twmul); break;
+    case 10: gstage_oop<10, SIGN, IN_SWZ, false, PASS_TW>(in, out, stride, nbuf, n, Ns, tw, twmul); break;
+    case 12: gstage_oop<12, SIGN, IN_SWZ, false, PASS_TW>(in, out, stride, nbuf, n, Ns, tw, twmul); break;
+    case 18: gstage_oop<18, SIGN, IN_SWZ, false, PASS_TW>(in, out, stride, nbuf, n, Ns, tw, twmul); break;
+    case 20: gstage_oop<20, SIGN, IN_SWZ, false, PASS_TW>(in, out, stride, nbuf, n, Ns, tw, twmul); break;
+    default: gstage_oop<24, SIGN, IN_SWZ, false, PASS_TW>(in, out, stride, nbuf, n, Ns, tw, twmul); break;
+  }
+}
+
+// Whole DFT of a struct_length n on nbuf arrays (b0 + a * stride), using the
+// arrays at b1 (same shape) as the other buffer; returns 0 if the result is in
+// b0, 1 if in b1.  Ends with a barrier.
+template <int SIGN, bool PASS_TW>
+__device__ __forceinline__ int cta_fft_struct_oop(float2* b0, float2* b1, int stride, int nbuf, int n,
+                                                  const float2* __restrict__ tw, int twmul) {
+  const int a2 = __ffs(n) - 1;
+  const int odd = n >> a2;
+  const int n16 = a2 >> 2, rem = a2 & 3;
+  const int rem2 = 1 << rem;
+  const int mt = merged_tail(rem2, odd);
+  // the passes after the radix-16 ones: one merged pass, or rem2 then odd
+  const int t1 = mt ? mt : (rem2 > 1 ? rem2 : odd);
+  const int t2 = mt ? 1 : (rem2 > 1 ? odd : 1);
+  float2* cur = b0;
+  float2* nxt = b1;
+  int res = 0;
+  auto flip = [&]() {
+    float2* t = cur;
+    cur = nxt;
+    nxt = t;
+    res ^= 1;
+  };
+  if (n == 16) {
+    gstage_oop<16, SIGN, false, false, PASS_TW>(cur, nxt, stride, nbuf, n, 1, tw, twmul);
+    flip();
+    return res;
+  }
+  gstage_oop<16, SIGN, false, true, PASS_TW>(cur, nxt, stride, nbuf, n, 1, tw, twmul);
+  flip();
+  int Ns = 16;
+  if (n16 >= 2) {
+    gstage_oop<16, SIGN, true, false, PASS_TW>(cur, nxt, stride, nbuf, n, Ns, tw, twmul);
+    flip();
+    Ns *= 16;
+    for (int i = 2; i < n16; ++i) {
+      gstage_oop<16, SIGN, false, false, PASS_TW>(cur, nxt, stride, nbuf, n, Ns, tw, twmul);
+      flip();
+      Ns *= 16;
+    }
+    if (t1 > 1) {
+      gstage_oop_tail<SIGN, false, PASS_TW>(cur, nxt, stride, nbuf, n, Ns, t1, tw, twmul);
+      flip();
+      Ns *= t1;
+    }
+  } else if (t1 > 1) {
+    gstage_oop_tail<SIGN, true, PASS_TW>(cur, nxt, stride, nbuf, n, Ns, t1, tw, twmul);
+    flip();
+    Ns *= t1;
+  }
+  if (t2 > 1) {
+    gstage_oop_tail<SIGN, false, PASS_TW>(cur, nxt, stride, nbuf, n, Ns, t2, tw, twmul);
+    flip();
+  }
+  return res;
+}
+
 // DFT dispatch of the nD kernels: SE (struct_length lengths) inlines the
 // structured engine, otherwise the generic plan-driven cta_fft.
 template <int SIGN, int PTS, bool TC, bool SE>
