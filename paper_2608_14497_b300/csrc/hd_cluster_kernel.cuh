@@ -112,6 +112,8 @@ __device__ __forceinline__ void cluster_arrive_relaxed() {
   asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
 }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
+// Per-thread (non-aligned) arrive: a thread may arrive from divergent code.
+__device__ __forceinline__ void cluster_arrive_thread() { asm volatile("barrier.cluster.arrive.relaxed;\n" ::: "memory"); }
 
 // Phase 1 (Eq. forwardr, sum over t and the pre-twiddle) for C = CC: for each
 // s of this CTA's slice, the p packed inputs f~_{tm+s} (t < p <= C; zero for
@@ -194,6 +196,9 @@ __device__ __forceinline__ void scatter_phase(const XCtx& x) {
 // Phase 3 (Eq. accumulation) for C = CC: w_r[s] of every residue from its
 // owner, times zeta_N^{-rs}, the backward q-point sum over r for the p needed
 // blocks t (two length-C DFTs), scaled by 1/N, unpacked to the real output.
+// Each thread arrives at the final cluster barrier as soon as its last
+// distributed-shared-memory value has been used, before its last output
+// stores; the caller waits (no CTA may exit while others read its memory).
 template <int CC>
 __device__ __forceinline__ void gather_phase(const XCtx& x) {
   constexpr int Q = 2 * CC;
@@ -201,6 +206,7 @@ __device__ __forceinline__ void gather_phase(const XCtx& x) {
   const int T = blockDim.x;
   const float sc = 1.0f / (float)(Q * x.m);
   float* hi = x.h + x.off;
+  bool arrived = false;
   for (int sb = x.s0 + (int)threadIdx.x; sb < x.s1; sb += U * T) {
     float2 yv[U][Q];
 #pragma unroll
@@ -226,6 +232,10 @@ __device__ __forceinline__ void gather_phase(const XCtx& x) {
           if (r & 1) e1[r >> 1] = w;
           else e0[r >> 1] = w;
         }
+        if (u == U - 1 && sb + U * T >= x.s1) {
+          cluster_arrive_thread();  // every remote value of this thread is consumed
+          arrived = true;
+        }
         dft_c<-1, CC>(e0);
         dft_c<-1, CC>(e1);
 #pragma unroll
@@ -240,6 +250,7 @@ __device__ __forceinline__ void gather_phase(const XCtx& x) {
       }
     }
   }
+  if (!arrived) cluster_arrive_thread();
 }
 
 // One convolution per cluster of C CTAs (C = cluster size); CTA c of the
@@ -343,9 +354,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClusterThreads, 1)
   xc.arr_local += (unsigned)(bwd_res * 2 * Sm * sizeof(float2));  // where the owners' results are
 
   // ---- phase 3: Eq. accumulation, gathered from the owners
-  gather_phase<C>(xc);
+  gather_phase<C>(xc);  // arrives at the final barrier
   // no CTA leaves while others may still read its shared memory
-  cluster.sync();
+  cluster_wait();
 }
 
 
