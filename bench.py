@@ -409,6 +409,33 @@ def compare_suite(reps=10):
     return out
 
 
+def run_nd(args):
+    """One convolution of shape --nd by --nd-algo, --warmup untimed and --steps timed
+    calls (CUDA events, inputs resident), printed as one JSON line; the unit of
+    the nD kernel profiles."""
+    import torch
+    import paper_2608_14497_b300 as hd
+    from paper_2608_14497_b300 import inputs
+    shape = tuple(int(x) for x in args.nd.split(","))
+    f, g = (inputs.uniform_pair if len(shape) < 3 else inputs.normal_pair)(shape, 4 if len(shape) < 3 else 5)
+    tf, tg = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    h = torch.empty_like(tf)
+    for _ in range(args.warmup):
+        hd.conv(tf, tg, algo=args.nd_algo, out=h)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        hd.conv(tf, tg, algo=args.nd_algo, out=h)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    n = int(np.prod(shape))
+    print(json.dumps({"mode": "nd", "shape": list(shape), "algo": args.nd_algo, "ms_per_conv": ms,
+                      "algorithmic_GBps_12B": 12 * n / (ms * 1e-3) / 1e9}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,6 +448,9 @@ def main():
     ap.add_argument("--no-check", action="store_true", help="accepted for compatibility; no effect")
     ap.add_argument("--compare", action="store_true",
                     help="add same-GPU timings of all algorithms on the 1D/2D/3D configs")
+    ap.add_argument("--nd", default=None,
+                    help="time one 1D/2D/3D convolution of this shape instead (e.g. 384,384,384); for profiling")
+    ap.add_argument("--nd-algo", default="hybridRCM", choices=["hybridRCM", "hybridCS", "explicitRCM", "explicit"])
     ap.add_argument("--items", type=int, default=N_ITEMS,
                     help="batch size; smaller batches are for profiling captures, not for the reported line")
     args = ap.parse_args()
@@ -428,6 +458,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.nd:
+        return run_nd(args)
     return run_gpu(args)
 
 
