@@ -870,12 +870,38 @@ __device__ __forceinline__ int cta_fft_struct_oop(float2* b0, float2* b1, int st
   return res;
 }
 
+// Structured pass sequence with the radix-16 passes on tensor cores
+// (fft_stage_tc16, split bf16 operands) and the leftover power of two and
+// odd factor in FP32 (gstage), natural order throughout.  Requires
+// nbuf * n <= 16 * blockDim.x (the tensor-core pass) and <= PTS * blockDim.x.
+template <int SIGN, int PTS>
+__device__ __forceinline__ void cta_fft_struct_tc(float2* base, int stride, int nbuf, int n,
+                                                  const float2* __restrict__ tw, int twmul) {
+  const int a2 = __ffs(n) - 1;
+  const int odd = n >> a2;
+  const int n16 = a2 >> 2, rem = a2 & 3;
+  const int mt = merged_tail(1 << rem, odd);
+  int Ns = 1;
+  for (int i = 0; i < n16; ++i) {
+    fft_stage_tc16<SIGN, PTS>(base, stride, nbuf, n, Ns, tw, twmul);
+    Ns *= 16;
+  }
+  if (mt) {
+    gstage_merged<SIGN, PTS, false, false>(base, stride, nbuf, n, Ns, mt, tw, twmul);
+  } else {
+    gstage_rem<SIGN, PTS, false, false>(base, stride, nbuf, n, Ns, rem, tw, twmul);
+    gstage_odd<SIGN, PTS, false, false>(base, stride, nbuf, n, Ns, odd, tw, twmul);
+  }
+}
+
 // DFT dispatch of the nD kernels: SE (struct_length lengths) inlines the
-// structured engine, otherwise the generic plan-driven cta_fft.
+// structured engine (TC: with tensor-core radix-16 passes), otherwise the
+// generic plan-driven cta_fft.
 template <int SIGN, int PTS, bool TC, bool SE>
 __device__ __forceinline__ void fft_sel(float2* base, int stride, int nbuf, const FftPlan& pl,
                                         const float2* __restrict__ tw, int twmul) {
-  if constexpr (SE) cta_fft_struct<SIGN, PTS>(base, stride, nbuf, pl.n, tw, twmul);
+  if constexpr (SE && TC) cta_fft_struct_tc<SIGN, PTS>(base, stride, nbuf, pl.n, tw, twmul);
+  else if constexpr (SE) cta_fft_struct<SIGN, PTS>(base, stride, nbuf, pl.n, tw, twmul);
   else cta_fft<SIGN, PTS, TC>(base, stride, nbuf, pl, tw, twmul);
 }
 

@@ -6,9 +6,10 @@ namespace hd {
 cudaError_t launch_col_fwd(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, const void* X, float2* Y,
                            ColGeom cg, int Lin, int m, int q, int p, int in_mode, int Lreal, const float2* tw,
                            FftPlan pl) {
-  auto k = e == Eng::SE   ? k_col_fwd<kPtsSE, false, true>
-           : e == Eng::TC ? k_col_fwd<kPts, true, false>
-                          : k_col_fwd<kPts, false, false>;
+  auto k = e == Eng::SE    ? k_col_fwd<kPtsSE, false, true>
+           : e == Eng::TC  ? k_col_fwd<kPts, true, false>
+           : e == Eng::TCS ? k_col_fwd<kPts, true, true>
+                           : k_col_fwd<kPts, false, false>;
   return launch_kernel(k, grid, T, smem, st, X, Y, cg, Lin, m, q, p, in_mode, Lreal, tw, pl);
 }
 

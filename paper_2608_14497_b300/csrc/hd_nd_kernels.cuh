@@ -647,11 +647,14 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_rows_fft(RowsIO io, int mod
 // threads), the generic plan-driven engine (kPts points per thread, <= 1024
 // threads), or the split-precision tensor-core passes (kPts, <= 512 threads).
 constexpr int kPtsSE = 32;
-enum class Eng { GEN, SE, TC };
-inline Eng pick_eng(bool tc, bool se_ok) { return tc ? Eng::TC : (se_ok ? Eng::SE : Eng::GEN); }
+// TCS: the structured sequence with tensor-core radix-16 passes (split bf16)
+enum class Eng { GEN, SE, TC, TCS };
+inline Eng pick_eng(bool tc, bool se_ok) {
+  return tc ? (se_ok ? Eng::TCS : Eng::TC) : (se_ok ? Eng::SE : Eng::GEN);
+}
 // Points one CTA may transform at once.
 inline int64_t max_points(Eng e) {
-  return e == Eng::SE ? (int64_t)kPtsSE * 512 : (int64_t)kPts * (e == Eng::TC ? 512 : 1024);
+  return e == Eng::SE ? (int64_t)kPtsSE * 512 : (int64_t)kPts * ((e == Eng::TC || e == Eng::TCS) ? 512 : 1024);
 }
 inline int eng_threads(Eng e, int64_t points) {
   if (e == Eng::SE) return std::min(512, threads_for_points(points, 16));
