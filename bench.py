@@ -48,13 +48,22 @@ CLUSTER_SOURCES = ("hd_cluster_kernel.cuh", "hd_cluster_c1.cu", "hd_cluster_c2.c
                    "hd_internal.h")
 
 
+def _code_only(text):
+    """Source text without comments and blank space (a comment edit does not
+    change the kernel whose traffic was measured)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "".join(text.split())
+
+
 def csrc_hash(names=CLUSTER_SOURCES):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2608_14497_b300", "csrc")
     for name in sorted(names):
-        with open(os.path.join(d, name), "rb") as fh:
+        with open(os.path.join(d, name), encoding="utf-8") as fh:
             h.update(name.encode())
-            h.update(fh.read())
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

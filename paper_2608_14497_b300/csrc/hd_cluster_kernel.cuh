@@ -23,9 +23,9 @@
 // Inputs are read once and outputs written once: the kernel's HBM traffic is
 // the 12 bytes per real element of the problem plus twiddle tables.
 //
-// One launch covers a whole batch: clusters have 8 CTAs; a cluster processes a
-// "unit" of 8/C convolutions of the same C (CTAs of different convolutions of a
-// unit never exchange data; they only share the cluster barriers).
+// The kernel is instantiated per C (cluster size C, one convolution per
+// cluster; hd_cluster_c{1,2,4,8}.cu); a batch launches one instance per C in
+// use, the launches running concurrently on separate streams (hd_batch.cu).
 #pragma once
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
