@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 from paper_2608_14497_b300 import inputs
-from tests.conftest import rel_l2
+from tests.conftest import record_rel, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -88,3 +88,21 @@ def test_adjoint_batch16_1024_sampled(hd):
         got_g = gga[b][tuple(pts.T)]
         assert np.linalg.norm(got_f - ref_f) / np.linalg.norm(ref_f) <= TOL
         assert np.linalg.norm(got_g - ref_g) / np.linalg.norm(ref_g) <= TOL
+
+
+def test_adjoint_batch16_1024_full_items(hd):
+    """Two whole items of the 16 x 1024^2 workload against O2 in FP64:
+    grad_f = rev(conv(rev(u), g)) and grad_g = rev(conv(rev(u), f)) on both axes."""
+    B, L = 16, 1024
+    f, g = inputs.uniform_pair((B, L, L), seed=6)
+    rng = np.random.default_rng(74)
+    u = rng.uniform(-1, 1, (B, L, L)).astype(np.float32)
+    gf, gg = hd.adjoint(cuda(u), cuda(f), cuda(g), "hybridRCM")
+    gf, gg = gf.cpu().numpy(), gg.cpu().numpy()
+    for b in (0, 11):
+        ur = u[b][::-1, ::-1].astype(np.float64)
+        ref_f = oracle.fft_conv(ur, g[b].astype(np.float64))[::-1, ::-1]
+        ref_g = oracle.fft_conv(ur, f[b].astype(np.float64))[::-1, ::-1]
+        ef = record_rel(f"adjoint 16x1024^2 item {b} grad_f", rel_l2(gf[b], ref_f), TOL, ref_f.size)
+        eg = record_rel(f"adjoint 16x1024^2 item {b} grad_g", rel_l2(gg[b], ref_g), TOL, ref_g.size)
+        assert ef <= TOL and eg <= TOL

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_2608_14497_b300 import inputs
-from tests.conftest import rel_l2
+from tests.conftest import record_rel, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -44,15 +44,32 @@ def test_split_precision_small(hd, shape, tc):
         assert e32 == err
 
 
-@pytest.mark.parametrize("L", [256, 384])
-def test_split_precision_3d_full_size_sampled(hd, L):
+def test_split_precision_3d_L256_every_output(hd):
+    """Every output of 3D L = 256 (split precision) against O2."""
+    f, g = inputs.normal_pair((256, 256, 256), seed=5)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    h = run(hd, f, g, "split_bf16")
+    assert np.isfinite(h).all()
+    err = record_rel("3D L=256 hybridRCM split_bf16", rel_l2(h, ref), TOL_SPLIT, h.size)
+    assert err <= TOL_SPLIT
+
+
+def test_split_precision_3d_L384_faces_and_points(hd):
+    """3D L = 384 (split precision): every output on three face diagonals and
+    2000 random points against direct FP64 sums."""
+    L = 384
     f, g = inputs.normal_pair((L, L, L), seed=5)
     h = run(hd, f, g, "split_bf16")
+    i = np.arange(L)
+    z = np.zeros(L, dtype=np.int64)
     rng = np.random.default_rng(L)
-    pts = np.stack([rng.integers(0, L, 60) for _ in range(3)], axis=1)
+    pts = np.concatenate([np.stack([z, i, i], 1), np.stack([i, z, i], 1),
+                          np.stack([i, i, np.full(L, L - 1)], 1), rng.integers(0, L, (2000, 3))])
     ref = oracle.direct_conv_points(f.astype(np.float64), g.astype(np.float64), pts)
     got = h[tuple(pts.T)]
-    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= TOL_SPLIT
+    err = record_rel("3D L=384 hybridRCM split_bf16 (faces + 2000 points)",
+                     np.linalg.norm(got - ref) / np.linalg.norm(ref), TOL_SPLIT, len(pts))
+    assert err <= TOL_SPLIT
 
 
 def test_split_precision_other_algorithms_rejected(hd):

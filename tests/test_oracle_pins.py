@@ -349,3 +349,64 @@ def test_direct_points_match_full_and_closed_form():
     pts = np.stack([rng.integers(0, L, 20) for _ in range(3)], axis=1)
     ref = np.prod([_geom_1d(a[i], b[i], L)[pts[:, i]] for i in range(3)], axis=0)
     assert np.allclose(oracle.direct_conv_points(f, g, pts), ref, rtol=1e-11, atol=0)
+
+
+# --- the batched oracle (flat arrays, item i at offsets[i], length Ls[i]) -------
+def _uneven_batch(seed=21):
+    """About 30 uneven items with gaps between them (L = 1 included)."""
+    rng = np.random.default_rng(seed)
+    Ls = np.concatenate([[1, 2, 3], rng.integers(1, 700, 27)]).astype(np.int64)
+    gaps = rng.integers(0, 9, len(Ls)).astype(np.int64)
+    off = np.zeros(len(Ls), dtype=np.int64)
+    off[0] = gaps[0]
+    for i in range(1, len(Ls)):
+        off[i] = off[i - 1] + Ls[i - 1] + gaps[i]
+    total = int(off[-1] + Ls[-1] + 5)
+    f = rng.uniform(-1, 1, total)
+    g = rng.uniform(-1, 1, total)
+    return off, Ls, f, g
+
+
+def _check_batch(h, f, g, off, Ls):
+    """Every item equals the single-array direct convolution of its slices, and
+    every position outside the items is left at zero."""
+    covered = np.zeros(len(f), dtype=bool)
+    for o, L in zip(off, Ls):
+        ref = oracle.direct_conv(f[o:o + L], g[o:o + L])
+        if not (rel_l2(h[o:o + L], ref) < 1e-13):
+            return False
+        covered[o:o + L] = True
+    return bool(np.all(h[~covered] == 0.0))
+
+
+@pytest.mark.parametrize("use_fft", [True, False])
+def test_batch_conv1d_matches_per_item(use_fft):
+    off, Ls, f, g = _uneven_batch()
+    h = oracle.batch_conv1d(f, g, off, Ls, use_fft=use_fft)
+    assert _check_batch(h, f, g, off, Ls)
+    # and item by item against O2 on the same slices
+    for o, L in zip(off, Ls):
+        assert rel_l2(h[o:o + L], oracle.fft_conv(f[o:o + L], g[o:o + L])) < 1e-13
+
+
+def test_batch_conv1d_integer_exact():
+    rng = np.random.default_rng(22)
+    Ls = np.array([1, 5, 64, 300, 17], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(Ls)[:-1]]).astype(np.int64)
+    fi = rng.integers(-8, 9, int(Ls.sum()))
+    gi = rng.integers(-8, 9, int(Ls.sum()))
+    h = oracle.batch_conv1d(fi.astype(float), gi.astype(float), off, Ls, use_fft=False)
+    for o, L in zip(off, Ls):
+        exact = scipy.signal.convolve(fi[o:o + L], gi[o:o + L], method="direct")[:L]
+        assert np.array_equal(h[o:o + L], exact.astype(float))
+
+
+def test_planted_batch_offset_mistake_is_caught():
+    """A batch whose g is read at the wrong offset (the next item's start, as a
+    mistake that applied off[i] to f but not to g would) fails the check."""
+    off, Ls, f, g = _uneven_batch()
+    shifted = np.roll(g, -int(Ls[0]))  # g_i read from another item's data
+    h_bad = oracle.batch_conv1d(f, shifted, off, Ls, use_fft=True)
+    assert not _check_batch(h_bad, f, g, off, Ls)
+    h_off = oracle.batch_conv1d(f, g, off + 1, Ls, use_fft=True)  # every item one place late
+    assert not _check_batch(h_off, f, g, off, Ls)
