@@ -26,9 +26,13 @@
  * or g (in place, as the paper times it); partial overlap is not allowed.
  * Calls are asynchronous on the given CUDA stream (NULL = legacy default).
  * The context owns twiddle tables and scratch; the first call for a new size
- * allocates them (cudaMalloc) and uploads tables, so capture a call in a CUDA
- * graph only after one uncaptured call of the same shape.  A context is not
- * thread-safe: use one per host thread.
+ * allocates them (cudaMalloc, and a synchronisation of the context's own
+ * table stream), and growing the scratch synchronises the device, so capture
+ * a call in a CUDA graph only after one uncaptured call of the same shape.
+ * Tables are complete before the call that creates them returns, so any
+ * stream may use them.  The scratch is one area per context: a context serves
+ * one stream at a time (calls on different streams that overlap on the GPU
+ * race on it); use one context per stream and per host thread.
  *
  * Errors: HD_EINVAL for invalid arguments (null pointer, L < 1, hybrid
  * parameters that do not dealias, see hd_dim_params), HD_EUNSUPPORTED for a

@@ -14,7 +14,9 @@
 
 namespace {
 thread_local std::string g_last_error;
+}  // namespace
 
+namespace hd {
 hd_status fail(hd_status s, const char* what) {
   g_last_error = what;
   return s;
@@ -24,7 +26,7 @@ hd_status cuda_fail(cudaError_t e, const char* where) {
   g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
   return HD_ECUDA;
 }
-}  // namespace
+}  // namespace hd
 
 namespace hd {
 
@@ -124,7 +126,7 @@ static hd_status conv1d_rcm_cluster(hd_ctx* c, const float* f, const float* g, f
   cl.one_item.tw = tw;
   cl.one_item.tabm = c->tables.get_pass_table(m, st, &terr);
   if (!cl.one_item.tabm) return fail(terr, "pass table allocation failed");
-  cudaError_t e = launch_rcm1d_cluster(cl, C, 1, cluster_smem_bytes(m), f, g, h, st);
+  cudaError_t e = launch_rcm1d_cluster(cl, C, m, 1, f, g, h, st);
   if (e != cudaSuccess) return cuda_fail(e, "cluster launch");
   return HD_OK;
 }

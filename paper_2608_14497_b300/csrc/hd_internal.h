@@ -31,10 +31,17 @@ int64_t next_smooth(int64_t n);
 int64_t ladder_ceil(int64_t n);  // smallest {1, 3, 5, 9} x 2^a >= n
 
 // Twiddle tables: zeta_N^k, k < N, FP64 on the device, rounded to FP32.
+// A table is built on the cache's own stream and is complete when get()
+// returns (that stream is synchronised once per new table), so a call on any
+// stream may read a cached table without an ordering hazard.  The stream
+// argument is kept for the call sites; it does not order the build.
 struct TableCache {
   std::map<int64_t, float2*> tabs;
+  cudaStream_t build = nullptr;  // private non-blocking stream of the builds
   const float2* get(int64_t N, cudaStream_t st, hd_status* err);
+  // per-length table of the cluster kernel, length n = 256 R3 (cl::Shape)
   const float2* get_pass_table(int n, cudaStream_t st, hd_status* err);
+  cudaStream_t build_stream(hd_status* err);
   void clear();
 };
 
@@ -68,7 +75,13 @@ struct hd_ctx {
 };
 
 namespace hd {
+// Record the reason of a failed call for hd_last_error_string (per host
+// thread) and return the status (HD_ECUDA for cuda_fail).
+hd_status fail(hd_status s, const char* what);
+hd_status cuda_fail(cudaError_t e, const char* where);
 hd_status ensure_ws(hd_ctx* c, size_t bytes);
+// Dynamic shared-memory opt-in of a kernel, set once per device and size.
+cudaError_t smem_optin(const void* fn, size_t smem);
 hd_status ensure_ws2(hd_ctx* c, size_t bytes);
 hd_status ensure_meta(hd_ctx* c, size_t bytes);
 }  // namespace hd

@@ -36,11 +36,13 @@ static float2* g_noalloc_addr[kNoAllocMaxDev];
 // Device address of the scratch array on the current device (looked up once
 // per device; the array's name is only a host-side stand-in).
 static hd_status noalloc_scratch(int dev, float2** out) {
-  if (dev < 0 || dev >= kNoAllocMaxDev) return HD_EUNSUPPORTED;
+  if (dev < 0 || dev >= kNoAllocMaxDev) return fail(HD_EUNSUPPORTED, "noalloc: device index beyond 63");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
     float2* p = nullptr;
-    if (cudaGetSymbolAddress((void**)&p, g_noalloc_scratch) != cudaSuccess || !p) return HD_ECUDA;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "noalloc: cudaGetSymbolAddress");
+    if (!p) return fail(HD_ECUDA, "noalloc: null scratch address");
     g_noalloc_addr[dev] = p;
   }
   *out = g_noalloc_addr[dev];
@@ -55,11 +57,13 @@ using namespace hd;
 
 extern "C" hd_status hd_conv1d_rcm_noalloc(const float* f, const float* g, float* h, int64_t L,
                                            const hd_dim_params* prm, void* stream) {
-  if (!f || !g || !h || L < 1) return HD_EINVAL;
-  if (L > kNoAllocMaxL) return HD_EUNSUPPORTED;
-  if (prm && (prm->m < 0 || prm->q < 0)) return HD_EINVAL;
+  if (!f || !g || !h) return fail(HD_EINVAL, "noalloc: null array pointer");
+  if (L < 1) return fail(HD_EINVAL, "noalloc: L < 1");
+  if (L > kNoAllocMaxL) return fail(HD_EUNSUPPORTED, "noalloc: L beyond the static scratch (L <= 524288)");
+  if (prm && (prm->m < 0 || prm->q < 0)) return fail(HD_EINVAL, "noalloc: negative m or q");
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return HD_ECUDA;
+  const cudaError_t de = cudaGetDevice(&dev);
+  if (de != cudaSuccess) return cuda_fail(de, "noalloc: cudaGetDevice");
   float2* scratch = nullptr;
   hd_status s = noalloc_scratch(dev, &scratch);
   if (s != HD_OK) return s;
@@ -70,8 +74,8 @@ extern "C" hd_status hd_conv1d_rcm_noalloc(const float* f, const float* g, float
   if (prm && prm->m > 0) {
     m = prm->m;
     q = prm->q > 0 ? prm->q : cdiv(L, m);
-    if (q * m < L) return HD_EINVAL;
-    if (m > mmax) return HD_EUNSUPPORTED;
+    if (q * m < L) return fail(HD_EINVAL, "noalloc: hybridRCM needs q m >= L (packed)");
+    if (m > mmax) return fail(HD_EUNSUPPORTED, "noalloc: m too large for one CTA (m <= 4096)");
   } else {
     m = next_smooth(Lp);
     q = 2;
@@ -83,16 +87,17 @@ extern "C" hd_status hd_conv1d_rcm_noalloc(const float* f, const float* g, float
       q = cdiv(L, m);
     }
   }
-  if (q * m > kNoAllocTab) return HD_EUNSUPPORTED;
+  if (q * m > kNoAllocTab) return fail(HD_EUNSUPPORTED, "noalloc: q m beyond the static twiddle table (q m <= 532480)");
   int max_smem = 0;
-  if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-    return HD_ECUDA;
+  const cudaError_t ae = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (ae != cudaSuccess) return cuda_fail(ae, "noalloc: cudaDeviceGetAttribute");
   const size_t smem = rcm1d_smem_bytes((int)L, (int)m, true);
-  if (smem + 1024 > (size_t)max_smem) return HD_EUNSUPPORTED;
+  if (smem + 1024 > (size_t)max_smem) return fail(HD_EUNSUPPORTED, "noalloc: shared memory too small for m");
   cudaStream_t st = (cudaStream_t)stream;
   float2* tw = scratch;                // zeta_N^k, rewritten by every call
   float2* acc = scratch + kNoAllocTab; // zeroed by the kernel before use
-  if (launch_roots_fp64(tw, q * m, st) != cudaSuccess) return HD_ECUDA;
+  cudaError_t le = launch_roots_fp64(tw, q * m, st);
+  if (le != cudaSuccess) return cuda_fail(le, "noalloc: table launch");
   Launch1D la;
   std::memset(&la, 0, sizeof(la));
   la.one.L = (int32_t)L;
@@ -105,6 +110,7 @@ extern "C" hd_status hd_conv1d_rcm_noalloc(const float* f, const float* g, float
   la.one.gacc = acc;
   factor_radices((int)m, &la.plan_m);
   const int threads = threads_for_points(4 * m, kPts);
-  if (launch_rcm1d(la, 1, threads, smem, f, g, h, st) != cudaSuccess) return HD_ECUDA;
+  le = launch_rcm1d(la, 1, threads, smem, f, g, h, st);
+  if (le != cudaSuccess) return cuda_fail(le, "noalloc: convolution launch");
   return HD_OK;
 }

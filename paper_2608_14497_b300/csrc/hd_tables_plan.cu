@@ -12,7 +12,7 @@
 #include <cstdio>
 #include <cstring>
 
-#include "hd_fft_fast.cuh"
+#include "hd_cl_kernel.cuh"
 #include "hd_internal.h"
 
 namespace hd {
@@ -28,24 +28,14 @@ __global__ void k_roots_fp64(float2* __restrict__ tw, int64_t N) {
   }
 }
 
-// Per-length table of the cluster kernels (layout in hd_fft_fast.cuh): the
-// pass twiddles zeta_{Ns R}^{r jm} followed by zeta_n^l, each evaluated in FP64
-// from its exact rational angle and rounded once.
-__global__ void k_pass_table_fp64(float2* __restrict__ out, int n, int nps, int4 Rs0, int4 Rs1) {
-  const int Rs[8] = {Rs0.x, Rs0.y, Rs0.z, Rs0.w, Rs1.x, Rs1.y, Rs1.z, Rs1.w};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * n - 1; i += gridDim.x * blockDim.x) {
+// Per-length table of the cluster kernel for m = 256 R3 (layout cl::Shape in
+// hd_cl_kernel.cuh): pass twiddles of the radix-R3 and radix-16 passes, then
+// zeta_m^l for the digit-reversed positions; each entry evaluated in FP64 from
+// its exact rational angle and rounded once.
+__global__ void k_cl_table_fp64(float2* __restrict__ out, int R3, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     long long num, den;
-    if (i >= n - 1) {
-      num = i - (n - 1);
-      den = n;
-    } else {
-      int Ns = 1, k = 0;
-      while (k < nps && i >= Ns - 1 + (Rs[k] - 1) * Ns) Ns *= Rs[k++];
-      const int o = i - (Ns - 1);
-      const int r = o / Ns + 1, jm = o - (r - 1) * Ns;
-      num = (long long)r * jm;
-      den = (long long)Ns * Rs[k];
-    }
+    cl::table_angle(i, R3, &num, &den);
     double s, c;
     double x = (2.0 * (double)(num % den)) / (double)den;
     if (x > 1.0) x -= 2.0;
@@ -54,20 +44,33 @@ __global__ void k_pass_table_fp64(float2* __restrict__ out, int n, int nps, int4
   }
 }
 
+cudaStream_t TableCache::build_stream(hd_status* err) {
+  if (!build && cudaStreamCreateWithFlags(&build, cudaStreamNonBlocking) != cudaSuccess) {
+    build = nullptr;
+    *err = HD_ECUDA;
+  }
+  return build;
+}
+
 // Key space: padded lengths N > 0; per-length pass tables under -n.
-const float2* TableCache::get_pass_table(int n, cudaStream_t st, hd_status* err) {
+const float2* TableCache::get_pass_table(int n, cudaStream_t /*st*/, hd_status* err) {
   auto it = tabs.find(-(int64_t)n);
   if (it != tabs.end()) return it->second;
+  cudaStream_t bs = build_stream(err);
+  if (!bs) return nullptr;
+  if (n < 256 || n % 256) {
+    *err = HD_EINVAL;
+    return nullptr;
+  }
+  const int R3 = n / 256;
+  const int entries = (R3 - 1) * 256 + 240 + n;  // cl::Shape<R3>::TABN
   float2* p = nullptr;
-  if (cudaMalloc(&p, sizeof(float2) * (size_t)(2 * n)) != cudaSuccess) {
+  if (cudaMalloc(&p, sizeof(float2) * (size_t)entries) != cudaSuccess) {
     *err = HD_ENOMEM;
     return nullptr;
   }
-  int Rs[8] = {1, 1, 1, 1, 1, 1, 1, 1};
-  const int nps = fast_passes(n, Rs);
-  k_pass_table_fp64<<<(2 * n + 255) / 256, 256, 0, st>>>(p, n, nps, make_int4(Rs[0], Rs[1], Rs[2], Rs[3]),
-                                                          make_int4(Rs[4], Rs[5], Rs[6], Rs[7]));
-  if (cudaGetLastError() != cudaSuccess) {
+  k_cl_table_fp64<<<(entries + 255) / 256, 256, 0, bs>>>(p, R3, entries);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(bs) != cudaSuccess) {
     cudaFree(p);
     *err = HD_ECUDA;
     return nullptr;
@@ -76,9 +79,11 @@ const float2* TableCache::get_pass_table(int n, cudaStream_t st, hd_status* err)
   return p;
 }
 
-const float2* TableCache::get(int64_t N, cudaStream_t st, hd_status* err) {
+const float2* TableCache::get(int64_t N, cudaStream_t /*st*/, hd_status* err) {
   auto it = tabs.find(N);
   if (it != tabs.end()) return it->second;
+  cudaStream_t bs = build_stream(err);
+  if (!bs) return nullptr;
   float2* p = nullptr;
   if (cudaMalloc(&p, sizeof(float2) * (size_t)N) != cudaSuccess) {
     *err = HD_ENOMEM;
@@ -87,8 +92,8 @@ const float2* TableCache::get(int64_t N, cudaStream_t st, hd_status* err) {
   int threads = 256;
   int64_t blocks64 = (N + threads - 1) / threads;
   int blocks = (int)(blocks64 < 4096 ? blocks64 : 4096);
-  k_roots_fp64<<<blocks, threads, 0, st>>>(p, N);
-  if (cudaGetLastError() != cudaSuccess) {
+  k_roots_fp64<<<blocks, threads, 0, bs>>>(p, N);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(bs) != cudaSuccess) {
     cudaFree(p);
     *err = HD_ECUDA;
     return nullptr;
@@ -100,6 +105,8 @@ const float2* TableCache::get(int64_t N, cudaStream_t st, hd_status* err) {
 void TableCache::clear() {
   for (auto& kv : tabs) cudaFree(kv.second);
   tabs.clear();
+  if (build) cudaStreamDestroy(build);
+  build = nullptr;
 }
 
 // Radix sequence for a DFT of length n: radix 16, 8, 4, 2 for the power of
@@ -152,6 +159,24 @@ int64_t ladder_ceil(int64_t n) {
     best = std::min(best, x);
   }
   return best;
+}
+
+// Raise a kernel's dynamic shared-memory limit to at least `smem` on the
+// current device, once: the limit is a per-device property of the function,
+// so later launches of the same size skip the driver call.
+cudaError_t smem_optin(const void* fn, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> set;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = set[{dev, fn}];
+  if (cur >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) cur = smem;
+  return e;
 }
 
 hd_status ensure_ws(hd_ctx* c, size_t bytes) {

@@ -9,7 +9,9 @@ is collected last so that a first failure here comes after every other test.
 import numpy as np
 import pytest
 
+import oracle
 from paper_2608_14497_b300 import inputs
+from tests.conftest import record_rel, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -41,9 +43,19 @@ def test_noalloc_matches_regular_entry_point(hd, L, prm):
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
         assert rel(out, ref) <= TOL
+    if L >= 33333:
+        # and directly against the FP64 oracle (O2)
+        exact = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+        err = record_rel(f"noalloc 1D L={L} prm={prm}", rel_l2(out.cpu().numpy(), exact), TOL, L)
+        assert err <= TOL
 
 
 def test_noalloc_rejects_beyond_limit(hd):
     x = torch.zeros(8, device="cuda")
     assert hd.hd_conv1d_rcm_noalloc(x.data_ptr(), x.data_ptr(), x.data_ptr(), 524289, None, 0) == hd.HD_EUNSUPPORTED
+    assert b"524288" in hd.load().hd_last_error_string()
     assert hd.hd_conv1d_rcm_noalloc(x.data_ptr(), x.data_ptr(), x.data_ptr(), 0, None, 0) == hd.HD_EINVAL
+    # q m just above the table's 532480 entries
+    assert hd.hd_conv1d_rcm_noalloc(x.data_ptr(), x.data_ptr(), x.data_ptr(), 4096, [(4096, 131)], 0) == \
+        hd.HD_EUNSUPPORTED
+    assert b"q m" in hd.load().hd_last_error_string()
