@@ -43,9 +43,8 @@ WORKLOAD = "1D batched: 4096 real convolutions, L ~ U{500..70000} (seed 2), N(0,
 
 # Sources compiled into the batched kernel's translation unit (the DRAM-traffic
 # record is valid only for these exact files).
-CLUSTER_SOURCES = ("hd_cluster_kernel.cuh", "hd_cluster_c1.cu", "hd_cluster_c2.cu", "hd_cluster_c4.cu",
-                   "hd_cluster_c8.cu", "hd_cluster.cuh", "hd_fft_fast.cuh", "hd_fft.cuh", "hd_conv1d.cuh",
-                   "hd_internal.h")
+CLUSTER_SOURCES = ("hd_cl_kernel.cuh", "hd_cl_launch.cuh", "hd_cl_c1.cu", "hd_cl_c1b.cu", "hd_cl_c2.cu",
+                   "hd_cl_c4.cu", "hd_cl_c8.cu", "hd_cluster.cuh", "hd_bfly.cuh", "hd_conv1d.cuh", "hd_internal.h")
 
 
 def _code_only(text):
@@ -271,8 +270,9 @@ def run_gpu(args):
     ms_step = ms / args.steps
     value = whole_job_rate(n, world, args.steps, ms)
 
-    # dominant kernel: k_rcm1d_cluster, every launch of the step (one per cluster
-    # size, concurrent; timed together by the events on the joining stream).
+    # dominant kernel: k_rcm_cl, every launch of the step (one per built
+    # instance (C, m) in the plan, the cluster sizes on concurrent streams;
+    # timed together by the events on the joining stream).
     # FP32-ALU roofline: algorithmic flops of the FFT convolutions, 15 L log2 L
     # + 6 L per item (three real transforms of length 2L at 2.5 (2L) log2(2L),
     # i.e. 5 L log2 L each to first order, plus the spectral products), over
@@ -285,7 +285,7 @@ def run_gpu(args):
     peak_alu = 148 * 128 * 2 * 2.032e9 / 1e12
     achieved_tf = alg_flops / (ms_step * 1e-3) / 1e12
     achieved_gbs = alg_bytes / (ms_step * 1e-3) / 1e9
-    traffic = recorded_traffic("k_rcm1d_cluster", args.algo)
+    traffic = recorded_traffic("k_rcm_cl", args.algo)
 
     # end to end: pinned host buffers, copies inside the timed region.  The
     # batch is cut into E2E_CHUNKS runs of consecutive items, each with its own
@@ -377,7 +377,7 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_alu, "unit": "TFLOP/s",
                      "frac": achieved_tf / peak_alu, "traffic": traffic,
                      "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
-                     "kernel": ("k_rcm1d_cluster<C> (all launches of one step)" if args.algo == "hybridRCM"
+                     "kernel": ("k_rcm_cl<C, R3> (all launches of one step)" if args.algo == "hybridRCM"
                                 else "k_cs1d"),
                      "traffic_unit": "DRAM bytes per step (all launches of one batched call)",
                      "algorithmic_flops_per_launch": alg_flops, "algorithmic_bytes_per_launch": alg_bytes,
@@ -387,8 +387,8 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "autotune": {"candidates": len(hd.hd_tuning_table(plan.ctx))},
     }
-    if args.compare:
-        line["comparisons"] = compare_suite()
+    if not args.no_compare:
+        line["comparisons"] = compare_suite(peak_hbm)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -400,30 +400,43 @@ def plan_launches(plan):
     return plan.launches
 
 
-def compare_suite(reps=10):
-    """Same-GPU comparison of the four algorithms on the paper-shaped configs
-    (1D L=4096, 2D L in {1024, 2048, 3000}, 3D L in {256, 384}) and the
-    differentiable 2D workload (batch 16 of 1024^2, forward + adjoint): median
-    of `reps` CUDA-event timings per call after warm-up, inputs resident in HBM.
-    Arrays smaller than L2 are timed L2-warm (noted per entry)."""
+def compare_suite(peak_hbm, reps=20):
+    """Same-GPU comparison of the four algorithms (hybridRCM, hybridCS,
+    explicitRCM, explicit) on the paper-shaped configs: 1D L=4096 (one
+    convolution per call), 2D L in {1024, 2048, 3000}, 3D L in {256, 384} (FP32
+    and the split-precision option), and the differentiable 2D workload (batch
+    16 of 1024^2, forward + adjoint).  Each call is captured once in a CUDA
+    graph after warm-up calls and replayed `reps` times between two CUDA events
+    (device time per call, no host overhead); inputs resident in HBM; arrays
+    smaller than the L2 are timed L2-warm (noted per entry).  Per entry: ms,
+    convolutions/s and the 12 L^d algorithmic bytes per convolution over the
+    time as a fraction of the measured HBM bandwidth."""
     import torch
     import paper_2608_14497_b300 as hd
     from paper_2608_14497_b300 import inputs
     out = {}
 
-    def time_call(fn):
+    def time_graph(fn, n=reps):
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
-        ts = []
-        for _ in range(reps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
+        s = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
             fn()
-            b.record()
             torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        return statistics.median(ts)
+            with torch.cuda.graph(graph, stream=s):
+                fn()
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            graph.replay()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
 
     cases = [("1D L=4096", (4096,), 1), ("2D L=1024", (1024, 1024), 4), ("2D L=2048", (2048, 2048), 4),
              ("2D L=3000", (3000, 3000), 4), ("3D L=256", (256, 256, 256), 5), ("3D L=384", (384, 384, 384), 5)]
@@ -438,10 +451,17 @@ def compare_suite(reps=10):
         for algo, prec in variants:
             key = algo if prec == "fp32" else f"{algo}[{prec}]"
             try:
-                ms = time_call(lambda: hd.conv(tf, tg, algo=algo, out=h, prec=prec))
-                row[key] = {"ms": ms, "conv_per_s": 1e3 / ms, "GBps_12B": 12 * f.size / (ms * 1e-3) / 1e9}
+                ms = time_graph(lambda: hd.conv(tf, tg, algo=algo, out=h, prec=prec),
+                                n=reps * (50 if len(shape) == 1 else 1))
+                gbs = 12 * f.size / (ms * 1e-3) / 1e9
+                row[key] = {"ms": round(ms, 5), "conv_per_s": round(1e3 / ms, 1),
+                            "hbm_frac": round(gbs / peak_hbm, 4)}
             except Exception as e:  # unsupported size for an algorithm
                 row[key] = {"error": str(e)[:80]}
+        hyb = [row[k]["ms"] for k in ("hybridRCM", "hybridCS") if "ms" in row.get(k, {})]
+        exp = [row[k]["ms"] for k in ("explicitRCM", "explicit") if "ms" in row.get(k, {})]
+        if hyb and exp:
+            row["explicit_over_hybrid"] = round(min(exp) / min(hyb), 3)
         out[name] = row
         del tf, tg, h
         torch.cuda.empty_cache()
@@ -455,7 +475,17 @@ def compare_suite(reps=10):
         tg.grad = None
         hd.hd_conv_fn(tf, tg, "hybridRCM").backward(u)
 
-    out["2D adjoint batch16 L=1024 (fwd+bwd)"] = {"ms": time_call(fwd_bwd)}
+    for _ in range(3):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(10):
+        fwd_bwd()
+    b.record()
+    torch.cuda.synchronize()
+    out["2D adjoint batch16 L=1024 (fwd+bwd, hybridRCM)"] = {"ms": round(a.elapsed_time(b) / 10, 4),
+                                                           "timing": "CUDA events over 10 eager steps"}
     return out
 
 
@@ -496,8 +526,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="accepted for compatibility; no effect")
-    ap.add_argument("--compare", action="store_true",
-                    help="add same-GPU timings of all algorithms on the 1D/2D/3D configs")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the same-GPU timings of all algorithms on the 1D/2D/3D configs")
+    ap.add_argument("--compare", action="store_true", help="accepted for compatibility (the comparison is default)")
     ap.add_argument("--nd", default=None,
                     help="time one 1D/2D/3D convolution of this shape instead (e.g. 384,384,384); for profiling")
     ap.add_argument("--nd-algo", default="hybridRCM", choices=["hybridRCM", "hybridCS", "explicitRCM", "explicit"])

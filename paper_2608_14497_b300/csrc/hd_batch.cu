@@ -6,11 +6,12 @@
 // distinct padded lengths N = qm share one twiddle table, and items are grouped
 // into one launch (block size and shared memory of the largest item), ordered
 // longest first so the block scheduler balances the tail.  hybridRCM lengths
-// the cluster kernel covers form one class per cluster size C; the classes run
-// concurrently on streams forked from the caller's stream and joined back
-// (8-CTA clusters pack into the GPCs less densely than smaller ones, so the
-// smaller classes fill the SMs the C = 8 class cannot use; the C = 8 class
-// runs at the higher stream priority).  Everything the kernels read (item
+// the cluster kernel covers form one class per built instance (cluster size
+// C, residue length m); the classes of one C run back to back on one stream,
+// the streams of the different C concurrently, forked from the caller's
+// stream and joined back (8-CTA clusters pack into the GPCs less densely than
+// smaller ones, so the smaller clusters fill the SMs the C = 8 class cannot
+// use; the C = 8 stream runs at the higher priority).  Everything the kernels read (item
 // table, radix plans, tables, accumulator scratch) is uploaded or allocated
 // here, so a launch of the plan performs no allocation and no host-to-device
 // copy and can be captured in a CUDA graph.
@@ -34,10 +35,10 @@ struct LaunchClass {
 };
 struct ClusterClass {
   int first = 0, count = 0;  // range in the device cluster item table
-  int C = 0;
-  size_t smem = 0;
+  int C = 0, m = 0;
+  int stream = 0;            // index of the side stream (one per cluster size)
 };
-constexpr int kMaxClusterClasses = 4;  // C in {8, 4, 2, 1}
+constexpr int kMaxClusterStreams = 4;  // C in {8, 4, 2, 1}
 }  // namespace hd
 
 struct hd_batch_plan {
@@ -52,9 +53,10 @@ struct hd_batch_plan {
   // cluster path (hybridRCM): one class per cluster size, concurrent streams
   hd::CItem* d_citems = nullptr;
   std::vector<hd::ClusterClass> cclasses;
-  cudaStream_t side[hd::kMaxClusterClasses] = {};
+  int nstreams = 0;
+  cudaStream_t side[hd::kMaxClusterStreams] = {};
   cudaEvent_t fork = nullptr;
-  cudaEvent_t join[hd::kMaxClusterClasses] = {};
+  cudaEvent_t join[hd::kMaxClusterStreams] = {};
 };
 
 using namespace hd;
@@ -107,7 +109,6 @@ extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, co
       ci.m = m;
       ci.p = p;
       ci.C = C;
-      ci.plan = plan_index(m);
       ci.tw = tw;
       ci.tabm = c->tables.get_pass_table(m, 0, &terr);
       if (!ci.tabm) return terr;
@@ -167,34 +168,39 @@ extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, co
     lc.threads = std::max(lc.threads, hs[i].P.threads);
     lc.smem = std::max(lc.smem, hs[i].P.smem);
   }
-  // cluster classes: by C (largest first), lengths descending within a class
+  // cluster classes: by C (largest first), then m (largest first); lengths
+  // descending within a class; one side stream per C
   if (!citems.empty()) {
     std::stable_sort(citems.begin(), citems.end(), [](const CItem& a, const CItem& b) {
       if (a.C != b.C) return a.C > b.C;
+      if (a.m != b.m) return a.m > b.m;
       return a.L > b.L;
     });
     for (size_t i = 0; i < citems.size(); ++i) {
-      if (bp->cclasses.empty() || bp->cclasses.back().C != citems[i].C) {
+      if (bp->cclasses.empty() || bp->cclasses.back().C != citems[i].C || bp->cclasses.back().m != citems[i].m) {
         ClusterClass k;
         k.first = (int)i;
         k.C = citems[i].C;
+        k.m = citems[i].m;
+        k.stream = bp->cclasses.empty() ? 0
+                   : bp->cclasses.back().stream + (bp->cclasses.back().C != citems[i].C ? 1 : 0);
         bp->cclasses.push_back(k);
       }
       ClusterClass& k = bp->cclasses.back();
       ++k.count;
-      k.smem = std::max(k.smem, cluster_smem_bytes(citems[i].m));
       bp->total_len += citems[i].L;
     }
+    bp->nstreams = bp->cclasses.back().stream + 1;
     if (cudaMalloc(&bp->d_citems, sizeof(CItem) * citems.size()) != cudaSuccess) {
       hd_batch_plan_destroy(bp);
       return HD_ENOMEM;
     }
     cudaMemcpy(bp->d_citems, citems.data(), sizeof(CItem) * citems.size(), cudaMemcpyHostToDevice);
-    if (bp->cclasses.size() > 1) {
+    if (bp->nstreams > 1) {
       int lo = 0, hi = 0;
       cudaDeviceGetStreamPriorityRange(&lo, &hi);
       bool ok = cudaEventCreateWithFlags(&bp->fork, cudaEventDisableTiming) == cudaSuccess;
-      for (size_t k = 0; k < bp->cclasses.size() && ok; ++k) {
+      for (int k = 0; k < bp->nstreams && ok; ++k) {
         ok = cudaStreamCreateWithPriority(&bp->side[k], cudaStreamNonBlocking, k == 0 ? hi : lo) == cudaSuccess &&
              cudaEventCreateWithFlags(&bp->join[k], cudaEventDisableTiming) == cudaSuccess;
       }
@@ -227,7 +233,7 @@ extern "C" hd_status hd_batch_plan_destroy(hd_batch_plan* bp) {
   if (bp->d_plans) cudaFree(bp->d_plans);
   if (bp->d_acc) cudaFree(bp->d_acc);
   if (bp->d_citems) cudaFree(bp->d_citems);
-  for (int k = 0; k < kMaxClusterClasses; ++k) {
+  for (int k = 0; k < kMaxClusterStreams; ++k) {
     if (bp->side[k]) cudaStreamDestroy(bp->side[k]);
     if (bp->join[k]) cudaEventDestroy(bp->join[k]);
   }
@@ -242,27 +248,31 @@ extern "C" hd_status hd_conv1d_batched(hd_ctx* c, const hd_batch_plan* bp, const
   cudaSetDevice(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   const int ncc = (int)bp->cclasses.size();
-  if (ncc == 1) {
-    const ClusterClass& k = bp->cclasses[0];
-    ClusterLaunch cl;
-    std::memset(&cl, 0, sizeof(cl));
-    cl.items = bp->d_citems + k.first;
-    if (launch_rcm1d_cluster(cl, k.C, k.count, k.smem, f, g, h, st) != cudaSuccess) return HD_ECUDA;
-  } else if (ncc > 1) {
-    // fork: every class on its own stream after the work already on `st`; join
-    if (cudaEventRecord(bp->fork, st) != cudaSuccess) return HD_ECUDA;
+  if (bp->nstreams == 1) {
     for (int i = 0; i < ncc; ++i) {
       const ClusterClass& k = bp->cclasses[i];
       ClusterLaunch cl;
       std::memset(&cl, 0, sizeof(cl));
       cl.items = bp->d_citems + k.first;
-      if (cudaStreamWaitEvent(bp->side[i], bp->fork, 0) != cudaSuccess ||
-          launch_rcm1d_cluster(cl, k.C, k.count, k.smem, f, g, h, bp->side[i]) != cudaSuccess ||
-          cudaEventRecord(bp->join[i], bp->side[i]) != cudaSuccess)
-        return HD_ECUDA;
+      if (launch_rcm1d_cluster(cl, k.C, k.m, k.count, f, g, h, st) != cudaSuccess) return HD_ECUDA;
     }
-    for (int i = 0; i < ncc; ++i)
-      if (cudaStreamWaitEvent(st, bp->join[i], 0) != cudaSuccess) return HD_ECUDA;
+  } else if (bp->nstreams > 1) {
+    // fork: every cluster size on its own stream after the work already on
+    // `st`; join back
+    if (cudaEventRecord(bp->fork, st) != cudaSuccess) return HD_ECUDA;
+    for (int s2 = 0; s2 < bp->nstreams; ++s2)
+      if (cudaStreamWaitEvent(bp->side[s2], bp->fork, 0) != cudaSuccess) return HD_ECUDA;
+    for (int i = 0; i < ncc; ++i) {
+      const ClusterClass& k = bp->cclasses[i];
+      ClusterLaunch cl;
+      std::memset(&cl, 0, sizeof(cl));
+      cl.items = bp->d_citems + k.first;
+      if (launch_rcm1d_cluster(cl, k.C, k.m, k.count, f, g, h, bp->side[k.stream]) != cudaSuccess) return HD_ECUDA;
+    }
+    for (int s2 = 0; s2 < bp->nstreams; ++s2)
+      if (cudaEventRecord(bp->join[s2], bp->side[s2]) != cudaSuccess ||
+          cudaStreamWaitEvent(st, bp->join[s2], 0) != cudaSuccess)
+        return HD_ECUDA;
   }
   for (const LaunchClass& lc : bp->classes) {
     Launch1D la;

@@ -1,32 +1,37 @@
 // hd_cluster.cu -- host side of the cluster hybridRCM kernel (the fast path
-// of the batched and single 1D calls; the kernel is in hd_cluster_kernel.cuh):
-// the ladder of residue DFT lengths, the parameter choice per length, the
-// autotuner and the launch dispatch over cluster sizes.
+// of the batched and single 1D calls; the kernel is in hd_cl_kernel.cuh and
+// hd_cl_launch.cuh): the built instances (C, m), the parameter choice per
+// length, the autotuner and the launch dispatch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
-#include <map>
 #include <vector>
 
 #include "hd_cluster.cuh"
 
 namespace hd {
 
-// ---------------------------------------------------------------------------
-// host side
-// ---------------------------------------------------------------------------
-// Candidate DFT lengths: {1, 3, 5, 9} x 2^a with a >= 4 (the lengths of the
-// structured engine, cta_fft_struct) up to the cap (few distinct lengths, so
-// twiddle tables are shared across a batch and stay in L2).
-static const std::vector<int>& ladder() {
-  static std::vector<int> v;
-  if (v.empty()) {
-    for (int base : {1, 3, 5, 9})
-      for (int x = 16 * base; x <= kClusterMaxM; x *= 2) v.push_back(x);
-    std::sort(v.begin(), v.end());
-    v.erase(std::unique(v.begin(), v.end()), v.end());
-  }
+// Built instances: m = 256 R3.  One CTA covers L <= 2 m for every R3; the
+// larger clusters start where the next smaller one ends (L > C * 4608), so
+// they need m > 2304, R3 in {10, 12, 16, 18}.
+static const int kR3One[] = {1, 2, 3, 4, 5, 6, 8, 9, 10, 12, 16, 18};
+static const int kR3Many[] = {10, 12, 16, 18};
+
+bool cluster_instance(int C, int m) {
+  if (m % 256) return false;
+  const int R3 = m / 256;
+  if (C == 1) return std::find(std::begin(kR3One), std::end(kR3One), R3) != std::end(kR3One);
+  if (C == 2 || C == 4 || C == 8) return std::find(std::begin(kR3Many), std::end(kR3Many), R3) != std::end(kR3Many);
+  return false;
+}
+
+// Every built (C, m), in increasing m per C.
+static std::vector<std::pair<int, int>> instances() {
+  std::vector<std::pair<int, int>> v;
+  for (int r : kR3One) v.push_back({1, 256 * r});
+  for (int C = 2; C <= 8; C *= 2)
+    for (int r : kR3Many) v.push_back({C, 256 * r});
   return v;
 }
 
@@ -34,14 +39,11 @@ bool cluster_params(int64_t L, int* C_out, int* m_out, int* p_out, const Cluster
   if (L < 1) return false;
   const int64_t Lp = (L + 1) / 2;
   if (tun && tun->valid) {
-    // cheapest measured candidate among the three shortest feasible lengths of each C
+    // the cheapest measured instance whose padded length 2 C m covers L
     double best = 1e300;
-    int seen[4] = {0, 0, 0, 0};
     for (size_t i = 0; i < tun->C.size(); ++i) {
       const int C = tun->C[i], mm = tun->m[i];
-      const int ci = C == 1 ? 0 : C == 2 ? 1 : C == 4 ? 2 : 3;
-      if ((int64_t)2 * C * mm < L || seen[ci] >= 3) continue;
-      ++seen[ci];
+      if ((int64_t)2 * C * mm < L || !cluster_instance(C, mm)) continue;
       if (tun->us[i] < best) {
         best = tun->us[i];
         *C_out = C;
@@ -51,29 +53,19 @@ bool cluster_params(int64_t L, int* C_out, int* m_out, int* p_out, const Cluster
     }
     if (best < 1e300) return true;
   }
-  for (int C = 1; C <= 8; C *= 2) {
-    const int64_t need = (L + 2 * C - 1) / (2 * C);  // q m >= L, q = 2C
-    for (int mm : ladder()) {
-      if (mm >= need) {
-        *C_out = C;
-        *m_out = mm;
-        *p_out = (int)((Lp + mm - 1) / mm);
-        return true;
-      }
+  for (const auto& cm : instances()) {
+    if ((int64_t)2 * cm.first * cm.second >= L) {
+      *C_out = cm.first;
+      *m_out = cm.second;
+      *p_out = (int)((Lp + cm.second - 1) / cm.second);
+      return true;
     }
   }
   return false;
 }
 
 hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out) {
-  // candidates in increasing m per C (cluster_params relies on that order)
-  std::vector<int> Cs, ms;
-  for (int C = 1; C <= 8; C *= 2)
-    for (int mm : ladder())
-      if (mm >= 64) {
-        Cs.push_back(C);
-        ms.push_back(mm);
-      }
+  const std::vector<std::pair<int, int>> cand = instances();
   const int64_t budget = int64_t{1} << 22;  // real elements per timed batch
   float *f = nullptr, *g = nullptr, *h = nullptr;
   CItem* d_items = nullptr;
@@ -81,7 +73,7 @@ hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaMalloc(&f, sizeof(float) * budget) != cudaSuccess || cudaMalloc(&g, sizeof(float) * budget) != cudaSuccess ||
       cudaMalloc(&h, sizeof(float) * budget) != cudaSuccess ||
-      cudaMalloc(&d_items, sizeof(CItem) * 4096) != cudaSuccess) {
+      cudaMalloc(&d_items, sizeof(CItem) * 16384) != cudaSuccess) {
     st = HD_ENOMEM;
   }
   if (st == HD_OK) {
@@ -93,11 +85,10 @@ hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out) {
   out->C.clear();
   out->m.clear();
   out->us.clear();
-  for (size_t i = 0; i < Cs.size() && st == HD_OK; ++i) {
-    const int C = Cs[i], mm = ms[i];
+  for (size_t i = 0; i < cand.size() && st == HD_OK; ++i) {
+    const int C = cand[i].first, mm = cand[i].second;
     const int64_t L = (int64_t)2 * C * mm;
-    const int64_t K = std::max<int64_t>(1, std::min<int64_t>(budget / L, 4096));
-    if (K * L > budget) continue;
+    const int64_t K = std::max<int64_t>(1, std::min<int64_t>(budget / L, 16384));
     hd_status terr = HD_OK;
     const float2* tw = c->tables.get(L, 0, &terr);
     const float2* tabm = tw ? c->tables.get_pass_table(mm, 0, &terr) : nullptr;
@@ -120,8 +111,7 @@ hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out) {
     ClusterLaunch cl;
     std::memset(&cl, 0, sizeof(cl));
     cl.items = d_items;
-    const size_t smem = cluster_smem_bytes(mm);
-    if (launch_rcm1d_cluster(cl, C, (int)K, smem, f, g, h, 0) != cudaSuccess) {
+    if (launch_rcm1d_cluster(cl, C, mm, (int)K, f, g, h, 0) != cudaSuccess) {
       st = HD_ECUDA;
       break;
     }
@@ -130,7 +120,7 @@ hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out) {
     float best_ms = 1e30f;
     for (int trial = 0; trial < 3 && st == HD_OK; ++trial) {
       cudaEventRecord(e0, 0);
-      for (int rep = 0; rep < 2; ++rep) launch_rcm1d_cluster(cl, C, (int)K, smem, f, g, h, 0);
+      for (int rep = 0; rep < 2; ++rep) launch_rcm1d_cluster(cl, C, mm, (int)K, f, g, h, 0);
       cudaEventRecord(e1, 0);
       if (cudaEventSynchronize(e1) != cudaSuccess) {
         st = HD_ECUDA;
@@ -155,15 +145,15 @@ hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out) {
   return st;
 }
 
-size_t cluster_smem_bytes(int m_max) { return sizeof(float2) * 5 * (size_t)swz_stride(m_max); }
-
-cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int C, int nitems, size_t smem, const float* f,
-                                 const float* g, float* h, cudaStream_t st) {
+cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int C, int m, int nitems, const float* f, const float* g,
+                                 float* h, cudaStream_t st) {
+  if (!cluster_instance(C, m) || nitems < 1) return cudaErrorInvalidValue;
+  const int R3 = m / 256;
   switch (C) {
-    case 1: return launch_cluster_c1(cl, nitems, smem, f, g, h, st);
-    case 2: return launch_cluster_c2(cl, nitems, smem, f, g, h, st);
-    case 4: return launch_cluster_c4(cl, nitems, smem, f, g, h, st);
-    case 8: return launch_cluster_c8(cl, nitems, smem, f, g, h, st);
+    case 1: return R3 <= 6 ? launch_cl_c1(R3, cl, nitems, f, g, h, st) : launch_cl_c1b(R3, cl, nitems, f, g, h, st);
+    case 2: return launch_cl_c2(R3, cl, nitems, f, g, h, st);
+    case 4: return launch_cl_c4(R3, cl, nitems, f, g, h, st);
+    case 8: return launch_cl_c8(R3, cl, nitems, f, g, h, st);
   }
   return cudaErrorInvalidValue;
 }

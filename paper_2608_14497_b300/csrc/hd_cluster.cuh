@@ -1,4 +1,5 @@
-// hd_cluster.cuh -- descriptors of the cluster hybridRCM kernel.
+// hd_cluster.cuh -- descriptors and host interface of the cluster hybridRCM
+// kernel (hd_cl_kernel.cuh, hd_cl_launch.cuh).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -7,45 +8,46 @@
 
 namespace hd {
 
-constexpr int kClusterCtas = 8;       // largest cluster (C = 8 CTAs, q = 16 residues)
-constexpr int kClusterThreads = 512;  // threads per CTA
-constexpr int kClusterPts = 24;       // FFT points per thread per pass
-constexpr int kClusterMaxM = 4608;    // largest residue DFT length (shared memory)
+constexpr int kClusterCtas = 8;     // largest cluster (C = 8 CTAs, q = 16 residues)
+constexpr int kClusterMaxM = 4608;  // largest residue DFT length (M = 256 R3, R3 <= 18)
 
-// One convolution: q = 2C residues of length m, p = ceil(Lp/m) <= C.
+// One convolution: q = 2C residues of length m = 256 R3, p = ceil(Lp/m) <= C.
 struct CItem {
   int64_t off;
   int32_t L, m, p, C;
-  int32_t plan;
-  int32_t pad_;
   const float2* tw;    // zeta_N^k, N = 2 C m
-  const float2* tabm;  // per-length table: pass twiddles, then zeta_m^l (hd_fft_fast.cuh)
+  const float2* tabm;  // per-length table of the kernel's passes and product (cl::Shape)
 };
 
-// Items of one launch (all of the same C, one cluster each), or one item by
-// value (items == nullptr).
+// Items of one launch (all of the same (C, m), one cluster each), or one item
+// by value (items == nullptr).
 struct ClusterLaunch {
   const CItem* items;
   CItem one_item;
 };
 
-// (C, m, p) for a length: the measured cheapest candidate when `tun` holds an
-// autotuner table, else the smallest cluster whose largest ladder length
+// Whether the kernel is built for clusters of C CTAs with residue length m.
+bool cluster_instance(int C, int m);
+// (C, m, p) for a length: the measured cheapest built instance when `tun`
+// holds an autotuner table, else the smallest cluster whose largest length
 // suffices, with the smallest such length.
 bool cluster_params(int64_t L, int* C, int* m, int* p, const ClusterTuning* tun = nullptr);
-// Time every candidate on synthetic batches (device scratch, a few tens of MB).
+// Time every built instance on synthetic batches (device scratch, ~50 MB).
 hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out);
-size_t cluster_smem_bytes(int m_max);
-// Launch over `nitems` convolutions of the same C (clusters of C CTAs).
-cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int C, int nitems, size_t smem, const float* f,
+// Launch over `nitems` convolutions of the same (C, m) (clusters of C CTAs).
+cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int C, int m, int nitems, const float* f,
                                  const float* g, float* h, cudaStream_t st);
-cudaError_t launch_cluster_c1(const ClusterLaunch& cl, int nitems, size_t smem, const float* f, const float* g,
-                              float* h, cudaStream_t st);
-cudaError_t launch_cluster_c2(const ClusterLaunch& cl, int nitems, size_t smem, const float* f, const float* g,
-                              float* h, cudaStream_t st);
-cudaError_t launch_cluster_c4(const ClusterLaunch& cl, int nitems, size_t smem, const float* f, const float* g,
-                              float* h, cudaStream_t st);
-cudaError_t launch_cluster_c8(const ClusterLaunch& cl, int nitems, size_t smem, const float* f, const float* g,
-                              float* h, cudaStream_t st);
+// Per-cluster-size dispatch over R3 = m / 256 (hd_cl_c*.cu); cudaErrorInvalidValue
+// for an instance that is not built.
+cudaError_t launch_cl_c1(int R3, const ClusterLaunch& cl, int nitems, const float* f, const float* g, float* h,
+                         cudaStream_t st);
+cudaError_t launch_cl_c1b(int R3, const ClusterLaunch& cl, int nitems, const float* f, const float* g, float* h,
+                          cudaStream_t st);
+cudaError_t launch_cl_c2(int R3, const ClusterLaunch& cl, int nitems, const float* f, const float* g, float* h,
+                         cudaStream_t st);
+cudaError_t launch_cl_c4(int R3, const ClusterLaunch& cl, int nitems, const float* f, const float* g, float* h,
+                         cudaStream_t st);
+cudaError_t launch_cl_c8(int R3, const ClusterLaunch& cl, int nitems, const float* f, const float* g, float* h,
+                         cudaStream_t st);
 
 }  // namespace hd

@@ -296,8 +296,7 @@ int threads_for_points(int64_t points, int pts) {
 // Raise the kernel's dynamic shared-memory limit to what this launch needs.
 template <typename K>
 static cudaError_t allow_smem(K kernel, size_t smem) {
-  if (smem <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return smem_optin((const void*)kernel, smem);
 }
 
 cudaError_t launch_rcm1d(const Launch1D& la, int nitems, int threads, size_t smem, const float* f, const float* g,

@@ -669,8 +669,8 @@ struct nodeduce {
 template <typename... A>
 cudaError_t launch_kernel(void (*k)(A...), unsigned grid, int T, size_t smem, cudaStream_t st,
                           typename nodeduce<A>::type... args) {
-  if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    const cudaError_t e = smem_optin((const void*)k, smem);
     if (e != cudaSuccess) return e;
   }
   void* argv[] = {(void*)&args...};

@@ -83,12 +83,11 @@ def test_autotune_table_matches_direct_timing(hd):
     if not tab:
         pytest.skip("autotuner disabled (HD_AUTOTUNE=0)")
     assert all(us > 0 for _, _, us in tab)
-    # the planner's rule: cheapest of the three shortest feasible lengths per C
-    seen, best = {}, None
+    # the planner's rule: the cheapest measured instance whose 2 C m covers L
+    best = None
     for C, m, us in tab:
-        if 2 * C * m < L or seen.get(C, 0) >= 3:
+        if 2 * C * m < L:
             continue
-        seen[C] = seen.get(C, 0) + 1
         if best is None or us < best[2]:
             best = (C, m, us)
     assert best is not None
@@ -129,7 +128,7 @@ def test_batched_graph_replay_matches_eager(hd):
     off, f, g = flat(Ls, 45)
     tf, tg = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
     plan = hd.BatchPlan(off, Ls, algo="hybridRCM")
-    assert 1 <= plan.launches <= 5
+    assert 1 <= plan.launches <= 25  # one per (cluster size, residue length) class, plus the one-CTA kernel
     h_eager = plan(tf, tg).clone()
     h = torch.zeros_like(tf)
     s = torch.cuda.Stream()
