@@ -28,8 +28,23 @@ def stale():
     return any(os.path.getmtime(p) > t for p in deps())
 
 
+def _includes(path, seen=None):
+    """The file and every local header it includes ("..." includes), transitively."""
+    import re
+    seen = set() if seen is None else seen
+    if path in seen or not os.path.exists(path):
+        return seen
+    seen.add(path)
+    with open(path, encoding="utf-8") as fh:
+        for name in re.findall(r'^\s*#\s*include\s+"([^"]+)"', fh.read(), flags=re.M):
+            _includes(os.path.normpath(os.path.join(os.path.dirname(path), name)), seen)
+    return seen
+
+
 def build(force=False, verbose=False, extra=()):
-    """Compile every .cu to an object in parallel, then link the shared library."""
+    """Compile every .cu to an object in parallel (only the objects older than
+    their source or one of its local headers, unless forced or given extra
+    flags), then link the shared library."""
     if not force and not stale():
         return LIB
     bdir = os.path.join(HERE, "_build")
@@ -38,6 +53,10 @@ def build(force=False, verbose=False, extra=()):
     for src in sources():
         obj = os.path.join(bdir, os.path.basename(src) + ".o")
         objs.append(obj)
+        if not force and not extra and os.path.exists(obj):
+            t = os.path.getmtime(obj)
+            if all(os.path.getmtime(d) <= t for d in _includes(src)):
+                continue
         cmd = [NVCC, *ARCH, *FLAGS[:-1], "-c", *extra, "-o", obj, src]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)

@@ -118,6 +118,7 @@ static hd_status conv1d_rcm_cluster(hd_ctx* c, const float* f, const float* g, f
   if (!tw) return fail(terr, "twiddle table allocation failed");
   ClusterLaunch cl;
   std::memset(&cl, 0, sizeof(cl));
+  cl.err = c->dev_err;
   cl.one_item.off = 0;
   cl.one_item.L = (int32_t)L;
   cl.one_item.m = m;

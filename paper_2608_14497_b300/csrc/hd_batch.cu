@@ -38,7 +38,7 @@ struct ClusterClass {
   int C = 0, m = 0;
   int stream = 0;            // index of the side stream (one per cluster size)
 };
-constexpr int kMaxClusterStreams = 4;  // C in {8, 4, 2, 1}
+constexpr int kMaxClusterStreams = 5;  // C in {16, 8, 4, 2, 1}
 }  // namespace hd
 
 struct hd_batch_plan {
@@ -254,6 +254,7 @@ extern "C" hd_status hd_conv1d_batched(hd_ctx* c, const hd_batch_plan* bp, const
       ClusterLaunch cl;
       std::memset(&cl, 0, sizeof(cl));
       cl.items = bp->d_citems + k.first;
+      cl.err = c->dev_err;
       if (launch_rcm1d_cluster(cl, k.C, k.m, k.count, f, g, h, st) != cudaSuccess) return HD_ECUDA;
     }
   } else if (bp->nstreams > 1) {
@@ -267,6 +268,7 @@ extern "C" hd_status hd_conv1d_batched(hd_ctx* c, const hd_batch_plan* bp, const
       ClusterLaunch cl;
       std::memset(&cl, 0, sizeof(cl));
       cl.items = bp->d_citems + k.first;
+      cl.err = c->dev_err;
       if (launch_rcm1d_cluster(cl, k.C, k.m, k.count, f, g, h, bp->side[k.stream]) != cudaSuccess) return HD_ECUDA;
     }
     for (int s2 = 0; s2 < bp->nstreams; ++s2)

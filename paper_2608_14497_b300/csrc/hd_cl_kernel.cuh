@@ -38,7 +38,8 @@
 // Shared memory: the four arrays F_a, F_b, G_a, G_b, M complex each, element i
 // at phys(i) = i ^ (((i >> 4) & 7) << 1): rows of 16 elements whose 16-byte
 // chunks are permuted by the row index, so every pass's 128-bit accesses are
-// free of bank conflicts (checked by enumeration on the host).
+// free of bank conflicts (checked by enumeration on the host); behind them the
+// pass twiddles, copied from the per-length table while phase 1 runs.
 //
 // Every step is written as a function of (thread index, CTA state) so the
 // same code can be stepped thread by thread on the host; on the device the
@@ -63,11 +64,15 @@ template <int R3>
 struct Shape {
   static constexpr int M = 256 * R3;
   static constexpr int T = 32 * R3;          // threads per CTA
+  // CTAs per SM the launch bounds ask registers for (what shared memory allows,
+  // up to a register budget that avoids spills)
+  static constexpr int MINB = R3 <= 2 ? 8 : R3 == 3 ? 6 : R3 == 4 ? 5 : R3 == 5 ? 4 : R3 == 6 ? 3 : R3 <= 10 ? 2 : 1;
   static constexpr int TAB1 = (R3 - 1) * 256;  // pass 1: zeta_M^{u j}, u = 1..R3-1, j < 256
   static constexpr int TAB2 = 240;           // pass 2: zeta_256^{u j}, u = 1..15, j < 16
   static constexpr int TABZ = TAB1 + TAB2;   // product table: zeta_M^{P^-1(p)}, p < M
   static constexpr int TABN = TABZ + M;      // entries of the per-length table
-  static constexpr size_t SMEM = sizeof(float2) * 4 * (size_t)M;
+  static constexpr int TABS = TAB1 + TAB2;    // pass twiddles, copied to shared memory behind the arrays
+  static constexpr size_t SMEM = sizeof(float2) * (4 * (size_t)M + TABS);
 };
 
 // Frequency held at position p of a digit-reversed length-M spectrum.
@@ -120,54 +125,47 @@ typedef unsigned raddr_t;
 #else
 typedef char* raddr_t;
 #endif
-__host__ __device__ __forceinline__ void rst2(raddr_t a, float2 v) {
+// 16-byte store into a cluster CTA's shared memory that, once written,
+// completes 16 bytes of the transaction count of that CTA's mbarrier `bar`
+// (st.async: no fence at the sender; the receiver waits on its own barrier).
+__host__ __device__ __forceinline__ void rst4_async(raddr_t a, float2 v0, float2 v1, raddr_t bar) {
 #ifdef __CUDA_ARCH__
-  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
-#else
-  *reinterpret_cast<float2*>(a) = v;
-#endif
-}
-__host__ __device__ __forceinline__ void rst4(raddr_t a, float2 v0, float2 v1) {
-#ifdef __CUDA_ARCH__
-  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "f"(v0.x), "f"(v0.y), "f"(v1.x),
-               "f"(v1.y)
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];\n" ::"r"(a),
+               "f"(v0.x), "f"(v0.y), "f"(v1.x), "f"(v1.y), "r"(bar)
                : "memory");
 #else
+  (void)bar;
   *reinterpret_cast<float4*>(a) = make_float4(v0.x, v0.y, v1.x, v1.y);
 #endif
 }
-__host__ __device__ __forceinline__ float2 rld2(raddr_t a) {
+// 8-byte form of rst4_async.
+__host__ __device__ __forceinline__ void rst2_async(raddr_t a, float2 v, raddr_t bar) {
 #ifdef __CUDA_ARCH__
-  float2 v;
-  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
-  return v;
-#else
-  return *reinterpret_cast<const float2*>(a);
-#endif
-}
-__host__ __device__ __forceinline__ void rld4(raddr_t a, float2& v0, float2& v1) {
-#ifdef __CUDA_ARCH__
-  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];\n"
-               : "=f"(v0.x), "=f"(v0.y), "=f"(v1.x), "=f"(v1.y)
-               : "r"(a)
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];\n" ::"r"(a),
+               "f"(v.x), "f"(v.y), "r"(bar)
                : "memory");
 #else
-  const float4 v = *reinterpret_cast<const float4*>(a);
-  v0 = make_float2(v.x, v.y);
-  v1 = make_float2(v.z, v.w);
+  (void)bar;
+  *reinterpret_cast<float2*>(a) = v;
 #endif
 }
 
-// zeta_{2C}^t for t < C (the residue sums over the blocks t), exact values
-// rounded to FP32: zeta_16^e = (cos, sin)(2 pi e / 16).
+// zeta_32^e = (cos, sin)(2 pi e / 32) (the residue sums over the blocks t use
+// zeta_{2C}^t = zeta_32^{16 t / C}), exact values rounded to FP32.
 template <int SIGN>
-__host__ __device__ __forceinline__ float2 root16(int e) {
-  const float c[16] = {1.0f, 0.92387953251128675613f, 0.70710678118654752440f, 0.38268343236508977173f,
-                       0.0f, -0.38268343236508977173f, -0.70710678118654752440f, -0.92387953251128675613f,
-                       -1.0f, -0.92387953251128675613f, -0.70710678118654752440f, -0.38268343236508977173f,
-                       0.0f, 0.38268343236508977173f, 0.70710678118654752440f, 0.92387953251128675613f};
-  const int es = e & 15;
-  return make_float2(c[es], SIGN * c[(es + 12) & 15]);  // sin x = cos(x - pi/2)
+__host__ __device__ __forceinline__ float2 root32(int e) {
+  const float c[32] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f, 0.83146961230254523708f,
+                       0.70710678118654752440f, 0.55557023301960222474f, 0.38268343236508977173f,
+                       0.19509032201612826785f, 0.0f, -0.19509032201612826785f, -0.38268343236508977173f,
+                       -0.55557023301960222474f, -0.70710678118654752440f, -0.83146961230254523708f,
+                       -0.92387953251128675613f, -0.98078528040323044913f, -1.0f, -0.98078528040323044913f,
+                       -0.92387953251128675613f, -0.83146961230254523708f, -0.70710678118654752440f,
+                       -0.55557023301960222474f, -0.38268343236508977173f, -0.19509032201612826785f, 0.0f,
+                       0.19509032201612826785f, 0.38268343236508977173f, 0.55557023301960222474f,
+                       0.70710678118654752440f, 0.83146961230254523708f, 0.92387953251128675613f,
+                       0.98078528040323044913f};
+  const int es = e & 31;
+  return make_float2(c[es], SIGN * c[(es + 24) & 31]);  // sin x = cos(x - pi/2)
 }
 
 template <int SIGN, int CC>
@@ -175,10 +173,11 @@ __host__ __device__ __forceinline__ void dft_small(float2* v) {
   if constexpr (CC == 2) dft2<SIGN>(v[0], v[1]);
   else if constexpr (CC == 4) dft4<SIGN>(v[0], v[1], v[2], v[3]);
   else if constexpr (CC == 8) dft8<SIGN>(v);
+  else if constexpr (CC == 16) dft16<SIGN>(v);
 }
 
-// zeta_N^{r s} for r < Q from the zeta_N table: three table reads (zeta^s,
-// zeta^{4s}, zeta^{8s}) and at most twelve complex products.
+// zeta_N^{r s} for r < Q from the zeta_N table: up to four table reads
+// (zeta^s, zeta^{4s}, zeta^{8s}, zeta^{16s}) and at most 27 complex products.
 template <int Q>
 __host__ __device__ __forceinline__ void residue_twiddles(const float2* tw, int s, float2* w) {
   w[0] = make_float2(1.f, 0.f);
@@ -197,6 +196,47 @@ __host__ __device__ __forceinline__ void residue_twiddles(const float2* tw, int 
 #pragma unroll
     for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
   }
+  if constexpr (Q >= 32) {
+    w[16] = ldg2(tw + 16 * s);
+#pragma unroll
+    for (int r = 17; r < 32; ++r) w[r] = cmul(w[16], w[r - 16]);
+  }
+}
+
+// The same twiddles built one at a time from six bases (for q = 32 residues,
+// where holding all of them would exhaust the registers): zeta_N^{r s} =
+// w16^{b4} w8^{b3} w4^{b2} w1^{r mod 4} for r = 16 b4 + 8 b3 + 4 b2 + (r mod 4).
+struct TwBases {
+  float2 w1, w2, w3, w4, w8, w16;
+};
+__host__ __device__ __forceinline__ TwBases twiddle_bases(const float2* tw, int s) {
+  TwBases b;
+  b.w1 = ldg2(tw + s);
+  b.w2 = cmul(b.w1, b.w1);
+  b.w3 = cmul(b.w2, b.w1);
+  b.w4 = ldg2(tw + 4 * s);
+  b.w8 = ldg2(tw + 8 * s);
+  b.w16 = ldg2(tw + 16 * s);
+  return b;
+}
+__host__ __device__ __forceinline__ float2 twiddle_of(const TwBases& b, int r) {
+  float2 t = make_float2(1.f, 0.f);
+  bool one = true;
+  const int lo = r & 3;
+  if (lo) {
+    t = lo == 1 ? b.w1 : lo == 2 ? b.w2 : b.w3;
+    one = false;
+  }
+  if (r & 4) {
+    t = one ? b.w4 : cmul(t, b.w4);
+    one = false;
+  }
+  if (r & 8) {
+    t = one ? b.w8 : cmul(t, b.w8);
+    one = false;
+  }
+  if (r & 16) t = one ? b.w16 : cmul(t, b.w16);
+  return t;
 }
 
 __host__ __device__ __forceinline__ int owner_of(int r, int C) { return r < C ? r : (r == C ? 0 : 2 * C - r); }
@@ -213,7 +253,9 @@ struct CtaState {
   const float2* tw;       // zeta_N^k, N = 2 C M
   const float2* tab;      // per-length table (Shape::TAB1 | TAB2 | product)
   float2* arr;            // this CTA's four arrays
-  raddr_t rbase[8];       // every owner's arrays, as seen from this CTA
+  raddr_t rbase[16];      // every CTA's arrays, as seen from this CTA
+  raddr_t rbar1[16];      // every CTA's phase-1 mbarrier (its four arrays received)
+  raddr_t rbar3[16];      // every CTA's phase-3 mbarrier (its gather buffer received)
 };
 
 // ---------------------------------------------------------------------------
@@ -226,7 +268,7 @@ struct Steps {
   static constexpr int T = S::T;
   static constexpr int Q = 2 * C;
   static constexpr int SL = M / C;                  // slice of s per CTA
-  static constexpr int SW1 = 2;                     // s per phase-1 task
+  static constexpr int SW1 = (C >= 16) ? 1 : 2;     // s per phase-1 task
   static constexpr int NT1 = 2 * SL / SW1;          // phase-1 tasks: {f, g} x s-pairs
   static constexpr int SW3 = (SL >= 2 * T) ? 2 : 1; // s per phase-3 task
   static constexpr int NT3 = SL / SW3;
@@ -242,7 +284,19 @@ struct Steps {
     for (int t = 0; t < C; ++t) {
       const int j = t * M + s;
       v[t][0] = v[t][1] = make_float2(0.f, 0.f);
-      if (t < x.p) {
+      if (t < x.p && SW1 == 1) {
+        const int rem = x.L - 2 * j;
+        if (rem >= 2 && x.in8) {
+#ifdef __CUDA_ARCH__
+          v[t][0] = __ldg(reinterpret_cast<const float2*>(src + 2 * j));
+#else
+          v[t][0] = *reinterpret_cast<const float2*>(src + 2 * j);
+#endif
+        } else {
+          if (rem > 0) v[t][0].x = ldgf(src + 2 * j);
+          if (rem > 1) v[t][0].y = ldgf(src + 2 * j + 1);
+        }
+      } else if (t < x.p) {
         const int rem = x.L - 2 * j;  // real values left from 2j
         if (rem >= 4 && x.in16) {
 #ifdef __CUDA_ARCH__
@@ -276,6 +330,27 @@ struct Steps {
   static __host__ __device__ __forceinline__ void scatter_task(const CtaState& x, int task, const float2 (&v)[C][2]) {
     const int which = task / (SL / SW1);
     const int s = x.c * SL + (task - which * (SL / SW1)) * SW1;
+    if constexpr (SW1 == 1) {
+      // one s, every residue stored as soon as it is formed
+      float2 e[C], o[C];
+#pragma unroll
+      for (int t = 0; t < C; ++t) {
+        e[t] = v[t][0];
+        o[t] = (t == 0) ? v[t][0] : cmul(v[t][0], root32<1>(t * (16 / C)));
+      }
+      dft_small<1, C>(e);
+      dft_small<1, C>(o);
+      const TwBases tb = twiddle_bases(x.tw, s);
+      const int ps = phys(s);
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        const float2 a = (r & 1) ? o[r >> 1] : e[r >> 1];
+        const int ow = owner_of(r, C), sl = slot_of(r, C);
+        const int idx = (which * 2 + sl) * M + ps;
+        rst2_async(x.rbase[ow] + (size_t)idx * sizeof(float2), r == 0 ? a : cmul(a, twiddle_of(tb, r)), x.rbar1[ow]);
+      }
+      return;
+    }
     float2 y[2][Q];
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
@@ -283,7 +358,7 @@ struct Steps {
 #pragma unroll
       for (int t = 0; t < C; ++t) {
         e[t] = v[t][w];
-        o[t] = (t == 0) ? v[t][w] : cmul(v[t][w], root16<1>(t * (8 / C)));  // zeta_q^t x_t
+        o[t] = (t == 0) ? v[t][w] : cmul(v[t][w], root32<1>(t * (16 / C)));  // zeta_q^t x_t
       }
       dft_small<1, C>(e);
       dft_small<1, C>(o);
@@ -300,15 +375,17 @@ struct Steps {
     for (int r = 0; r < Q; ++r) {
       const int ow = owner_of(r, C), sl = slot_of(r, C);
       const int idx = (which * 2 + sl) * M + ps;  // element index in the owner's arrays
-      rst4(x.rbase[ow] + (size_t)idx * sizeof(float2), y[0][r], y[1][r]);
+      if constexpr (C == 1) sts4(x.arr + idx, y[0][r], y[1][r]);  // one CTA: its own arrays
+      else rst4_async(x.rbase[ow] + (size_t)idx * sizeof(float2), y[0][r], y[1][r], x.rbar1[ow]);
     }
   }
 
   // ---- length-M DFTs: in-place DIF (forward) and DIT (backward) passes -----
-  // Pass 1: radix R3, stride 256 (transform size M), twiddles zeta_M^{u j}.
+  // Pass 1: radix R3, stride 256 (transform size M), twiddles zeta_M^{u j}
+  // read from `tws` (the table's first TABS entries, in shared memory).
   // Task = (array, pair of adjacent j) for W = 2, (array, j) for W = 1.
   template <int SIGN, int NARR, int W>
-  static __host__ __device__ __forceinline__ void pass1(float2* arr, int tid, const float2* tab) {
+  static __host__ __device__ __forceinline__ void pass1(float2* arr, int tid, const float2* tws) {
     if constexpr (R3 > 1) {
       constexpr int PER = 256 / W;
       constexpr int NT = NARR * PER;
@@ -329,11 +406,11 @@ struct Steps {
 #pragma unroll
             for (int u = 1; u < R3; ++u) {
               if constexpr (W == 2) {
-                const float4 t = ldg4(tab + (u - 1) * 256 + j);
+                const float4 t = *reinterpret_cast<const float4*>(tws + (u - 1) * 256 + j);
                 v[0][u] = cmul(v[0][u], make_float2(t.x, -t.y));
                 v[1][u] = cmul(v[1][u], make_float2(t.z, -t.w));
               } else {
-                v[0][u] = cmul(v[0][u], cconj(ldg2(tab + (u - 1) * 256 + j)));
+                v[0][u] = cmul(v[0][u], cconj(tws[(u - 1) * 256 + j]));
               }
             }
           }
@@ -343,11 +420,11 @@ struct Steps {
 #pragma unroll
             for (int u = 1; u < R3; ++u) {
               if constexpr (W == 2) {
-                const float4 t = ldg4(tab + (u - 1) * 256 + j);
+                const float4 t = *reinterpret_cast<const float4*>(tws + (u - 1) * 256 + j);
                 v[0][u] = cmul(v[0][u], make_float2(t.x, t.y));
                 v[1][u] = cmul(v[1][u], make_float2(t.z, t.w));
               } else {
-                v[0][u] = cmul(v[0][u], ldg2(tab + (u - 1) * 256 + j));
+                v[0][u] = cmul(v[0][u], tws[(u - 1) * 256 + j]);
               }
             }
           }
@@ -364,10 +441,10 @@ struct Steps {
   // Pass 2: radix 16, stride 16, inside each of the R3 blocks of 256;
   // twiddles zeta_256^{u j}, j < 16.
   template <int SIGN, int NARR, int W>
-  static __host__ __device__ __forceinline__ void pass2(float2* arr, int tid, const float2* tab) {
+  static __host__ __device__ __forceinline__ void pass2(float2* arr, int tid, const float2* tws) {
     constexpr int PER = 16 / W;          // tasks per block
     constexpr int NT = NARR * R3 * PER;
-    const float2* t2 = tab + S::TAB1;
+    const float2* t2 = tws + S::TAB1;
 #pragma unroll
     for (int k = 0; k < (NT + T - 1) / T; ++k) {
       const int task = tid + k * T;
@@ -385,11 +462,11 @@ struct Steps {
 #pragma unroll
           for (int u = 1; u < 16; ++u) {
             if constexpr (W == 2) {
-              const float4 t = ldg4(t2 + (u - 1) * 16 + j);
+              const float4 t = *reinterpret_cast<const float4*>(t2 + (u - 1) * 16 + j);
               v[0][u] = cmul(v[0][u], make_float2(t.x, -t.y));
               v[1][u] = cmul(v[1][u], make_float2(t.z, -t.w));
             } else {
-              v[0][u] = cmul(v[0][u], cconj(ldg2(t2 + (u - 1) * 16 + j)));
+              v[0][u] = cmul(v[0][u], cconj(t2[(u - 1) * 16 + j]));
             }
           }
         }
@@ -399,11 +476,11 @@ struct Steps {
 #pragma unroll
           for (int u = 1; u < 16; ++u) {
             if constexpr (W == 2) {
-              const float4 t = ldg4(t2 + (u - 1) * 16 + j);
+              const float4 t = *reinterpret_cast<const float4*>(t2 + (u - 1) * 16 + j);
               v[0][u] = cmul(v[0][u], make_float2(t.x, t.y));
               v[1][u] = cmul(v[1][u], make_float2(t.z, t.w));
             } else {
-              v[0][u] = cmul(v[0][u], ldg2(t2 + (u - 1) * 16 + j));
+              v[0][u] = cmul(v[0][u], t2[(u - 1) * 16 + j]);
             }
           }
         }
@@ -513,18 +590,74 @@ struct Steps {
   }
 
   // ---- phase 3 --------------------------------------------------------------
-  // w_r[s] from the owners (backward results in F_a / F_b), zeta_N^{-rs}, the
-  // backward sum over r for t < p, scale, unpacked stores.  Returns after its
-  // last distributed-shared-memory read of the task.
+  // Each owner pushes w_r[s] of its two residues to the CTA whose slice holds
+  // s, into that CTA's gather buffer (its G arrays, free after the product):
+  // buffer index r SL + (s - d SL) for residue r and destination d = s / SL.
+  // Task k of destination D: (slot, pair of s in D's slice), k < SL.
+  template <int D>
+  static __host__ __device__ __forceinline__ void push_task(const CtaState& x, int k) {
+    const int slot = k / (SL / 2);
+    const int sl = 2 * (k - slot * (SL / 2));
+    const int s = D * SL + sl;
+    const int r = slot ? (x.c == 0 ? C : Q - x.c) : x.c;
+    float2 a0, a1;
+    lds4(x.arr + slot * M + phys(s), a0, a1);
+    rst4_async(x.rbase[D] + (size_t)(2 * M + r * SL + sl) * sizeof(float2), a0, a1, x.rbar3[D]);
+  }
+  template <int D = 0>
+  static __host__ __device__ __forceinline__ void push_all(const CtaState& x, int tid) {
+    if constexpr (D < C) {
+#pragma unroll
+      for (int k = tid; k < SL; k += T) push_task<D>(x, k);
+      push_all<D + 1>(x, tid);
+    }
+  }
+
+  // w_r[s] from the gather buffer (one CTA: from its own arrays), zeta_N^{-rs},
+  // the backward sum over r for t < p, scale, unpacked stores.
   static __host__ __device__ __forceinline__ void gather_task(const CtaState& x, int task, float sc) {
-    const int s = x.c * SL + task * SW3;
+    const int sl = task * SW3;
+    const int s = x.c * SL + sl;
+    const float2* buf = x.arr + 2 * M;
+    if constexpr (Q >= 32) {
+      static_assert(SW3 == 1, "q = 32 gathers one s per task");
+      // residues read and twiddled one at a time into the two length-C sums
+      const TwBases tb = twiddle_bases(x.tw, s);
+      float2 e[C], o[C];
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        const float2 y = buf[r * SL + sl];
+        const float2 v = (r == 0) ? y : cmul(y, cconj(twiddle_of(tb, r)));
+        if (r & 1) o[r >> 1] = v;
+        else e[r >> 1] = v;
+      }
+      dft_small<-1, C>(e);
+      dft_small<-1, C>(o);
+      float* hi = x.h + x.off;
+#pragma unroll
+      for (int t = 0; t < C; ++t) {
+        if (t < x.p) {
+          const float2 ov = (t == 0) ? o[0] : cmul(o[t], root32<-1>(t * (16 / C)));
+          const float2 out = cscale(cadd(e[t], ov), sc);
+          const int j = t * M + s;
+          const int rem = x.L - 2 * j;
+          if (rem > 0) hi[2 * j] = out.x;
+          if (rem > 1) hi[2 * j + 1] = out.y;
+        }
+      }
+      return;
+    }
     float2 y[SW3][Q];
-    const int ps = phys(s);
 #pragma unroll
     for (int r = 0; r < Q; ++r) {
-      const raddr_t a = x.rbase[owner_of(r, C)] + (size_t)(slot_of(r, C) * M + ps) * sizeof(float2);
-      if constexpr (SW3 == 2) rld4(a, y[0][r], y[1][r]);
-      else y[0][r] = rld2(a);
+      if constexpr (C == 1) {  // one CTA: residue r's result is its array r, in natural order
+        static_assert(SW3 == 2, "one CTA gathers pairs of s");
+        lds4(x.arr + r * M + phys(s), y[0][r], y[1][r]);
+      } else if constexpr (SW3 == 2) {
+        lds4(buf + r * SL + sl, y[0][r], y[1][r]);
+      } else {
+        y[0][r] = buf[r * SL + sl];
+      }
     }
     float2 out[SW3][C];
 #pragma unroll
@@ -542,7 +675,7 @@ struct Steps {
       dft_small<-1, C>(o);
 #pragma unroll
       for (int t = 0; t < C; ++t) {
-        const float2 ov = (t == 0) ? o[0] : cmul(o[t], root16<-1>(t * (8 / C)));
+        const float2 ov = (t == 0) ? o[0] : cmul(o[t], root32<-1>(t * (16 / C)));
         out[w][t] = cscale(cadd(e[t], ov), sc);
       }
     }

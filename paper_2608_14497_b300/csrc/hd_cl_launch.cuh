@@ -22,16 +22,77 @@ __device__ __forceinline__ void arrive_relaxed() { asm volatile("barrier.cluster
 __device__ __forceinline__ void arrive_release() { asm volatile("barrier.cluster.arrive.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ void wait_acquire() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
 
+// mbarrier with one arrival (the thread that posts the expected byte count)
+// and a transaction count completed by the senders' st.async stores.
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Wait for phase 0 of `bar`, bounded: the data of one cluster arrive within
+// microseconds (the CTAs of a cluster are co-scheduled), so after kWaitCycles
+// of SM clock (about 16 ms) the wait gives up, records HD_ETIMEOUT in the
+// device error word and returns; once the word is set, later waits return at
+// once, so a faulty launch ends quickly.  The results are then invalid; the
+// host reads the word with hd_last_device_error.
+constexpr long long kWaitCycles = 1LL << 25;
+__device__ __forceinline__ void mbar_wait(unsigned bar, int* err) {
+  if (err && *(volatile int*)err != 0) return;
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar)
+        : "memory");
+    if (done) return;
+    if (clock64() - t0 > kWaitCycles) {
+      if (err) atomicExch(err, (int)HD_ETIMEOUT);
+      return;
+    }
+  }
+}
+
 // One convolution per cluster of C CTAs; CTA c owns the residue pair {c, q - c}.
+// Data move between the CTAs only by st.async stores that complete on the
+// receiver's mbarrier: phase 1 into the owners' four arrays (barrier 1, 32 M
+// bytes per CTA), phase 3 into the gather buffers (barrier 3, 16 M bytes).
+// The hardware cluster barrier is used twice: once at the start (every CTA
+// is running and its mbarriers are initialised before any remote store) and
+// once after the product (every CTA's G arrays, the gather buffers, are free).
+// A single CTA (C = 1) works in its own shared memory only.
 template <int C, int R3>
-__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(Shape<R3>::T, 1)
+__global__ void __launch_bounds__(Shape<R3>::T, Shape<R3>::MINB)
     k_rcm_cl(ClusterLaunch la, const float* f, const float* g, float* h) {
   using K = Steps<C, R3>;
   constexpr int T = K::T;
+  constexpr int M = K::M;
   extern __shared__ float4 smem_raw[];
+  __shared__ __align__(8) unsigned long long bars[2];
   float2* arr = reinterpret_cast<float2*>(smem_raw);
+  float2* tws = arr + 4 * M;  // pass twiddles (Shape::TABS entries)
   const int tid = threadIdx.x;
+  const unsigned bar1 = (unsigned)__cvta_generic_to_shared(&bars[0]);
+  const unsigned bar3 = (unsigned)__cvta_generic_to_shared(&bars[1]);
+  if (C > 1 && tid == 0) {
+    mbar_init(bar1);
+    mbar_init(bar3);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    mbar_expect(bar1, (unsigned)(sizeof(float2) * 4 * M));  // the four arrays
+    mbar_expect(bar3, (unsigned)(sizeof(float2) * 2 * M));  // q slices of M / C
+  }
+  // every CTA of the cluster must be running, with its barriers initialised,
+  // before the first remote store: arrive now, wait after the first loads
+  if constexpr (C > 1) arrive_relaxed();
   const CItem it = la.items ? la.items[blockIdx.x / C] : la.one_item;
+  // copy the pass twiddles to shared memory while phase 1 runs; 16-byte chunks
+  for (int i = tid; i < Shape<R3>::TABS / 2; i += T) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(tws + 2 * i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(it.tabm + 2 * i) : "memory");
+  }
   CtaState x;
   x.f = f;
   x.g = g;
@@ -52,58 +113,89 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(Shape<R3>::T, 1)
   }
   const unsigned local = (unsigned)__cvta_generic_to_shared(arr);
 #pragma unroll
-  for (int o = 0; o < C; ++o) x.rbase[o] = (raddr_t)(uintptr_t)mapa_u32(local, (unsigned)o);  // raddr_t: 32-bit on the device
-  // every CTA of the cluster must be running before the first remote store:
-  // arrive now, wait after the first loads are in flight
-  arrive_relaxed();
-
-  // ---- phase 1 (Eq. forwardr, inner sum), scattered to the owners
-  {
-    float2 v[C][2];
-    if (tid < K::NT1) K::load_task(x, tid, v);
-    wait_acquire();
-#pragma unroll 1
-    for (int task = tid; task < K::NT1; task += T) {
-      K::scatter_task(x, task, v);
-      if (task + T < K::NT1) K::load_task(x, task + T, v);
-    }
+  for (int o = 0; o < C; ++o) {  // raddr_t: 32-bit shared::cluster addresses on the device
+    x.rbase[o] = (raddr_t)(uintptr_t)mapa_u32(local, (unsigned)o);
+    x.rbar1[o] = (raddr_t)(uintptr_t)mapa_u32(bar1, (unsigned)o);
+    x.rbar3[o] = (raddr_t)(uintptr_t)mapa_u32(bar3, (unsigned)o);
   }
-  arrive_release();
-  wait_acquire();
+
+  static_assert(C <= 16, "clusters of at most 16 CTAs");
+  // ---- phase 1 (Eq. forwardr, inner sum), pushed to the owners: every
+  // task's loads in flight first (8 / C tasks of C blocks x 2 values)
+  {
+    float2 v[K::U1][C][2];
+#pragma unroll
+    for (int u = 0; u < K::U1; ++u)
+      if (K::NT1 % T == 0 || tid + u * T < K::NT1) K::load_task(x, tid + u * T, v[u]);
+    if constexpr (C > 1) wait_acquire();
+#pragma unroll
+    for (int u = 0; u < K::U1; ++u)
+      if (K::NT1 % T == 0 || tid + u * T < K::NT1) K::scatter_task(x, tid + u * T, v[u]);
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();  // the twiddle copies of every thread are visible
+  if constexpr (C > 1) mbar_wait(bar1, la.err);
 
   // ---- forward DFTs (DIF), RCM product, backward DFTs (DIT)
-  K::template pass1<1, 4, 2>(arr, tid, x.tab);
+  K::template pass1<1, 4, 2>(arr, tid, tws);
   __syncthreads();
-  K::template pass2<1, 4, 2>(arr, tid, x.tab);
+  K::template pass2<1, 4, 2>(arr, tid, tws);
   __syncthreads();
   K::template pass3<1, 4>(arr, tid);
   __syncthreads();
   K::product(x, tid);
   __syncthreads();
+  if constexpr (C > 1) arrive_release();  // this CTA's G arrays (a gather buffer from now on) are free
   K::template pass3<-1, 2>(arr, tid);
   __syncthreads();
-  K::template pass2<-1, 2, 1>(arr, tid, x.tab);
+  K::template pass2<-1, 2, 1>(arr, tid, tws);
   __syncthreads();
-  K::template pass1<-1, 2, 1>(arr, tid, x.tab);
-  arrive_release();
-  wait_acquire();
+  K::template pass1<-1, 2, 1>(arr, tid, tws);
+  __syncthreads();
+  if constexpr (C > 1) wait_acquire();  // every CTA's gather buffer is free
 
-  // ---- phase 3 (Eq. accumulation), gathered from the owners
-  const float sc = 1.0f / (float)(2 * C * K::M);
+  // ---- phase 3 (Eq. accumulation): push w_r[s] to the slice owners, gather
+  if constexpr (C > 1) {
+    K::push_all(x, tid);
+    mbar_wait(bar3, la.err);
+  }
+  const float sc = 1.0f / (float)(2 * C * M);
 #pragma unroll 1
   for (int task = tid; task < K::NT3; task += T) K::gather_task(x, task, sc);
-  // no CTA leaves while others may still read its shared memory
-  arrive_relaxed();
-  wait_acquire();
 }
 
-// Launch over `nitems` convolutions of the same (C, R3): grid nitems x C.
+// Launch over `nitems` convolutions of the same (C, R3): grid nitems x C in
+// clusters of C CTAs (the cluster size is a launch attribute; 16 is beyond the
+// portable size and is allowed per kernel).
 template <int C, int R3>
 cudaError_t launch(const ClusterLaunch& la, int nitems, const float* f, const float* g, float* h, cudaStream_t st) {
-  const cudaError_t e = smem_optin((const void*)k_rcm_cl<C, R3>, Shape<R3>::SMEM);
+  auto kern = k_rcm_cl<C, R3>;
+  cudaError_t e = smem_optin((const void*)kern, Shape<R3>::SMEM);
   if (e != cudaSuccess) return e;
-  k_rcm_cl<C, R3><<<nitems * C, Shape<R3>::T, Shape<R3>::SMEM, st>>>(la, f, g, h);
-  return cudaGetLastError();
+  if constexpr (C > 8) {
+    static bool nonportable_set[64] = {};
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !nonportable_set[dev]) {
+      e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+      if (dev >= 0 && dev < 64) nonportable_set[dev] = true;
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nitems * C), 1, 1);
+  cfg.blockDim = dim3(Shape<R3>::T, 1, 1);
+  cfg.dynamicSmemBytes = Shape<R3>::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, la, f, g, h);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace cl

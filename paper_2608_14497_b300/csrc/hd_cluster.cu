@@ -12,17 +12,31 @@
 
 namespace hd {
 
-// Built instances: m = 256 R3.  One CTA covers L <= 2 m for every R3; the
-// larger clusters start where the next smaller one ends (L > C * 4608), so
-// they need m > 2304, R3 in {10, 12, 16, 18}.
+// Built instances: m = 256 R3.  One CTA covers L <= 2 m; a cluster of C CTAs
+// covers L <= 2 C m.  Up to R3 = 10 two or more CTAs fit on an SM (shared
+// memory 32 m + 8 (m - 16) bytes), so for long items the planner may trade a
+// larger cluster for CTAs that overlap on the SMs; the autotuner decides.
 static const int kR3One[] = {1, 2, 3, 4, 5, 6, 8, 9, 10, 12, 16, 18};
-static const int kR3Many[] = {10, 12, 16, 18};
+static const int kR3Two[] = {10, 12, 16, 18};
+static const int kR3Four[] = {5, 6, 8, 9, 10, 12, 16, 18};
+static const int kR3Eight[] = {5, 6, 8, 9, 10, 12, 16, 18};
+static const int kR3Sixteen[] = {5, 6, 8, 9};
+
+template <size_t N>
+static bool has(const int (&v)[N], int x) {
+  return std::find(std::begin(v), std::end(v), x) != std::end(v);
+}
 
 bool cluster_instance(int C, int m) {
   if (m % 256) return false;
   const int R3 = m / 256;
-  if (C == 1) return std::find(std::begin(kR3One), std::end(kR3One), R3) != std::end(kR3One);
-  if (C == 2 || C == 4 || C == 8) return std::find(std::begin(kR3Many), std::end(kR3Many), R3) != std::end(kR3Many);
+  switch (C) {
+    case 1: return has(kR3One, R3);
+    case 2: return has(kR3Two, R3);
+    case 4: return has(kR3Four, R3);
+    case 8: return has(kR3Eight, R3);
+    case 16: return has(kR3Sixteen, R3);
+  }
   return false;
 }
 
@@ -30,8 +44,10 @@ bool cluster_instance(int C, int m) {
 static std::vector<std::pair<int, int>> instances() {
   std::vector<std::pair<int, int>> v;
   for (int r : kR3One) v.push_back({1, 256 * r});
-  for (int C = 2; C <= 8; C *= 2)
-    for (int r : kR3Many) v.push_back({C, 256 * r});
+  for (int r : kR3Two) v.push_back({2, 256 * r});
+  for (int r : kR3Four) v.push_back({4, 256 * r});
+  for (int r : kR3Eight) v.push_back({8, 256 * r});
+  for (int r : kR3Sixteen) v.push_back({16, 256 * r});
   return v;
 }
 
@@ -111,6 +127,7 @@ hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out) {
     ClusterLaunch cl;
     std::memset(&cl, 0, sizeof(cl));
     cl.items = d_items;
+    cl.err = c->dev_err;
     if (launch_rcm1d_cluster(cl, C, mm, (int)K, f, g, h, 0) != cudaSuccess) {
       st = HD_ECUDA;
       break;
@@ -152,8 +169,9 @@ cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int C, int m, int nite
   switch (C) {
     case 1: return R3 <= 6 ? launch_cl_c1(R3, cl, nitems, f, g, h, st) : launch_cl_c1b(R3, cl, nitems, f, g, h, st);
     case 2: return launch_cl_c2(R3, cl, nitems, f, g, h, st);
-    case 4: return launch_cl_c4(R3, cl, nitems, f, g, h, st);
-    case 8: return launch_cl_c8(R3, cl, nitems, f, g, h, st);
+    case 4: return R3 <= 9 ? launch_cl_c4(R3, cl, nitems, f, g, h, st) : launch_cl_c4b(R3, cl, nitems, f, g, h, st);
+    case 8: return R3 <= 9 ? launch_cl_c8(R3, cl, nitems, f, g, h, st) : launch_cl_c8b(R3, cl, nitems, f, g, h, st);
+    case 16: return launch_cl_c16(R3, cl, nitems, f, g, h, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -8,7 +8,7 @@
 
 namespace hd {
 
-constexpr int kClusterCtas = 8;     // largest cluster (C = 8 CTAs, q = 16 residues)
+constexpr int kClusterCtas = 16;    // largest cluster (C = 16 CTAs, q = 32 residues)
 constexpr int kClusterMaxM = 4608;  // largest residue DFT length (M = 256 R3, R3 <= 18)
 
 // One convolution: q = 2C residues of length m = 256 R3, p = ceil(Lp/m) <= C.
@@ -24,6 +24,7 @@ struct CItem {
 struct ClusterLaunch {
   const CItem* items;
   CItem one_item;
+  int* err;  // device error word (bounded waits that gave up), or nullptr
 };
 
 // Whether the kernel is built for clusters of C CTAs with residue length m.
@@ -39,15 +40,17 @@ cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int C, int m, int nite
                                  const float* g, float* h, cudaStream_t st);
 // Per-cluster-size dispatch over R3 = m / 256 (hd_cl_c*.cu); cudaErrorInvalidValue
 // for an instance that is not built.
-cudaError_t launch_cl_c1(int R3, const ClusterLaunch& cl, int nitems, const float* f, const float* g, float* h,
-                         cudaStream_t st);
-cudaError_t launch_cl_c1b(int R3, const ClusterLaunch& cl, int nitems, const float* f, const float* g, float* h,
-                          cudaStream_t st);
-cudaError_t launch_cl_c2(int R3, const ClusterLaunch& cl, int nitems, const float* f, const float* g, float* h,
-                         cudaStream_t st);
-cudaError_t launch_cl_c4(int R3, const ClusterLaunch& cl, int nitems, const float* f, const float* g, float* h,
-                         cudaStream_t st);
-cudaError_t launch_cl_c8(int R3, const ClusterLaunch& cl, int nitems, const float* f, const float* g, float* h,
-                         cudaStream_t st);
+#define HD_CL_LAUNCHER(name)                                                                                   \
+  cudaError_t name(int R3, const ClusterLaunch& cl, int nitems, const float* f, const float* g, float* h, \
+                   cudaStream_t st);
+HD_CL_LAUNCHER(launch_cl_c1)
+HD_CL_LAUNCHER(launch_cl_c1b)
+HD_CL_LAUNCHER(launch_cl_c2)
+HD_CL_LAUNCHER(launch_cl_c4)
+HD_CL_LAUNCHER(launch_cl_c4b)
+HD_CL_LAUNCHER(launch_cl_c8)
+HD_CL_LAUNCHER(launch_cl_c8b)
+HD_CL_LAUNCHER(launch_cl_c16)
+#undef HD_CL_LAUNCHER
 
 }  // namespace hd
