@@ -26,9 +26,10 @@
  * or g (in place, as the paper times it); partial overlap is not allowed.
  * Calls are asynchronous on the given CUDA stream (NULL = legacy default).
  * The context owns twiddle tables and scratch; the first call for a new size
- * allocates them (cudaMalloc, and a synchronisation of the context's own
- * table stream), and growing the scratch synchronises the device, so capture
- * a call in a CUDA graph only after one uncaptured call of the same shape.
+ * allocates them (tables: cudaMalloc and a synchronisation of the context's
+ * own table stream; scratch: stream-ordered cudaMallocAsync / cudaFreeAsync on
+ * the call's stream, no device synchronisation), so capture a call in a CUDA
+ * graph only after one uncaptured call of the same shape.
  * Tables are complete before the call that creates them returns, so any
  * stream may use them.  The scratch is one area per context: a context serves
  * one stream at a time (calls on different streams that overlap on the GPU
@@ -96,6 +97,15 @@ hd_status hd_conv2d(hd_ctx* ctx, hd_algo algo, hd_prec prec, const float* f, con
 hd_status hd_conv3d(hd_ctx* ctx, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h,
                     int64_t L1, int64_t L2, int64_t L3, const hd_dim_params* prm, void* stream);
 
+/* `batch` independent convolutions of equal extents Ls[0..ndim) stored back to
+ * back in f, g and h (item b at offset b * prod(Ls)); the same result as one
+ * hd_conv1d/2d/3d call per item.  hybridRCM in FP32 runs the whole batch in
+ * one pass sequence (1D: one cluster launch; 2D/3D: every outer pass and the
+ * row pass over all items at once, Sec. 5); other algorithms run item by item.
+ * Errors as hd_conv1d. */
+hd_status hd_conv_batch(hd_ctx* ctx, hd_algo algo, hd_prec prec, int ndim, const int64_t* Ls, int32_t batch,
+                        const float* f, const float* g, float* h, void* stream);
+
 /* Batched 1D convolutions of uneven lengths.  A plan is built on the host
  * from HOST arrays: item i occupies floats [offsets[i], offsets[i] + L[i]) of
  * f, g and h (items must not overlap).  The planner picks (m, q) per length
@@ -117,8 +127,14 @@ hd_status hd_batch_plan_launches(const hd_batch_plan* plan, int32_t* n);
  * independent problems of extents Ls[0..ndim) stored back to back: given
  * grad_h, grad_f[j] = sum_k grad_h[k] g[k-j] and grad_g[j] = sum_k grad_h[k]
  * f[k-j], computed as rev(conv(rev(grad_h), g)) on every axis (the adjoint of
- * a truncated convolution is a reversed truncated convolution).  grad_f or
- * grad_g may be NULL to skip it. */
+ * a truncated convolution is a reversed truncated convolution; the paper has
+ * no adjoint, this follows from the definition).  grad_f or grad_g may be
+ * NULL to skip it; neither may overlap grad_h, f, g or the other gradient
+ * (HD_EINVAL).  hybridRCM in 2D/3D runs one fused pass sequence for the whole
+ * batch: the reversal is folded into the first pass's loads and the last
+ * pass's stores, and the transforms of rev(grad_h) are formed once for both
+ * gradients; other cases reverse the batch in one launch per array and
+ * convolve with hd_conv_batch.  Scratch grows stream-ordered on `stream`. */
 hd_status hd_conv_adjoint(hd_ctx* ctx, hd_algo algo, int ndim, const int64_t* Ls, int32_t batch,
                           const float* grad_h, const float* f, const float* g, float* grad_f, float* grad_g,
                           void* stream);

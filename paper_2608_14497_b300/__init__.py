@@ -27,7 +27,7 @@ PRECS = {"fp32": HD_FP32, "split_bf16": HD_SPLIT_BF16}
 EXPORTS = ("hd_create", "hd_destroy", "hd_conv1d", "hd_conv2d", "hd_conv3d", "hd_batch_plan_create",
            "hd_batch_plan_destroy", "hd_conv1d_batched", "hd_conv_adjoint", "hd_plan", "hd_last_device_error",
            "hd_strerror", "hd_last_error_string", "hd_conv1d_rcm_noalloc",
-           "hd_tuning_table", "hd_batch_plan_launches")
+           "hd_tuning_table", "hd_batch_plan_launches", "hd_conv_batch")
 
 
 class HDError(RuntimeError):
@@ -75,6 +75,7 @@ def load(build_if_missing=False):
         "hd_conv1d_rcm_noalloc": ([P, P, P, I64, DP, P], I),
         "hd_tuning_table": ([P, I32, P, P, P, P], I),
         "hd_batch_plan_launches": ([P, P], I),
+        "hd_conv_batch": ([P, I, I, I, P, I32, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -144,6 +145,11 @@ def hd_batch_plan_destroy(plan):
 
 def hd_conv1d_batched(ctx, plan, f_ptr, g_ptr, h_ptr, stream=0):
     return load().hd_conv1d_batched(ctx, plan, f_ptr, g_ptr, h_ptr, stream)
+
+
+def hd_conv_batch(ctx, algo, prec, Ls, batch, f_ptr, g_ptr, h_ptr, stream=0):
+    arr = (ctypes.c_int64 * len(Ls))(*[int(x) for x in Ls])
+    return load().hd_conv_batch(ctx, algo, prec, len(Ls), arr, batch, f_ptr, g_ptr, h_ptr, stream)
 
 
 def hd_conv_adjoint(ctx, algo, Ls, batch, gh_ptr, f_ptr, g_ptr, gf_ptr, gg_ptr, stream=0):
@@ -218,22 +224,19 @@ def conv(f, g, algo="hybridRCM", params=None, out=None, prec="fp32"):
 
 
 def conv_batch(f, g, ndim, algo="hybridRCM", out=None):
-    """Independent convolutions of f[b] with g[b] over a leading batch dimension."""
+    """Independent convolutions of f[b] with g[b] over a leading batch dimension
+    (one hd_conv_batch call)."""
     import torch
     _check_tensor(f, "f")
     _check_tensor(g, "g")
     if f.shape != g.shape or f.dim() != ndim + 1:
         raise ValueError("f and g must be (batch, *extents) with matching shapes")
     h = torch.empty_like(f) if out is None else out
+    _check_tensor(h, "out")
     ctx = context(f.device.index)
-    a = ALGOS[algo]
-    n = f[0].numel() * 4
-    L = tuple(f.shape[1:])
-    fn = {1: hd_conv1d, 2: hd_conv2d, 3: hd_conv3d}[ndim]
-    for b in range(f.shape[0]):
-        st = fn(ctx, a, HD_FP32, f.data_ptr() + b * n, g.data_ptr() + b * n, h.data_ptr() + b * n, *L,
-                None, _stream_ptr())
-        _check(st, "conv_batch")
+    st = hd_conv_batch(ctx, ALGOS[algo], HD_FP32, tuple(f.shape[1:]), f.shape[0], f.data_ptr(), g.data_ptr(),
+                       h.data_ptr(), _stream_ptr())
+    _check(st, "conv_batch")
     return h
 
 
@@ -262,9 +265,10 @@ def _autograd_fn():
 
         @staticmethod
         def forward(ctx, f, g, algo="hybridRCM"):
+            f, g = f.contiguous(), g.contiguous()
             ctx.save_for_backward(f, g)
             ctx.algo = algo
-            return conv_batch(f.contiguous(), g.contiguous(), f.dim() - 1, algo)
+            return conv_batch(f, g, f.dim() - 1, algo)
 
         @staticmethod
         def backward(ctx, grad_h):

@@ -110,9 +110,10 @@ hd_status resolve_cs1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D*
   return HD_OK;
 }
 
-// hybridRCM with planner parameters: the cluster kernel, one unit by value.
+// hybridRCM with planner parameters: the cluster kernel, one item by value,
+// repeated `batch` times at a stride of L floats.
 static hd_status conv1d_rcm_cluster(hd_ctx* c, const float* f, const float* g, float* h, int64_t L, int C, int m,
-                                    int p, cudaStream_t st) {
+                                    int p, cudaStream_t st, int64_t batch = 1) {
   hd_status terr = HD_OK;
   const float2* tw = c->tables.get((int64_t)2 * C * m, st, &terr);
   if (!tw) return fail(terr, "twiddle table allocation failed");
@@ -127,7 +128,8 @@ static hd_status conv1d_rcm_cluster(hd_ctx* c, const float* f, const float* g, f
   cl.one_item.tw = tw;
   cl.one_item.tabm = c->tables.get_pass_table(m, st, &terr);
   if (!cl.one_item.tabm) return fail(terr, "pass table allocation failed");
-  cudaError_t e = launch_rcm1d_cluster(cl, C, m, 1, f, g, h, st);
+  cl.stride = L;
+  cudaError_t e = launch_rcm1d_cluster(cl, C, m, (int)batch, f, g, h, st);
   if (e != cudaSuccess) return cuda_fail(e, "cluster launch");
   return HD_OK;
 }
@@ -158,7 +160,7 @@ static hd_status conv1d_hybrid(hd_ctx* c, hd_algo algo, const float* f, const fl
   if (P.m % 2 == 0) factor_radices(P.m / 2, &la.plan_half);
   if (P.gacc) {
     const size_t bytes = (algo == HD_HYBRID_RCM) ? sizeof(float2) * (size_t)ceil_div(L, 2) : sizeof(float) * (size_t)L;
-    if (ensure_ws(c, bytes) != HD_OK) return fail(HD_ENOMEM, "workspace allocation failed");
+    if (ensure_ws(c, bytes, st) != HD_OK) return fail(HD_ENOMEM, "workspace allocation failed");
     la.one.gacc = c->ws;
   }
   cudaError_t e = (algo == HD_HYBRID_RCM) ? launch_rcm1d(la, 1, P.threads, P.smem, f, g, h, st)
@@ -264,6 +266,33 @@ hd_status hd_conv1d(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, const
     case HD_EXPLICIT_RCM: return explicit_nd(c, algo, 1, &L, f, g, h, st);
   }
   return fail(HD_EINVAL, "unknown algorithm");
+}
+
+hd_status hd_conv_batch(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const int64_t* Ls, int32_t batch,
+                        const float* f, const float* g, float* h, void* stream) {
+  if (!c || !Ls || !f || !g || !h || ndim < 1 || ndim > 3 || batch < 1) return fail(HD_EINVAL, "null argument");
+  int64_t n = 1;
+  for (int i = 0; i < ndim; ++i) {
+    if (Ls[i] < 1) return fail(HD_EINVAL, "L < 1");
+    n *= Ls[i];
+  }
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == HD_FP32 && algo == HD_HYBRID_RCM) {
+    if (ndim >= 2) return conv_nd_batch_rcm(c, ndim, Ls, batch, f, g, h, st);
+    int C, m, p;
+    if (batch < (1 << 24) && cluster_params(Ls[0], &C, &m, &p)) return conv1d_rcm_cluster(c, f, g, h, Ls[0], C, m, p, st, batch);
+  }
+  // every other case: one call per item
+  for (int32_t b = 0; b < batch; ++b) {
+    const int64_t o = (int64_t)b * n;
+    hd_status s;
+    if (ndim == 1) s = hd_conv1d(c, algo, prec, f + o, g + o, h + o, Ls[0], nullptr, stream);
+    else if (ndim == 2) s = hd_conv2d(c, algo, prec, f + o, g + o, h + o, Ls[0], Ls[1], nullptr, stream);
+    else s = hd_conv3d(c, algo, prec, f + o, g + o, h + o, Ls[0], Ls[1], Ls[2], nullptr, stream);
+    if (s != HD_OK) return s;
+  }
+  return HD_OK;
 }
 
 hd_status hd_last_device_error(hd_ctx* c) {

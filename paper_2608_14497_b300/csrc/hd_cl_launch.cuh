@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(Shape<R3>::T, Shape<R3>::MINB)
   // every CTA of the cluster must be running, with its barriers initialised,
   // before the first remote store: arrive now, wait after the first loads
   if constexpr (C > 1) arrive_relaxed();
-  const CItem it = la.items ? la.items[blockIdx.x / C] : la.one_item;
+  CItem it = la.items ? la.items[blockIdx.x / C] : la.one_item;
+  if (!la.items) it.off += (int64_t)(blockIdx.x / C) * la.stride;
   // copy the pass twiddles to shared memory while phase 1 runs; 16-byte chunks
   for (int i = tid; i < Shape<R3>::TABS / 2; i += T) {
     const unsigned dst = (unsigned)__cvta_generic_to_shared(tws + 2 * i);

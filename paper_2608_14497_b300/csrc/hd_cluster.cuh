@@ -20,10 +20,12 @@ struct CItem {
 };
 
 // Items of one launch (all of the same (C, m), one cluster each), or one item
-// by value (items == nullptr).
+// by value (items == nullptr) repeated at offsets one_item.off + i * stride
+// (a batch of equal lengths).
 struct ClusterLaunch {
   const CItem* items;
   CItem one_item;
+  int64_t stride;
   int* err;  // device error word (bounded waits that gave up), or nullptr
 };
 

@@ -79,9 +79,9 @@ namespace hd {
 // thread) and return the status (HD_ECUDA for cuda_fail).
 hd_status fail(hd_status s, const char* what);
 hd_status cuda_fail(cudaError_t e, const char* where);
-hd_status ensure_ws(hd_ctx* c, size_t bytes);
+hd_status ensure_ws(hd_ctx* c, size_t bytes, cudaStream_t st);
 // Dynamic shared-memory opt-in of a kernel, set once per device and size.
 cudaError_t smem_optin(const void* fn, size_t smem);
-hd_status ensure_ws2(hd_ctx* c, size_t bytes);
+hd_status ensure_ws2(hd_ctx* c, size_t bytes, cudaStream_t st);
 hd_status ensure_meta(hd_ctx* c, size_t bytes);
 }  // namespace hd

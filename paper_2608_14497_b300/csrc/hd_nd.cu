@@ -191,73 +191,139 @@ static hd_status row_params(hd_ctx* c, int64_t L, bool packed, const hd_dim_para
   return cp->tw ? HD_OK : terr;
 }
 
-static hd_status hybrid_rcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_params* prm, const float* f,
-                               const float* g, float* h, cudaStream_t st, bool tc = false) {
-  // d = 2: [L0][L1]; d = 3: [L0][L1][L2]; the last dimension is packed
-  const int64_t Ln = L[d - 1];
-  const int64_t Lp = (Ln + 1) / 2;
+// Outer and row parameters of a hybridRCM 2D/3D convolution.
+struct RcmNdPlan {
   ColPass outer[2], row;
+  int64_t Lp, M0, M1;
+};
+static hd_status rcm_nd_plan(hd_ctx* c, int d, const int64_t* L, const hd_dim_params* prm, RcmNdPlan* P,
+                             cudaStream_t st) {
+  P->Lp = (L[d - 1] + 1) / 2;
   for (int i = 0; i < d - 1; ++i) {
-    hd_status s = outer_params(c, L[i], prm ? &prm[i] : nullptr, &outer[i], st);
+    hd_status s = outer_params(c, L[i], prm ? &prm[i] : nullptr, &P->outer[i], st);
     if (s != HD_OK) return s;
   }
-  hd_status s = row_params(c, Ln, true, prm ? &prm[d - 1] : nullptr, &row, st);
+  hd_status s = row_params(c, L[d - 1], true, prm ? &prm[d - 1] : nullptr, &P->row, st);
   if (s != HD_OK) return s;
-  const int64_t M0 = (int64_t)outer[0].q * outer[0].m;
-  const int64_t M1 = d == 3 ? (int64_t)outer[1].q * outer[1].m : 1;
-  // scratch: F, G spectra [M0][M1][Lp] plus (3D) the intermediate [M0][L1][Lp]
-  const int64_t spec = M0 * M1 * Lp;
-  const int64_t mid = d == 3 ? M0 * L[1] * Lp : 0;
-  const size_t bytes = sizeof(float2) * (size_t)(2 * spec + 2 * mid);
-  if (ensure_ws(c, bytes) != HD_OK) return HD_ENOMEM;
+  P->M0 = (int64_t)P->outer[0].q * P->outer[0].m;
+  P->M1 = d == 3 ? (int64_t)P->outer[1].q * P->outer[1].m : 1;
+  return HD_OK;
+}
+
+// Forward outer passes of one real array (batch items back to back, each
+// [L0][L1] or [L0][L1][L2]) into its outer spectra S = [batch][M0][M1][Lp];
+// T is the 3D intermediate [batch][M0][L1][Lp].
+static hd_status rcm_nd_forward(hd_ctx* c, int d, const int64_t* L, int64_t batch, const RcmNdPlan& P,
+                                const float* x, int in_mode, float2* S, float2* T, cudaStream_t st, bool tc) {
+  const int Ln = (int)L[d - 1];
+  if (d == 2) return col_fwd(c, x, in_mode, Ln, S, batch, (int)L[0], P.Lp, P.outer[0], st, 0, tc);
+  hd_status s = col_fwd(c, x, in_mode, Ln, T, batch, (int)L[0], L[1] * P.Lp, P.outer[0], st, P.Lp, tc);
+  if (s == HD_OK) s = col_fwd(c, T, IN_COMPLEX, 0, S, batch * P.M0, (int)L[1], P.Lp, P.outer[1], st, 0, tc);
+  return s;
+}
+
+// Backward outer passes from the outer spectra S to the real result.
+static hd_status rcm_nd_backward(hd_ctx* c, int d, const int64_t* L, int64_t batch, const RcmNdPlan& P,
+                                 const float2* S, float2* T, float* z, int out_mode, cudaStream_t st, bool tc) {
+  const int Ln = (int)L[d - 1];
+  if (d == 2)
+    return col_bwd(c, S, z, out_mode, Ln, batch, (int)L[0], P.Lp, P.outer[0], 1.0f / (float)P.M0, st, 0, tc);
+  hd_status s =
+      col_bwd(c, S, T, OUT_COMPLEX, 0, batch * P.M0, (int)L[1], P.Lp, P.outer[1], 1.0f / (float)P.M1, st, 0, tc);
+  if (s == HD_OK)
+    s = col_bwd(c, T, z, out_mode, Ln, batch, (int)L[0], L[1] * P.Lp, P.outer[0], 1.0f / (float)P.M0, st, P.Lp,
+                tc);
+  return s;
+}
+
+static RowGeom rcm_row_geom(int d, int64_t batch, const RcmNdPlan& P) {
+  RowGeom rg;
+  std::memset(&rg, 0, sizeof(rg));
+  rg.rpi = (int)(P.M0 * P.M1);
+  rg.nrows = (int)(batch * P.M0 * P.M1);
+  rg.Lrow = (int)P.Lp;
+  rg.m = P.row.m;
+  rg.q = P.row.q;
+  rg.p = P.row.p;
+  rg.nd = d - 1;
+  rg.om[0] = P.outer[0].m;
+  rg.oq[0] = P.outer[0].q;
+  if (d == 3) {
+    rg.om[1] = P.outer[1].m;
+    rg.oq[1] = P.outer[1].q;
+  }
+  return rg;
+}
+
+// hybridRCM in 2D/3D (Sec. 5) for `batch` problems stored back to back: outer
+// forward passes of f and g, C_1 on every row pair, outer backward passes.
+static hd_status hybrid_rcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_params* prm, const float* f,
+                               const float* g, float* h, cudaStream_t st, bool tc = false, int64_t batch = 1) {
+  RcmNdPlan P;
+  hd_status s = rcm_nd_plan(c, d, L, prm, &P, st);
+  if (s != HD_OK) return s;
+  // scratch: F, G spectra [batch][M0][M1][Lp] plus (3D) the intermediates [batch][M0][L1][Lp]
+  const int64_t spec = batch * P.M0 * P.M1 * P.Lp;
+  const int64_t mid = d == 3 ? batch * P.M0 * L[1] * P.Lp : 0;
+  if (ensure_ws(c, sizeof(float2) * (size_t)(2 * spec + 2 * mid), st) != HD_OK) return HD_ENOMEM;
   float2* SF = reinterpret_cast<float2*>(c->ws);
   float2* SG = SF + spec;
   float2* TF = SG + spec;
   float2* TG = TF + mid;
-  // forward along the outer dimensions
-  if (d == 2) {
-    s = col_fwd(c, f, IN_PACKED_REAL, (int)Ln, SF, 1, (int)L[0], Lp, outer[0], st, 0, tc);
-    if (s == HD_OK) s = col_fwd(c, g, IN_PACKED_REAL, (int)Ln, SG, 1, (int)L[0], Lp, outer[0], st, 0, tc);
-  } else {
-    s = col_fwd(c, f, IN_PACKED_REAL, (int)Ln, TF, 1, (int)L[0], L[1] * Lp, outer[0], st, Lp, tc);
-    if (s == HD_OK) s = col_fwd(c, g, IN_PACKED_REAL, (int)Ln, TG, 1, (int)L[0], L[1] * Lp, outer[0], st, Lp, tc);
-    if (s == HD_OK) s = col_fwd(c, TF, IN_COMPLEX, 0, SF, M0, (int)L[1], Lp, outer[1], st, 0, tc);
-    if (s == HD_OK) s = col_fwd(c, TG, IN_COMPLEX, 0, SG, M0, (int)L[1], Lp, outer[1], st, 0, tc);
-  }
+  s = rcm_nd_forward(c, d, L, batch, P, f, IN_PACKED_REAL, SF, TF, st, tc);
+  if (s == HD_OK) s = rcm_nd_forward(c, d, L, batch, P, g, IN_PACKED_REAL, SG, TG, st, tc);
   if (s != HD_OK) return s;
-  // rows: C_1 on each row pair
-  RowGeom rg;
-  std::memset(&rg, 0, sizeof(rg));
-  rg.nrows = (int)(M0 * M1);
-  rg.Lrow = (int)Lp;
-  rg.m = row.m;
-  rg.q = row.q;
-  rg.p = row.p;
-  rg.nd = d - 1;
-  rg.om[0] = outer[0].m;
-  rg.oq[0] = outer[0].q;
-  if (d == 3) {
-    rg.om[1] = outer[1].m;
-    rg.oq[1] = outer[1].q;
-  }
-  // arrays per residue step: {A, C, B, D} x (1 or 2 residues); with q <= 2
-  // every residue is its own partner, so 4
-  const int narr = row.q <= 2 ? 4 : 8;
-  const Eng reng = pick_eng(tc, struct_length(row.m) && row.q <= 2);
-  const size_t smem = sizeof(float2) * ((size_t)acc_slots(2 * (int)Lp) + narr * (size_t)row.m);
-  if (smem > (size_t)c->max_smem || narr * (int64_t)row.m > max_points(reng)) return HD_EUNSUPPORTED;
-  const int T = eng_threads(reng, narr * (int64_t)row.m);
-  HD_TRY(launch_rows_rcm(reng, (unsigned)rg.nrows, T, smem, st, SF, SG, rg, 1.0f / (float)(row.q * row.m), row.tw,
-             row.pl));
-  // backward along the outer dimensions, unpacking at the end
-  if (d == 2) {
-    s = col_bwd(c, SF, h, OUT_UNPACK_REAL, (int)Ln, 1, (int)L[0], Lp, outer[0], 1.0f / (float)M0, st, 0, tc);
-  } else {
-    s = col_bwd(c, SF, TF, OUT_COMPLEX, 0, M0, (int)L[1], Lp, outer[1], 1.0f / (float)M1, st, 0, tc);
-    if (s == HD_OK)
-      s = col_bwd(c, TF, h, OUT_UNPACK_REAL, (int)Ln, 1, (int)L[0], L[1] * Lp, outer[0], 1.0f / (float)M0, st, Lp,
-                  tc);
-  }
+  // rows: C_1 on each row pair; arrays per residue step: {A, C, B, D} x (1 or
+  // 2 residues); with q <= 2 every residue is its own partner, so 4
+  const RowGeom rg = rcm_row_geom(d, batch, P);
+  const int narr = P.row.q <= 2 ? 4 : 8;
+  const Eng reng = pick_eng(tc, struct_length(P.row.m) && P.row.q <= 2);
+  const size_t smem = sizeof(float2) * ((size_t)acc_slots(2 * (int)P.Lp) + narr * (size_t)P.row.m);
+  if (smem > (size_t)c->max_smem || narr * (int64_t)P.row.m > max_points(reng)) return HD_EUNSUPPORTED;
+  const int T = eng_threads(reng, narr * (int64_t)P.row.m);
+  HD_TRY(launch_rows_rcm(reng, (unsigned)rg.nrows, T, smem, st, SF, SG, rg, 1.0f / (float)(P.row.q * P.row.m),
+                         P.row.tw, P.row.pl));
+  return rcm_nd_backward(c, d, L, batch, P, SF, TF, h, OUT_UNPACK_REAL, st, tc);
+}
+
+// The adjoint of hybridRCM 2D/3D for `batch` problems: U = outer spectra of
+// rev(grad_h) (the reversal folded into the first pass's loads), F and G the
+// outer spectra of f and g; one row pass forms U's row transforms once and
+// applies C_1 to (U, G) and (U, F); the backward passes write grad_f =
+// rev(conv(rev(grad_h), g)) and grad_g = rev(conv(rev(grad_h), f)), the
+// reversal folded into the last pass's stores.  Nothing is stored from the
+// forward call.
+hd_status adjoint_rcm_nd(hd_ctx* c, int d, const int64_t* L, int64_t batch, const float* u, const float* f,
+                         const float* g, float* gf, float* gg, cudaStream_t st) {
+  RcmNdPlan P;
+  hd_status s = rcm_nd_plan(c, d, L, nullptr, &P, st);
+  if (s != HD_OK) return s;
+  const int64_t spec = batch * P.M0 * P.M1 * P.Lp;
+  const int64_t mid = d == 3 ? batch * P.M0 * L[1] * P.Lp : 0;
+  if (ensure_ws(c, sizeof(float2) * (size_t)(3 * spec + mid), st) != HD_OK) return HD_ENOMEM;
+  float2* SU = reinterpret_cast<float2*>(c->ws);
+  float2* SF = SU + spec;
+  float2* SG = SF + spec;
+  float2* TM = SG + spec;  // 3D intermediate, reused by every pass
+  // Both gradients: SG <- g, SF <- f.  One gradient: its source (g for
+  // grad_f, f for grad_g) goes to SG, SF aliases SG and only G is written.
+  const bool both = gf && gg;
+  s = rcm_nd_forward(c, d, L, batch, P, u, IN_PACKED_REAL_REV, SU, TM, st, false);
+  if (s == HD_OK) s = rcm_nd_forward(c, d, L, batch, P, gf ? g : f, IN_PACKED_REAL, SG, TM, st, false);
+  if (s == HD_OK && both) s = rcm_nd_forward(c, d, L, batch, P, f, IN_PACKED_REAL, SF, TM, st, false);
+  if (!both) SF = SG;
+  if (s != HD_OK) return s;
+  const RowGeom rg = rcm_row_geom(d, batch, P);
+  const int narr = P.row.q <= 2 ? 6 : 12;  // {U, F, G} x {row, partner} x residues
+  const Eng reng = pick_eng(false, struct_length(P.row.m) && P.row.q <= 2);
+  const size_t smem = sizeof(float2) * ((size_t)acc_slots(4 * (int)P.Lp) + narr * (size_t)P.row.m);
+  if (smem > (size_t)c->max_smem || narr * (int64_t)P.row.m > max_points(reng)) return HD_EUNSUPPORTED;
+  const int T = eng_threads(reng, narr * (int64_t)P.row.m);
+  const int outs = both ? 3 : 1;
+  HD_TRY(launch_rows_adj(reng, (unsigned)rg.nrows, T, smem, st, SF, SG, SU, rg, 1.0f / (float)(P.row.q * P.row.m),
+                         outs, P.row.tw, P.row.pl));
+  if (gf) s = rcm_nd_backward(c, d, L, batch, P, SG, TM, gf, OUT_UNPACK_REAL_REV, st, false);
+  if (s == HD_OK && gg) s = rcm_nd_backward(c, d, L, batch, P, both ? SF : SG, TM, gg, OUT_UNPACK_REAL_REV, st, false);
   return s;
 }
 
@@ -297,7 +363,7 @@ static hd_status hybrid_cs_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_p
   const int64_t rowsz = (d == 3 ? M1 : 1) * Lr;  // complex elements per first-dim row of the spectra
   const int64_t spec = (int64_t)R0 * rowsz;
   const int64_t tmp = d == 3 ? (int64_t)R0 * L[1] * Lr : 0;
-  if (ensure_ws(c, sizeof(float2) * (size_t)(2 * spec + 2 * tmp)) != HD_OK) return HD_ENOMEM;
+  if (ensure_ws(c, sizeof(float2) * (size_t)(2 * spec + 2 * tmp), st) != HD_OK) return HD_ENOMEM;
   float2* SF = reinterpret_cast<float2*>(c->ws);
   float2* SG = SF + spec;
   float2* TF = SG + spec;
@@ -363,7 +429,7 @@ hd_status explicit_nd(hd_ctx* c, hd_algo algo, int d, const int64_t* Lin, const 
   const int64_t bins = rcm ? n : n + 1;                 // complex per row after the last-dim pass
   const int64_t Preal = rows * 2 * n;                   // padded real elements per array
   const int64_t spec = rows * bins;
-  if (ensure_ws(c, sizeof(float) * (size_t)(2 * Preal) + sizeof(float2) * (size_t)(2 * spec)) != HD_OK)
+  if (ensure_ws(c, sizeof(float) * (size_t)(2 * Preal) + sizeof(float2) * (size_t)(2 * spec), st) != HD_OK)
     return HD_ENOMEM;
   float* PF = reinterpret_cast<float*>(c->ws);
   float* PG = PF + Preal;
@@ -457,6 +523,14 @@ hd_status explicit_nd(hd_ctx* c, hd_algo algo, int d, const int64_t* Lin, const 
 }  // namespace hd
 
 using namespace hd;
+
+namespace hd {
+// hybridRCM 2D/3D over a batch of equal-size problems (one pass sequence).
+hd_status conv_nd_batch_rcm(hd_ctx* c, int d, const int64_t* L, int64_t batch, const float* f, const float* g,
+                            float* h, cudaStream_t st) {
+  return hybrid_rcm_nd(c, d, L, nullptr, f, g, h, st, false, batch);
+}
+}  // namespace hd
 
 static hd_status conv_nd(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h, int d,
                          const int64_t* L, const hd_dim_params* prm, void* stream) {

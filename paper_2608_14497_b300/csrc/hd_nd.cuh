@@ -7,4 +7,11 @@
 namespace hd {
 hd_status explicit_nd(hd_ctx* c, hd_algo algo, int d, const int64_t* L, const float* f, const float* g, float* h,
                       cudaStream_t st);
+// hybridRCM 2D/3D over `batch` problems of extents L stored back to back.
+hd_status conv_nd_batch_rcm(hd_ctx* c, int d, const int64_t* L, int64_t batch, const float* f, const float* g,
+                            float* h, cudaStream_t st);
+// Gradients of h = conv(f, g) (hybridRCM 2D/3D) for `batch` problems: grad_f =
+// rev(conv(rev(u), g)), grad_g = rev(conv(rev(u), f)); either may be NULL.
+hd_status adjoint_rcm_nd(hd_ctx* c, int d, const int64_t* L, int64_t batch, const float* u, const float* f,
+                         const float* g, float* gf, float* gg, cudaStream_t st);
 }  // namespace hd

@@ -47,9 +47,24 @@ __device__ __forceinline__ int64_t packed_offset(const ColGeom& cg, int64_t a, i
   return ((a * Lrows + j) * (cg.B / cg.Bp) + sub) * (int64_t)Lreal;
 }
 
+// Mirror image of packed element (row j of block a, column b) in a real array
+// reversed on every axis inside its block: rows Lrows-1-j, sub-rows
+// (B/Bp)-1-sub, reals Lreal-1-2c' and Lreal-2-2c' (the second absent when
+// 2c'+1 >= Lreal).  Returns the real offset of the first; *second is -1 when
+// there is none.  The adjoint reads rev(u) and writes rev(result) this way.
+__device__ __forceinline__ int64_t packed_offset_rev(const ColGeom& cg, int64_t a, int64_t Lrows, int64_t j,
+                                                     int64_t b, int Lreal, int64_t* second) {
+  const int64_t nsub = cg.B / cg.Bp;
+  const int64_t sub = b / cg.Bp;
+  const int64_t c2 = 2 * (b - sub * cg.Bp);
+  const int64_t base = ((a * Lrows + (Lrows - 1 - j)) * nsub + (nsub - 1 - sub)) * (int64_t)Lreal;
+  *second = (c2 + 1 < Lreal) ? base + Lreal - 2 - c2 : -1;
+  return base + Lreal - 1 - c2;
+}
+
 // Input element loaders for the column passes.
-enum : int { IN_COMPLEX = 0, IN_PACKED_REAL = 1 };
-enum : int { OUT_COMPLEX = 0, OUT_UNPACK_REAL = 1 };
+enum : int { IN_COMPLEX = 0, IN_PACKED_REAL = 1, IN_PACKED_REAL_REV = 2 };
+enum : int { OUT_COMPLEX = 0, OUT_UNPACK_REAL = 1, OUT_UNPACK_REAL_REV = 2 };
 
 // ---------------------------------------------------------------------------
 // k_col_fwd: complex hybrid forward transform along a strided dimension.
@@ -83,10 +98,15 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_col_fwd(const void*
       const int64_t e = (a * Lin + j) * cg.B + b;
       if (in_mode == IN_COMPLEX) {
         v = reinterpret_cast<const float2*>(Xv)[e];
-      } else {
+      } else if (in_mode == IN_PACKED_REAL) {
         int64_t c;
         const float* fr = reinterpret_cast<const float*>(Xv) + packed_offset(cg, a, Lin, j, b, Lreal, &c);
         v = make_float2(fr[c], (c + 1 < Lreal) ? fr[c + 1] : 0.f);
+      } else {
+        int64_t second;
+        const float* xr = reinterpret_cast<const float*>(Xv);
+        const int64_t first = packed_offset_rev(cg, a, Lin, j, b, Lreal, &second);
+        v = make_float2(xr[first], second >= 0 ? xr[second] : 0.f);
       }
     }
     dst[w * ldst + j] = v;
@@ -181,11 +201,17 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_col_bwd(const float
     const float2 v = cscale(res[w * lres + j], scale);
     if (out_mode == OUT_COMPLEX) {
       reinterpret_cast<float2*>(Zv)[(a * Lout + j) * cg.B + b] = v;
-    } else {
+    } else if (out_mode == OUT_UNPACK_REAL) {
       int64_t c;
       float* hr = reinterpret_cast<float*>(Zv) + packed_offset(cg, a, Lout, j, b, Lreal, &c);
       hr[c] = v.x;
       if (c + 1 < Lreal) hr[c + 1] = v.y;
+    } else {
+      int64_t second;
+      float* zr = reinterpret_cast<float*>(Zv);
+      const int64_t first = packed_offset_rev(cg, a, Lout, j, b, Lreal, &second);
+      zr[first] = v.x;
+      if (second >= 0) zr[second] = v.y;
     }
   }
 }
@@ -393,18 +419,20 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_col_bwd_cs(const float2* __
 // that is its own partner reduces to the 1D RCM of Eqs. Hr / Hr-conj.
 // ---------------------------------------------------------------------------
 struct RowGeom {
-  int nrows;        // rows in the grid
+  int nrows;        // rows in the grid (every item of a batch)
   int Lrow;         // row length (complex)
   int m, q, p;      // hybrid parameters along the row
   int nd;           // number of outer dimensions (1 or 2)
   int om[2], oq[2]; // outer (m, q) per outer dimension
+  int rpi;          // rows per item: rows pair only inside their own item
 };
 
 __device__ __forceinline__ int row_partner(int row, const RowGeom& g) {
-  if (g.nd == 1) return partner_row(row, g.om[0], g.oq[0]);
+  const int item = row / g.rpi, r = row - item * g.rpi;
+  if (g.nd == 1) return item * g.rpi + partner_row(r, g.om[0], g.oq[0]);
   const int M2 = g.om[1] * g.oq[1];
-  const int r1 = row / M2, r2 = row - r1 * M2;
-  return partner_row(r1, g.om[0], g.oq[0]) * M2 + partner_row(r2, g.om[1], g.oq[1]);
+  const int r1 = r / M2, r2 = r - r1 * M2;
+  return item * g.rpi + partner_row(r1, g.om[0], g.oq[0]) * M2 + partner_row(r2, g.om[1], g.oq[1]);
 }
 
 template <int PTS, bool TC, bool SE>
@@ -516,6 +544,133 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_rows_rcm(float2* F,
   for (int idx = tid; idx < nrow * Lr; idx += T) {
     const int rr = idx / Lr, j = idx - rr * Lr;
     F[(int64_t)(rr ? prow : row) * Lr + j] = cscale(acc[idx], scale);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_rows_adj: the row pass of the adjoint.  For the row pair (row, prow) of
+// the outer spectra of U = rev(grad_h), F and G it forms the row transforms of
+// U once and applies the operator C_1 (Sec. 5) to (U, G) and to (U, F):
+//   G rows <- C_1(U, G)  (outer spectra of rev(grad_f)),
+//   F rows <- C_1(U, F)  (outer spectra of rev(grad_g)),
+// in place; `outs` selects which of the two are written (bit 0: G, bit 1: F).
+// Shared arrays per residue step: [U, F, G] x [row, partner] x [residues].
+// ---------------------------------------------------------------------------
+template <int PTS, bool SE>
+__global__ void __launch_bounds__(SE ? 512 : 1024) k_rows_adj(float2* F, float2* G, const float2* __restrict__ U,
+                                                              RowGeom rg, float scale, int outs,
+                                                              const float2* __restrict__ tw, FftPlan pl) {
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  const int row = blockIdx.x;
+  const int prow = row_partner(row, rg);
+  if (prow < row) return;
+  const bool selfrow = (prow == row);
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int Lr = rg.Lrow, m = rg.m, q = rg.q, p = rg.p, N = q * m;
+  const int nrow = selfrow ? 1 : 2;
+  float2* acc = sm;                              // [output (0: G, 1: F)][nrow][Lr]
+  float2* buf = sm + acc_slots(2 * nrow * Lr);   // arrays of m
+  const float2* srcs[3] = {U, F, G};
+  for (int idx = tid; idx < 2 * nrow * Lr; idx += T) acc[idx] = make_float2(0.f, 0.f);
+  __syncthreads();
+  auto residue_pass = [&](int ra) __attribute__((always_inline)) {
+    const int rb = (q - ra) % q;
+    const bool selfres = (ra == rb);
+    const int nres = selfres ? 1 : 2;
+    const int narr = 3 * nrow * nres;
+    auto arr = [&](int which, int k, int slot) { return buf + (size_t)((which * nrow + k) * nres + slot) * m; };
+    // Eq. forwardr, first half, for every (source, row, residue)
+    for (int idx = tid; idx < narr * m; idx += T) {
+      const int a = idx / m, s = idx - a * m;
+      const int slot = a % nres, k = (a / nres) % nrow, which = a / (nres * nrow);
+      const float2* x = srcs[which] + (int64_t)(k ? prow : row) * Lr;
+      const int r = slot ? rb : ra;
+      float2 sum = make_float2(0.f, 0.f);
+      int e = r * s;
+      for (int t = 0; t < p; ++t) {
+        const int j = t * m + s;
+        if (j >= Lr) break;
+        sum = cadd(sum, cmul(x[j], tw_get<1>(tw, e)));
+        e += r * m;
+        if (e >= N) e -= N;
+      }
+      buf[idx] = sum;
+    }
+    __syncthreads();
+    fft_sel<1, PTS, false, SE>(buf, m, narr, pl, tw, q);
+    // C_1 on (U, G) and (U, F); U's transforms are only read
+    if (selfrow) {
+      const int sb = selfres ? 0 : 1;
+      for (int l = tid; l < m; l += T) {
+        int ls;
+        if (selfres) {
+          ls = (ra == 0) ? (l == 0 ? 0 : m - l) : (m - 1 - l);
+          if (l > ls) continue;
+        } else {
+          ls = m - 1 - l;
+        }
+        const float2 Uk = arr(0, 0, 0)[l], Uc = arr(0, 0, sb)[ls];
+        const float2 z = tw_get<1>(tw, q * l + ra);
+        const float2 Z = make_float2(0.25f * (1.f + z.x), 0.25f * z.y);
+        const float2 du = csub(Uk, cconj(Uc));
+#pragma unroll
+        for (int which = 1; which <= 2; ++which) {
+          float2* Bl = arr(which, 0, 0);
+          float2* Bs = arr(which, 0, sb);
+          const float2 B = Bl[l], Bc = Bs[ls];
+          const float2 alpha = cmul(cmul(du, csub(B, cconj(Bc))), Z);
+          Bl[l] = csub(cmul(Uk, B), alpha);
+          if (!(selfres && ls == l)) Bs[ls] = csub(cmul(Uc, Bc), cconj(alpha));
+        }
+      }
+    } else {
+      for (int idx = tid; idx < nres * m; idx += T) {
+        const int slot = idx / m, l = idx - slot * m;
+        const int r = slot ? rb : ra;
+        const int pslot = selfres ? 0 : 1 - slot;
+        const int ls = (r == 0) ? (l == 0 ? 0 : m - l) : (m - 1 - l);
+        const float2 A = arr(0, 0, slot)[l], Cs = arr(0, 1, pslot)[ls];
+        const float2 z = tw_get<1>(tw, q * l + r);
+        const float2 Z = make_float2(0.25f * (1.f + z.x), 0.25f * z.y);
+        const float2 du = csub(A, cconj(Cs));
+#pragma unroll
+        for (int which = 1; which <= 2; ++which) {
+          float2* Br = arr(which, 0, slot);
+          float2* Dr = arr(which, 1, pslot);
+          const float2 B = Br[l], D = Dr[ls];
+          const float2 alpha = cmul(cmul(du, csub(B, cconj(D))), Z);
+          Br[l] = csub(cmul(A, B), alpha);
+          Dr[ls] = csub(cmul(Cs, D), cconj(alpha));
+        }
+      }
+    }
+    __syncthreads();
+    // inverse of the F and G arrays (contiguous after the U arrays)
+    fft_sel<-1, PTS, false, SE>(arr(1, 0, 0), m, 2 * nrow * nres, pl, tw, q);
+    for (int idx = tid; idx < 2 * nrow * Lr; idx += T) {
+      const int o = idx / (nrow * Lr), rem = idx - o * nrow * Lr;
+      const int rr = rem / Lr, j = rem - rr * Lr;
+      const int which = o == 0 ? 2 : 1;
+      const int s = j % m;
+      float2 v = cmul(arr(which, rr, 0)[s], tw_get<-1>(tw, modmul(ra, j, N)));
+      if (!selfres) v = cadd(v, cmul(arr(which, rr, 1)[s], tw_get<-1>(tw, modmul(rb, j, N))));
+      acc[idx] = cadd(acc[idx], v);
+    }
+    __syncthreads();
+  };
+  if constexpr (SE) {
+    residue_pass(0);
+    if (q > 1) residue_pass(1);
+  } else {
+    for (int ra = 0; ra <= q / 2; ++ra) residue_pass(ra);
+  }
+  for (int idx = tid; idx < 2 * nrow * Lr; idx += T) {
+    const int o = idx / (nrow * Lr), rem = idx - o * nrow * Lr;
+    if (!((outs >> o) & 1)) continue;
+    const int rr = rem / Lr, j = rem - rr * Lr;
+    float2* dst = (o == 0 ? G : F) + (int64_t)(rr ? prow : row) * Lr;
+    dst[j] = cscale(acc[idx], scale);
   }
 }
 
@@ -692,6 +847,8 @@ cudaError_t launch_col_bwd_cs(Eng e, unsigned grid, int T, size_t smem, cudaStre
                               FftPlan pl_h);
 cudaError_t launch_rows_rcm(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, float2* F, const float2* G,
                             RowGeom rg, float scale, const float2* tw, FftPlan pl);
+cudaError_t launch_rows_adj(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, float2* F, float2* G,
+                            const float2* U, RowGeom rg, float scale, int outs, const float2* tw, FftPlan pl);
 cudaError_t launch_rows_cconv(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, float2* F, const float2* G,
                               int Lr, int m, int q, int p, float scale, const float2* tw, FftPlan pl);
 cudaError_t launch_rows_fft(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, RowsIO io, int mode, int n,

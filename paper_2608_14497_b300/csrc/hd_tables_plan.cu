@@ -179,15 +179,15 @@ cudaError_t smem_optin(const void* fn, size_t smem) {
   return e;
 }
 
-hd_status ensure_ws(hd_ctx* c, size_t bytes) {
+// Grow the context's scratch to `bytes`, stream-ordered on `st`: the old area
+// is released after the work already queued on `st` and the new one is ready
+// for what follows, with no device synchronisation.
+hd_status ensure_ws(hd_ctx* c, size_t bytes, cudaStream_t st) {
   if (bytes <= c->ws_bytes) return HD_OK;
-  if (c->ws) {
-    cudaDeviceSynchronize();
-    cudaFree(c->ws);
-    c->ws = nullptr;
-    c->ws_bytes = 0;
-  }
-  if (cudaMalloc(&c->ws, bytes) != cudaSuccess) return HD_ENOMEM;
+  if (c->ws) cudaFreeAsync(c->ws, st);
+  c->ws = nullptr;
+  c->ws_bytes = 0;
+  if (cudaMallocAsync(&c->ws, bytes, st) != cudaSuccess) return HD_ENOMEM;
   c->ws_bytes = bytes;
   return HD_OK;
 }

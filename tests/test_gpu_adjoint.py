@@ -106,3 +106,50 @@ def test_adjoint_batch16_1024_full_items(hd):
         ef = record_rel(f"adjoint 16x1024^2 item {b} grad_f", rel_l2(gf[b], ref_f), TOL, ref_f.size)
         eg = record_rel(f"adjoint 16x1024^2 item {b} grad_g", rel_l2(gg[b], ref_g), TOL, ref_g.size)
         assert ef <= TOL and eg <= TOL
+
+
+@pytest.mark.parametrize("shape", [(5, 7), (33, 40), (4, 5, 6), (9, 8, 7), (64, 3)])
+@pytest.mark.parametrize("which", ["f", "g"])
+def test_adjoint_single_gradient(hd, shape, which):
+    """Only one gradient requested (the other pointer NULL, its input absent)."""
+    rng = np.random.default_rng(75)
+    f, g, u = (rng.uniform(-1, 1, (3,) + shape).astype(np.float32) for _ in range(3))
+    gf, gg = hd.adjoint(cuda(u), cuda(f), cuda(g), "hybridRCM", need_f=(which == "f"), need_g=(which == "g"))
+    for b in range(3):
+        if which == "f":
+            assert gg is None
+            assert rel_l2(gf.cpu().numpy()[b], oracle.direct_corr(u[b], g[b])) <= TOL
+        else:
+            assert gf is None
+            assert rel_l2(gg.cpu().numpy()[b], oracle.direct_corr(u[b], f[b])) <= TOL
+
+
+def test_adjoint_rejects_overlap(hd):
+    """A gradient that overlaps an input would be read after it is written."""
+    x = torch.zeros((2, 8, 8), device="cuda")
+    y = torch.zeros_like(x)
+    out = torch.zeros_like(x)
+    ctx = hd.context()
+    st = hd.hd_conv_adjoint(ctx, hd.HD_HYBRID_RCM, (8, 8), 2, out.data_ptr(), x.data_ptr(), y.data_ptr(),
+                            x.data_ptr(), None, 0)
+    assert st == hd.HD_EINVAL
+    assert b"overlap" in hd.load().hd_last_error_string()
+    st = hd.hd_conv_adjoint(ctx, hd.HD_HYBRID_RCM, (8, 8), 2, out.data_ptr(), x.data_ptr(), y.data_ptr(),
+                            out.data_ptr(), None, 0)
+    assert st == hd.HD_EINVAL
+
+
+def test_autograd_non_contiguous_inputs(hd):
+    """Transposed (non-contiguous) leaves: forward and backward both run."""
+    rng = np.random.default_rng(76)
+    f, g, u = (rng.uniform(-1, 1, (2, 24, 20)).astype(np.float32) for _ in range(3))
+    tf = cuda(f.transpose(0, 2, 1)).transpose(1, 2).requires_grad_(True)  # values of f, strides transposed
+    tg = cuda(g)
+    tg = tg.requires_grad_(True)
+    assert not tf.is_contiguous()
+    h = hd.hd_conv_fn(tf, tg, "hybridRCM")
+    (h * cuda(u)).sum().backward()
+    for b in range(2):
+        assert rel_l2(h.detach().cpu().numpy()[b], oracle.direct_conv(f[b], g[b])) <= TOL
+        assert rel_l2(tf.grad.cpu().numpy()[b], oracle.direct_corr(u[b], g[b])) <= TOL
+        assert rel_l2(tg.grad.cpu().numpy()[b], oracle.direct_corr(u[b], f[b])) <= TOL
