@@ -170,7 +170,7 @@ static hd_status outer_params(hd_ctx* c, int64_t L, const hd_dim_params* prm, Co
 // Parameters of the last (row) dimension for the RCM rows (packed, needs
 // q m >= L) or CS rows (complex, needs q m >= 2L-1).
 static hd_status row_params(hd_ctx* c, int64_t L, bool packed, const hd_dim_params* prm, ColPass* cp,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool cl_rows = false) {
   const int64_t Lr = packed ? (L + 1) / 2 : L;
   const int64_t need = packed ? L : 2 * L - 1;
   int64_t m, q;
@@ -181,6 +181,15 @@ static hd_status row_params(hd_ctx* c, int64_t L, bool packed, const hd_dim_para
   } else {
     m = ladder_ceil(Lr);
     q = (need + m - 1) / m;
+    if (packed && cl_rows && Lr > 128) {
+      // the row-pair kernel on the compile-time engine: q = 2, m = 256 R3 >= Lp
+      for (int R3 : {1, 2, 3, 4, 5, 6, 8})
+        if (256 * R3 >= Lr) {
+          m = 256 * R3;
+          q = 2;
+          break;
+        }
+    }
   }
   cp->m = (int)m;
   cp->q = (int)q;
@@ -197,13 +206,13 @@ struct RcmNdPlan {
   int64_t Lp, M0, M1;
 };
 static hd_status rcm_nd_plan(hd_ctx* c, int d, const int64_t* L, const hd_dim_params* prm, RcmNdPlan* P,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool cl_rows = false) {
   P->Lp = (L[d - 1] + 1) / 2;
   for (int i = 0; i < d - 1; ++i) {
     hd_status s = outer_params(c, L[i], prm ? &prm[i] : nullptr, &P->outer[i], st);
     if (s != HD_OK) return s;
   }
-  hd_status s = row_params(c, L[d - 1], true, prm ? &prm[d - 1] : nullptr, &P->row, st);
+  hd_status s = row_params(c, L[d - 1], true, prm ? &prm[d - 1] : nullptr, &P->row, st, cl_rows);
   if (s != HD_OK) return s;
   P->M0 = (int64_t)P->outer[0].q * P->outer[0].m;
   P->M1 = d == 3 ? (int64_t)P->outer[1].q * P->outer[1].m : 1;
@@ -260,7 +269,7 @@ static RowGeom rcm_row_geom(int d, int64_t batch, const RcmNdPlan& P) {
 static hd_status hybrid_rcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_params* prm, const float* f,
                                const float* g, float* h, cudaStream_t st, bool tc = false, int64_t batch = 1) {
   RcmNdPlan P;
-  hd_status s = rcm_nd_plan(c, d, L, prm, &P, st);
+  hd_status s = rcm_nd_plan(c, d, L, prm, &P, st, !tc);
   if (s != HD_OK) return s;
   // scratch: F, G spectra [batch][M0][M1][Lp] plus (3D) the intermediates [batch][M0][L1][Lp]
   const int64_t spec = batch * P.M0 * P.M1 * P.Lp;
@@ -276,6 +285,14 @@ static hd_status hybrid_rcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_
   // rows: C_1 on each row pair; arrays per residue step: {A, C, B, D} x (1 or
   // 2 residues); with q <= 2 every residue is its own partner, so 4
   const RowGeom rg = rcm_row_geom(d, batch, P);
+  if (!tc && P.row.q == 2 && rows_cl_length(P.row.m)) {
+    hd_status terr = HD_OK;
+    const float2* tab = c->tables.get_pass_table(P.row.m, st, &terr);
+    if (!tab) return terr;
+    HD_TRY(launch_rows_cl(P.row.m, (unsigned)rg.nrows, st, SF, SG, rg, 1.0f / (float)(P.row.q * P.row.m), P.row.tw,
+                          tab));
+    return rcm_nd_backward(c, d, L, batch, P, SF, TF, h, OUT_UNPACK_REAL, st, tc);
+  }
   const int narr = P.row.q <= 2 ? 4 : 8;
   const Eng reng = pick_eng(tc, struct_length(P.row.m) && P.row.q <= 2);
   const size_t smem = sizeof(float2) * ((size_t)acc_slots(2 * (int)P.Lp) + narr * (size_t)P.row.m);

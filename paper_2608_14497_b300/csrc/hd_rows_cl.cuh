@@ -1,0 +1,199 @@
+// hd_rows_cl.cuh -- the row pass of hybridRCM in 2D/3D (Sec. 5, operator C_1)
+// on the compile-time DFT engine of the cluster kernel (hd_cl_kernel.cuh).
+//
+// After the outer passes every row of the outer spectra F and G (packed
+// complex, length Lp) must be convolved along the row with the operator C_1,
+// which couples row k1 with its conjugate partner row k1* (Eqs. RCM-ndim).
+// One CTA takes a row pair: the hybrid transform of each row with q = 2
+// residues of length M = 256 R3 >= Lp (p = 1: residue 0 is the DFT of the row,
+// residue 1 the DFT of the row times zeta_{2M}^s, Eq. forwardr), C_1 on the
+// digit-reversed spectra (residue 0: l pairs with (M - l) mod M; residue 1: l
+// with M - 1 - l; the partner values come from the partner row, or from the
+// same row when the row is its own partner), the backward transforms of the
+// two products (Eq. accumulator), and h~_s = (w_0[s] + zeta_{2M}^{-s} w_1[s]) /
+// (2M) written back over F's rows (Eq. accumulation).
+//
+// Shared arrays, M complex each, layout of hd_cl_kernel.cuh (phys): for a row
+// pair [F row r0, F row r1, F partner r0, F partner r1, G row r0, G row r1,
+// G partner r0, G partner r1]; for a row that is its own partner [F r0, F r1,
+// G r0, G r1] (the one-CTA layout of the cluster kernel); pass twiddles behind.
+#pragma once
+#include "hd_cl_kernel.cuh"
+#include "hd_nd_kernels.cuh"
+
+namespace hd {
+namespace rows {
+
+using cl::phys;
+
+template <int R3>
+struct RowShape {
+  static constexpr int M = 256 * R3;
+  static constexpr int T = 32 * R3;
+  static constexpr size_t SMEM = sizeof(float2) * (8 * (size_t)M + cl::Shape<R3>::TABS);
+  // CTAs per SM the launch bounds ask registers for (what shared memory allows)
+  static constexpr int MINB = R3 == 1 ? 12 : R3 == 2 ? 6 : R3 <= 4 ? 3 : 2;
+};
+
+template <int R3>
+struct RowSteps {
+  using K = cl::Steps<1, R3>;
+  static constexpr int M = K::M;
+  static constexpr int T = K::T;
+
+  // residues 0 and 1 of source row x (p = 1) into arrays a0, a0 + M, pairs of s
+  static __device__ __forceinline__ void load_row(const float2* __restrict__ x, int Lp, float2* a0,
+                                                  const float2* __restrict__ tw, int tid) {
+#pragma unroll 2
+    for (int k = tid; k < M / 2; k += T) {
+      const int s = 2 * k;
+      float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+      if (s + 1 < Lp) {
+        v0 = x[s];
+        v1 = x[s + 1];
+      } else if (s < Lp) {
+        v0 = x[s];
+      }
+      const float4 w = cl::ldg4(tw + s);  // zeta_{2M}^s, zeta_{2M}^{s+1}
+      cl::sts4(a0 + phys(s), v0, v1);
+      cl::sts4(a0 + M + phys(s), cmul(v0, make_float2(w.x, w.y)), cmul(v1, make_float2(w.z, w.w)));
+    }
+  }
+
+  // C_1 across a row pair: residue 0 with the (M - l) mod M pairing (one
+  // position per task), residue 1 with M - 1 - p (pairs of positions).
+  static __device__ __forceinline__ void product_pair(float2* arr, const float2* __restrict__ zt, float2 z1, int tid) {
+    float2* Fr0 = arr;
+    float2* Fr1 = arr + M;
+    float2* Fp0 = arr + 2 * M;
+    float2* Fp1 = arr + 3 * M;
+    const float2* Gr0 = arr + 4 * M;
+    const float2* Gr1 = arr + 5 * M;
+    const float2* Gp0 = arr + 6 * M;
+    const float2* Gp1 = arr + 7 * M;
+    for (int p = tid; p < M; p += T) {
+      const int l = cl::digit_freq(p, R3);
+      const int ps = cl::digit_pos(l == 0 ? 0 : M - l, R3);
+      float2 A = Fr0[phys(p)], Cs = Fp0[phys(ps)];
+      K::rcm_pair(A, Gr0[phys(p)], Cs, Gp0[phys(ps)], K::rcm_factor(cl::ldg2(zt + p), make_float2(1.f, 0.f)), false);
+      Fr0[phys(p)] = A;
+      Fp0[phys(ps)] = Cs;
+    }
+#pragma unroll 2
+    for (int k = tid; k < M / 2; k += T) {
+      const int p = 2 * k, pp = M - 2 - p;
+      float2 A0, A1, B0, B1, C0, C1, D0, D1;
+      cl::lds4(Fr1 + phys(p), A0, A1);
+      cl::lds4(Gr1 + phys(p), B0, B1);
+      cl::lds4(Fp1 + phys(pp), C1, C0);
+      cl::lds4(Gp1 + phys(pp), D1, D0);
+      const float4 z = cl::ldg4(zt + p);
+      K::rcm_pair(A0, B0, C0, D0, K::rcm_factor(make_float2(z.x, z.y), z1), false);
+      K::rcm_pair(A1, B1, C1, D1, K::rcm_factor(make_float2(z.z, z.w), z1), false);
+      cl::sts4(Fr1 + phys(p), A0, A1);
+      cl::sts4(Fp1 + phys(pp), C1, C0);
+    }
+  }
+
+  // h~_s = (w_0[s] + zeta_{2M}^{-s} w_1[s]) * scale for s < Lp, written to row x.
+  static __device__ __forceinline__ void store_row(float2* __restrict__ x, int Lp, const float2* a0,
+                                                   const float2* __restrict__ tw, float scale, int tid) {
+#pragma unroll 2
+    for (int k = tid; k < M / 2; k += T) {
+      const int s = 2 * k;
+      if (s >= Lp) continue;
+      float2 w00, w01, w10, w11;
+      cl::lds4(a0 + phys(s), w00, w01);
+      cl::lds4(a0 + M + phys(s), w10, w11);
+      const float4 w = cl::ldg4(tw + s);
+      x[s] = cscale(cadd(w00, cmul(w10, make_float2(w.x, -w.y))), scale);
+      if (s + 1 < Lp) x[s + 1] = cscale(cadd(w01, cmul(w11, make_float2(w.z, -w.w))), scale);
+    }
+  }
+};
+
+// One row pair per CTA (rows whose partner precedes them exit at once).
+template <int R3>
+__global__ void __launch_bounds__(RowShape<R3>::T, RowShape<R3>::MINB)
+    k_rows_cl(float2* F, const float2* __restrict__ G, RowGeom rg, float scale, const float2* __restrict__ tw,
+              const float2* __restrict__ tab) {
+  using S = RowSteps<R3>;
+  using K = typename S::K;
+  constexpr int M = S::M, T = S::T;
+  const int row = blockIdx.x;
+  const int prow = row_partner(row, rg);
+  if (prow < row) return;
+  extern __shared__ float4 smem_raw[];
+  float2* arr = reinterpret_cast<float2*>(smem_raw);
+  float2* tws = arr + 8 * M;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < cl::Shape<R3>::TABS / 2; i += T) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(tws + 2 * i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(tab + 2 * i) : "memory");
+  }
+  const int Lp = rg.Lrow;
+  const float2* zt = tab + cl::Shape<R3>::TABZ;
+  if (prow == row) {
+    // the row is its own partner: the one-CTA convolution of the cluster kernel
+    S::load_row(F + (int64_t)row * Lp, Lp, arr, tw, tid);
+    S::load_row(G + (int64_t)row * Lp, Lp, arr + 2 * M, tw, tid);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    K::template pass1<1, 4, 2>(arr, tid, tws);
+    __syncthreads();
+    K::template pass2<1, 4, 2>(arr, tid, tws);
+    __syncthreads();
+    K::template pass3<1, 4>(arr, tid);
+    __syncthreads();
+    cl::CtaState x;
+    x.arr = arr;
+    x.c = 0;
+    x.tw = tw;
+    x.tab = tab;
+    K::product(x, tid);
+    __syncthreads();
+    K::template pass3<-1, 2>(arr, tid);
+    __syncthreads();
+    K::template pass2<-1, 2, 1>(arr, tid, tws);
+    __syncthreads();
+    K::template pass1<-1, 2, 1>(arr, tid, tws);
+    __syncthreads();
+    S::store_row(F + (int64_t)row * Lp, Lp, arr, tw, scale, tid);
+    return;
+  }
+  S::load_row(F + (int64_t)row * Lp, Lp, arr, tw, tid);
+  S::load_row(F + (int64_t)prow * Lp, Lp, arr + 2 * M, tw, tid);
+  S::load_row(G + (int64_t)row * Lp, Lp, arr + 4 * M, tw, tid);
+  S::load_row(G + (int64_t)prow * Lp, Lp, arr + 6 * M, tw, tid);
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  K::template pass1<1, 8, 2>(arr, tid, tws);
+  __syncthreads();
+  K::template pass2<1, 8, 2>(arr, tid, tws);
+  __syncthreads();
+  K::template pass3<1, 8>(arr, tid);
+  __syncthreads();
+  S::product_pair(arr, zt, cl::ldg2(tw + 1), tid);
+  __syncthreads();
+  K::template pass3<-1, 4>(arr, tid);
+  __syncthreads();
+  K::template pass2<-1, 4, 1>(arr, tid, tws);
+  __syncthreads();
+  K::template pass1<-1, 4, 1>(arr, tid, tws);
+  __syncthreads();
+  S::store_row(F + (int64_t)row * Lp, Lp, arr, tw, scale, tid);
+  S::store_row(F + (int64_t)prow * Lp, Lp, arr + 2 * M, tw, scale, tid);
+}
+
+template <int R3>
+cudaError_t launch_rows(unsigned grid, cudaStream_t st, float2* F, const float2* G, RowGeom rg, float scale,
+                        const float2* tw, const float2* tab) {
+  auto k = k_rows_cl<R3>;
+  cudaError_t e = smem_optin((const void*)k, RowShape<R3>::SMEM);
+  if (e != cudaSuccess) return e;
+  k<<<grid, RowShape<R3>::T, RowShape<R3>::SMEM, st>>>(F, G, rg, scale, tw, tab);
+  return cudaGetLastError();
+}
+
+}  // namespace rows
+}  // namespace hd
