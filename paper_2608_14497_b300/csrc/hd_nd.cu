@@ -181,7 +181,7 @@ static hd_status row_params(hd_ctx* c, int64_t L, bool packed, const hd_dim_para
   } else {
     m = ladder_ceil(Lr);
     q = (need + m - 1) / m;
-    if (packed && cl_rows && Lr > 128) {
+    if (packed && cl_rows && Lr > 64) {
       // the row-pair kernel on the compile-time engine: q = 2, m = 256 R3 >= Lp
       for (int R3 : {1, 2, 3, 4, 5, 6, 8})
         if (256 * R3 >= Lr) {
@@ -313,7 +313,7 @@ static hd_status hybrid_rcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_
 hd_status adjoint_rcm_nd(hd_ctx* c, int d, const int64_t* L, int64_t batch, const float* u, const float* f,
                          const float* g, float* gf, float* gg, cudaStream_t st) {
   RcmNdPlan P;
-  hd_status s = rcm_nd_plan(c, d, L, nullptr, &P, st);
+  hd_status s = rcm_nd_plan(c, d, L, nullptr, &P, st, true);
   if (s != HD_OK) return s;
   const int64_t spec = batch * P.M0 * P.M1 * P.Lp;
   const int64_t mid = d == 3 ? batch * P.M0 * L[1] * P.Lp : 0;
@@ -331,14 +331,22 @@ hd_status adjoint_rcm_nd(hd_ctx* c, int d, const int64_t* L, int64_t batch, cons
   if (!both) SF = SG;
   if (s != HD_OK) return s;
   const RowGeom rg = rcm_row_geom(d, batch, P);
+  const int outs = both ? 3 : 1;
+  if (P.row.q == 2 && rows_cl_length(P.row.m)) {
+    hd_status terr = HD_OK;
+    const float2* tab = c->tables.get_pass_table(P.row.m, st, &terr);
+    if (!tab) return terr;
+    HD_TRY(launch_rows_adj_cl(P.row.m, (unsigned)rg.nrows, st, SF, SG, SU, rg, 1.0f / (float)(P.row.q * P.row.m),
+                              outs, P.row.tw, tab));
+  } else {
   const int narr = P.row.q <= 2 ? 6 : 12;  // {U, F, G} x {row, partner} x residues
   const Eng reng = pick_eng(false, struct_length(P.row.m) && P.row.q <= 2);
   const size_t smem = sizeof(float2) * ((size_t)acc_slots(4 * (int)P.Lp) + narr * (size_t)P.row.m);
   if (smem > (size_t)c->max_smem || narr * (int64_t)P.row.m > max_points(reng)) return HD_EUNSUPPORTED;
   const int T = eng_threads(reng, narr * (int64_t)P.row.m);
-  const int outs = both ? 3 : 1;
   HD_TRY(launch_rows_adj(reng, (unsigned)rg.nrows, T, smem, st, SF, SG, SU, rg, 1.0f / (float)(P.row.q * P.row.m),
                          outs, P.row.tw, P.row.pl));
+  }
   if (gf) s = rcm_nd_backward(c, d, L, batch, P, SG, TM, gf, OUT_UNPACK_REAL_REV, st, false);
   if (s == HD_OK && gg) s = rcm_nd_backward(c, d, L, batch, P, both ? SF : SG, TM, gg, OUT_UNPACK_REAL_REV, st, false);
   return s;

@@ -1,5 +1,6 @@
 // hd_nd_rowscl.cu -- instances of the row-pair kernel of hybridRCM in 2D/3D on
-// the compile-time DFT engine (hd_rows_cl.cuh), residue lengths 256 R3.
+// the compile-time DFT engine (hd_rows_cl.cuh), residue lengths 256 R3, and
+// of the adjoint's row pass.
 #include "hd_rows_cl.cuh"
 
 namespace hd {
@@ -20,6 +21,20 @@ cudaError_t launch_rows_cl(int m, unsigned grid, cudaStream_t st, float2* F, con
     case 5: return rows::launch_rows<5>(grid, st, F, G, rg, scale, tw, tab);
     case 6: return rows::launch_rows<6>(grid, st, F, G, rg, scale, tw, tab);
     case 8: return rows::launch_rows<8>(grid, st, F, G, rg, scale, tw, tab);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rows_adj_cl(int m, unsigned grid, cudaStream_t st, float2* F, float2* G, const float2* U,
+                               RowGeom rg, float scale, int outs, const float2* tw, const float2* tab) {
+  switch (m / 256) {
+    case 1: return rows::launch_rows_adj<1>(grid, st, F, G, U, rg, scale, outs, tw, tab);
+    case 2: return rows::launch_rows_adj<2>(grid, st, F, G, U, rg, scale, outs, tw, tab);
+    case 3: return rows::launch_rows_adj<3>(grid, st, F, G, U, rg, scale, outs, tw, tab);
+    case 4: return rows::launch_rows_adj<4>(grid, st, F, G, U, rg, scale, outs, tw, tab);
+    case 5: return rows::launch_rows_adj<5>(grid, st, F, G, U, rg, scale, outs, tw, tab);
+    case 6: return rows::launch_rows_adj<6>(grid, st, F, G, U, rg, scale, outs, tw, tab);
+    case 8: return rows::launch_rows_adj<8>(grid, st, F, G, U, rg, scale, outs, tw, tab);
   }
   return cudaErrorInvalidValue;
 }

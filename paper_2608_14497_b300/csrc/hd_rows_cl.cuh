@@ -185,6 +185,168 @@ __global__ void __launch_bounds__(RowShape<R3>::T, RowShape<R3>::MINB)
   S::store_row(F + (int64_t)prow * Lp, Lp, arr + 2 * M, tw, scale, tid);
 }
 
+// ---------------------------------------------------------------------------
+// The adjoint's row pass: C_1 applied to (U, G) and (U, F) for the row pair,
+// with U = rev(grad_h)'s outer spectra transformed once and only read; the
+// products replace G's and F's rows (outs bit 0: G, bit 1: F).  Arrays: for
+// a row pair [U row, U partner, F row, F partner, G row, G partner] x {r0, r1};
+// for a row that is its own partner [U, F, G] x {r0, r1}.
+// ---------------------------------------------------------------------------
+// B_k <- U_k B_k - alpha, B_k* <- U_k* B_k* - conj(alpha),
+// alpha = (U_k - conj U_k*)(B_k - conj B_k*) Z.
+__host__ __device__ __forceinline__ void dual_pair(float2 Uk, float2 Uc, float2& Bk, float2& Bc, float2 Z, bool self) {
+  const float2 alpha = cmul(cmul(csub(Uk, cconj(Uc)), csub(Bk, cconj(Bc))), Z);
+  const float2 h1 = csub(cmul(Uk, Bk), alpha);
+  if (!self) Bc = csub(cmul(Uc, Bc), cconj(alpha));
+  Bk = h1;
+}
+
+template <int R3>
+struct RowAdjSteps {
+  using K = cl::Steps<1, R3>;
+  static constexpr int M = K::M;
+  static constexpr int T = K::T;
+
+  // arrays: U r0/r1 at u0, u0 + M; partner values at up0 (residue 0 at up0,
+  // residue 1 at up0 + M); B arrays likewise at b0 / bp0.  `cross` marks a
+  // row pair (partner arrays distinct); otherwise the row pairs with itself.
+  static __device__ __forceinline__ void product(float2* arr, int u0, int up0, int nb, const int* b0, const int* bp0,
+                                                 bool cross, const float2* __restrict__ zt, float2 z1, int tid) {
+    // residue 0: l pairs with (M - l) mod M
+    for (int p = tid; p < M; p += T) {
+      const int l = cl::digit_freq(p, R3);
+      const int ls = (l == 0) ? 0 : M - l;
+      if (!cross && l > ls) continue;
+      const bool self = !cross && ls == l;
+      const int ps = cl::digit_pos(ls, R3);
+      const float2 Uk = arr[u0 + phys(p)], Uc = arr[up0 + phys(ps)];
+      const float2 Z = K::rcm_factor(cl::ldg2(zt + p), make_float2(1.f, 0.f));
+      for (int i = 0; i < nb; ++i) {
+        float2 Bk = arr[b0[i] + phys(p)], Bc = arr[bp0[i] + phys(ps)];
+        dual_pair(Uk, Uc, Bk, Bc, Z, self);
+        arr[b0[i] + phys(p)] = Bk;
+        if (!self) arr[bp0[i] + phys(ps)] = Bc;
+      }
+    }
+    // residue 1: position p pairs with M - 1 - p (pairs of positions per task)
+    const int NT = cross ? M / 2 : M / 4;
+    for (int k = tid; k < NT; k += T) {
+      const int p = 2 * k, pp = M - 2 - p;
+      float2 U0, U1, C0, C1;
+      cl::lds4(arr + u0 + M + phys(p), U0, U1);
+      cl::lds4(arr + up0 + M + phys(pp), C1, C0);
+      const float4 z = cl::ldg4(zt + p);
+      const float2 Z0 = K::rcm_factor(make_float2(z.x, z.y), z1), Z1 = K::rcm_factor(make_float2(z.z, z.w), z1);
+      for (int i = 0; i < nb; ++i) {
+        float2 B0, B1, D0, D1;
+        cl::lds4(arr + b0[i] + M + phys(p), B0, B1);
+        cl::lds4(arr + bp0[i] + M + phys(pp), D1, D0);
+        dual_pair(U0, C0, B0, D0, Z0, false);
+        dual_pair(U1, C1, B1, D1, Z1, false);
+        cl::sts4(arr + b0[i] + M + phys(p), B0, B1);
+        cl::sts4(arr + bp0[i] + M + phys(pp), D1, D0);
+      }
+    }
+  }
+};
+
+template <int R3>
+struct RowAdjShape {
+  static constexpr size_t SMEM = sizeof(float2) * (12 * (size_t)(256 * R3) + cl::Shape<R3>::TABS);
+  static constexpr int MINB = R3 == 1 ? 8 : R3 == 2 ? 4 : R3 <= 4 ? 2 : 1;
+};
+
+template <int R3>
+__global__ void __launch_bounds__(RowShape<R3>::T, RowAdjShape<R3>::MINB)
+    k_rows_adj_cl(float2* F, float2* G, const float2* __restrict__ U, RowGeom rg, float scale, int outs,
+                  const float2* __restrict__ tw, const float2* __restrict__ tab) {
+  using S = RowSteps<R3>;
+  using A = RowAdjSteps<R3>;
+  using K = typename S::K;
+  constexpr int M = S::M, T = S::T;
+  const int row = blockIdx.x;
+  const int prow = row_partner(row, rg);
+  if (prow < row) return;
+  extern __shared__ float4 smem_raw[];
+  float2* arr = reinterpret_cast<float2*>(smem_raw);
+  float2* tws = arr + 12 * M;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < cl::Shape<R3>::TABS / 2; i += T) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(tws + 2 * i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(tab + 2 * i) : "memory");
+  }
+  const int Lp = rg.Lrow;
+  const float2* zt = tab + cl::Shape<R3>::TABZ;
+  const float2 z1 = cl::ldg2(tw + 1);
+  if (prow == row) {  // [U, F, G] x {r0, r1}
+    S::load_row(U + (int64_t)row * Lp, Lp, arr, tw, tid);
+    S::load_row(F + (int64_t)row * Lp, Lp, arr + 2 * M, tw, tid);
+    S::load_row(G + (int64_t)row * Lp, Lp, arr + 4 * M, tw, tid);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    K::template pass1<1, 6, 2>(arr, tid, tws);
+    __syncthreads();
+    K::template pass2<1, 6, 2>(arr, tid, tws);
+    __syncthreads();
+    K::template pass3<1, 6>(arr, tid);
+    __syncthreads();
+    const int b0[2] = {2 * M, 4 * M};
+    A::product(arr, 0, 0, 2, b0, b0, false, zt, z1, tid);
+    __syncthreads();
+    K::template pass3<-1, 4>(arr + 2 * M, tid);
+    __syncthreads();
+    K::template pass2<-1, 4, 1>(arr + 2 * M, tid, tws);
+    __syncthreads();
+    K::template pass1<-1, 4, 1>(arr + 2 * M, tid, tws);
+    __syncthreads();
+    if (outs & 1) S::store_row(G + (int64_t)row * Lp, Lp, arr + 4 * M, tw, scale, tid);
+    if (outs & 2) S::store_row(F + (int64_t)row * Lp, Lp, arr + 2 * M, tw, scale, tid);
+    return;
+  }
+  // [U row, U partner, F row, F partner, G row, G partner] x {r0, r1}
+  S::load_row(U + (int64_t)row * Lp, Lp, arr, tw, tid);
+  S::load_row(U + (int64_t)prow * Lp, Lp, arr + 2 * M, tw, tid);
+  S::load_row(F + (int64_t)row * Lp, Lp, arr + 4 * M, tw, tid);
+  S::load_row(F + (int64_t)prow * Lp, Lp, arr + 6 * M, tw, tid);
+  S::load_row(G + (int64_t)row * Lp, Lp, arr + 8 * M, tw, tid);
+  S::load_row(G + (int64_t)prow * Lp, Lp, arr + 10 * M, tw, tid);
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  K::template pass1<1, 12, 2>(arr, tid, tws);
+  __syncthreads();
+  K::template pass2<1, 12, 2>(arr, tid, tws);
+  __syncthreads();
+  K::template pass3<1, 12>(arr, tid);
+  __syncthreads();
+  const int b0[2] = {4 * M, 8 * M}, bp0[2] = {6 * M, 10 * M};
+  A::product(arr, 0, 2 * M, 2, b0, bp0, true, zt, z1, tid);
+  __syncthreads();
+  K::template pass3<-1, 8>(arr + 4 * M, tid);
+  __syncthreads();
+  K::template pass2<-1, 8, 1>(arr + 4 * M, tid, tws);
+  __syncthreads();
+  K::template pass1<-1, 8, 1>(arr + 4 * M, tid, tws);
+  __syncthreads();
+  if (outs & 1) {
+    S::store_row(G + (int64_t)row * Lp, Lp, arr + 8 * M, tw, scale, tid);
+    S::store_row(G + (int64_t)prow * Lp, Lp, arr + 10 * M, tw, scale, tid);
+  }
+  if (outs & 2) {
+    S::store_row(F + (int64_t)row * Lp, Lp, arr + 4 * M, tw, scale, tid);
+    S::store_row(F + (int64_t)prow * Lp, Lp, arr + 6 * M, tw, scale, tid);
+  }
+}
+
+template <int R3>
+cudaError_t launch_rows_adj(unsigned grid, cudaStream_t st, float2* F, float2* G, const float2* U, RowGeom rg,
+                            float scale, int outs, const float2* tw, const float2* tab) {
+  auto k = k_rows_adj_cl<R3>;
+  cudaError_t e = smem_optin((const void*)k, RowAdjShape<R3>::SMEM);
+  if (e != cudaSuccess) return e;
+  k<<<grid, RowShape<R3>::T, RowAdjShape<R3>::SMEM, st>>>(F, G, U, rg, scale, outs, tw, tab);
+  return cudaGetLastError();
+}
+
 template <int R3>
 cudaError_t launch_rows(unsigned grid, cudaStream_t st, float2* F, const float2* G, RowGeom rg, float scale,
                         const float2* tw, const float2* tab) {
