@@ -17,7 +17,11 @@
  *                    pointwise product, inverse, crop (the standard method).
  *   HD_EXPLICIT_RCM  explicit padding with implicit packing: pack, complex DFT
  *                    of half length, the RCM operator (Eq. RCM, Alg. 4),
- *                    inverse, unpack (Algs. 3 and 5).
+ *                    inverse, unpack (Algs. 3 and 5).  In 1D (single calls
+ *                    up to L = 73728, batches) it runs on the same cluster
+ *                    kernel as hybridRCM, reading zero-padded copies of f and
+ *                    g (real length 2L, materialised in scratch) block by
+ *                    block with no block skipped.
  *   HD_HYBRID_CS     hybrid dealiasing with conjugate symmetries (Sec. 3).
  *   HD_HYBRID_RCM    hybrid dealiasing with implicit packing (Sec. 4).
  *
@@ -111,7 +115,11 @@ hd_status hd_conv_batch(hd_ctx* ctx, hd_algo algo, hd_prec prec, int ndim, const
  * f, g and h (items must not overlap).  The planner picks (m, q) per length
  * and uploads the item table; hd_conv1d_batched then enqueues a fixed set of
  * launches with no allocation and no host-to-device copy, so it can be
- * captured in a CUDA graph.  The plan must outlive every launch that uses it. */
+ * captured in a CUDA graph.  The plan must outlive every launch that uses it.
+ * algo: HD_HYBRID_RCM, HD_HYBRID_CS, or HD_EXPLICIT_RCM (the explicit-padding
+ * baseline: the plan holds zero-padded copies of the items, 16 bytes per
+ * real input element, written by each call; lengths up to 73728, else
+ * HD_EUNSUPPORTED). */
 hd_status hd_batch_plan_create(hd_ctx* ctx, hd_algo algo, int32_t n, const int64_t* offsets, const int32_t* L,
                                hd_batch_plan** plan);
 hd_status hd_batch_plan_destroy(hd_batch_plan* plan);

@@ -291,7 +291,8 @@ def hd_conv_fn(f, g, algo="hybridRCM"):
 
 
 class BatchPlan:
-    """Host-built plan of many 1D convolutions of uneven lengths on flat arrays."""
+    """Host-built plan of many 1D convolutions of uneven lengths on flat arrays
+    (algo: hybridRCM, hybridCS, or explicitRCM, the explicit-padding baseline)."""
 
     def __init__(self, offsets, lengths, algo="hybridRCM", device=None):
         self.ctx = context(device)

@@ -134,6 +134,37 @@ static hd_status conv1d_rcm_cluster(hd_ctx* c, const float* f, const float* g, f
   return HD_OK;
 }
 
+// The explicit-padding baseline on the same kernel: zero-padded copies of f
+// and g (real length 2L per item, in scratch), every block read, the full
+// q-point sums; `batch` items of length L back to back.
+static hd_status conv1d_explicit_cluster(hd_ctx* c, const float* f, const float* g, float* h, int64_t L, int C, int m,
+                                         int p, cudaStream_t st, int64_t batch = 1) {
+  hd_status terr = HD_OK;
+  const float2* tw = c->tables.get((int64_t)2 * C * m, st, &terr);
+  if (!tw) return fail(terr, "twiddle table allocation failed");
+  const float2* tabm = c->tables.get_pass_table(m, st, &terr);
+  if (!tabm) return fail(terr, "pass table allocation failed");
+  if (ensure_ws(c, sizeof(float) * 4 * (size_t)L * (size_t)batch, st) != HD_OK)
+    return fail(HD_ENOMEM, "workspace allocation failed");
+  float* pf = reinterpret_cast<float*>(c->ws);
+  float* pg = pf + 2 * L * batch;
+  cudaError_t e = launch_pad_one(L, batch, f, g, pf, pg, st);
+  if (e != cudaSuccess) return cuda_fail(e, "padding launch");
+  ClusterLaunch cl;
+  std::memset(&cl, 0, sizeof(cl));
+  cl.err = c->dev_err;
+  cl.one_item.L = (int32_t)L;
+  cl.one_item.m = m;
+  cl.one_item.p = p;
+  cl.one_item.C = C;
+  cl.one_item.tw = tw;
+  cl.one_item.tabm = tabm;
+  cl.stride = L;
+  e = launch_rcm1d_cluster(cl, C, m, (int)batch, pf, pg, h, st, true);
+  if (e != cudaSuccess) return cuda_fail(e, "cluster launch");
+  return HD_OK;
+}
+
 static hd_status conv1d_hybrid(hd_ctx* c, hd_algo algo, const float* f, const float* g, float* h, int64_t L,
                                const hd_dim_params* prm, cudaStream_t st) {
   if (algo == HD_HYBRID_RCM && !(prm && prm->m > 0)) {
@@ -262,8 +293,12 @@ hd_status hd_conv1d(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, const
   switch (algo) {
     case HD_HYBRID_RCM:
     case HD_HYBRID_CS: return conv1d_hybrid(c, algo, f, g, h, L, prm, st);
-    case HD_EXPLICIT:
-    case HD_EXPLICIT_RCM: return explicit_nd(c, algo, 1, &L, f, g, h, st);
+    case HD_EXPLICIT_RCM: {
+      int C, m, p;
+      if (cluster_params(L, &C, &m, &p) && C <= 8) return conv1d_explicit_cluster(c, f, g, h, L, C, m, p, st);
+      return explicit_nd(c, algo, 1, &L, f, g, h, st);
+    }
+    case HD_EXPLICIT: return explicit_nd(c, algo, 1, &L, f, g, h, st);
   }
   return fail(HD_EINVAL, "unknown algorithm");
 }
@@ -281,7 +316,13 @@ hd_status hd_conv_batch(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const i
   if (prec == HD_FP32 && algo == HD_HYBRID_RCM) {
     if (ndim >= 2) return conv_nd_batch_rcm(c, ndim, Ls, batch, f, g, h, st);
     int C, m, p;
-    if (batch < (1 << 24) && cluster_params(Ls[0], &C, &m, &p)) return conv1d_rcm_cluster(c, f, g, h, Ls[0], C, m, p, st, batch);
+    if (batch < (1 << 24) && cluster_params(Ls[0], &C, &m, &p))
+      return conv1d_rcm_cluster(c, f, g, h, Ls[0], C, m, p, st, batch);
+  }
+  if (prec == HD_FP32 && algo == HD_EXPLICIT_RCM && ndim == 1) {
+    int C, m, p;
+    if (batch < (1 << 24) && cluster_params(Ls[0], &C, &m, &p) && C <= 8)
+      return conv1d_explicit_cluster(c, f, g, h, Ls[0], C, m, p, st, batch);
   }
   // every other case: one call per item
   for (int32_t b = 0; b < batch; ++b) {

@@ -52,11 +52,17 @@ struct hd_batch_plan {
   int64_t total_len = 0;
   // cluster path (hybridRCM): one class per cluster size, concurrent streams
   hd::CItem* d_citems = nullptr;
+  int64_t d_citems_count = 0;
   std::vector<hd::ClusterClass> cclasses;
   int nstreams = 0;
   cudaStream_t side[hd::kMaxClusterStreams] = {};
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[hd::kMaxClusterStreams] = {};
+  // explicit-padding baseline: zero-padded copies of f and g (item i at 2 off_i)
+  bool exp = false;
+  float* d_pad = nullptr;
+  int64_t pad_floats = 0;  // per array
+  int Lmax = 0;
 };
 
 using namespace hd;
@@ -64,7 +70,8 @@ using namespace hd;
 extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, const int64_t* offsets,
                                           const int32_t* Ls, hd_batch_plan** out) {
   if (!c || !offsets || !Ls || !out || n < 1) return HD_EINVAL;
-  if (algo != HD_HYBRID_RCM && algo != HD_HYBRID_CS) return HD_EUNSUPPORTED;
+  if (algo != HD_HYBRID_RCM && algo != HD_HYBRID_CS && algo != HD_EXPLICIT_RCM) return HD_EUNSUPPORTED;
+  const bool exp = (algo == HD_EXPLICIT_RCM);
   cudaSetDevice(c->device);
   struct HostItem {
     Item1D it;
@@ -89,22 +96,27 @@ extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, co
   // hybridRCM: every length the cluster kernel covers goes there
   std::vector<CItem> citems;
   std::vector<char> in_cluster(n, 0);
-  if (algo == HD_HYBRID_RCM) {
-    // autotune the cluster kernel once per context (HD_AUTOTUNE=0 disables it)
+  if (algo == HD_HYBRID_RCM || exp) {
+    // autotune the cluster kernel once per context (HD_AUTOTUNE=0 disables
+    // it); the explicit-padding baseline takes the rule (no C = 16 instances)
     const char* at = getenv("HD_AUTOTUNE");
-    if (!c->tuning.valid && !(at && at[0] == '0')) {
+    if (!exp && !c->tuning.valid && !(at && at[0] == '0')) {
       hd_status ts = cluster_autotune(c, &c->tuning);
       if (ts != HD_OK) c->tuning.valid = false;
     }
     for (int i = 0; i < n; ++i) {
       int C, m, p;
-      if (!cluster_params(Ls[i], &C, &m, &p, &c->tuning)) continue;
+      if (!cluster_params(Ls[i], &C, &m, &p, exp ? nullptr : &c->tuning) || (exp && C > 8)) {
+        if (exp) return HD_EUNSUPPORTED;  // the explicit baseline covers L <= 73728
+        continue;
+      }
       hd_status terr = HD_OK;
       const float2* tw = c->tables.get((int64_t)2 * C * m, 0, &terr);
       if (!tw) return terr;
       CItem ci;
       std::memset(&ci, 0, sizeof(ci));
       ci.off = offsets[i];
+      ci.off_in = 2 * offsets[i];
       ci.L = Ls[i];
       ci.m = m;
       ci.p = p;
@@ -147,6 +159,7 @@ extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, co
   std::stable_sort(hs.begin(), hs.end(), [](const HostItem& a, const HostItem& b) { return a.it.L > b.it.L; });
   hd_batch_plan* bp = new hd_batch_plan();
   bp->algo = algo;
+  bp->exp = exp;
   bp->n = n;
   bp->device = c->device;
   if (acc_total > 0 && cudaMalloc(&bp->d_acc, acc_total) != cudaSuccess) {
@@ -191,11 +204,24 @@ extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, co
       bp->total_len += citems[i].L;
     }
     bp->nstreams = bp->cclasses.back().stream + 1;
+    if (exp) {
+      int64_t extent = 0;
+      for (const CItem& ci : citems) {
+        extent = std::max<int64_t>(extent, ci.off + ci.L);
+        bp->Lmax = std::max(bp->Lmax, ci.L);
+      }
+      bp->pad_floats = 2 * extent;
+      if (cudaMalloc(&bp->d_pad, sizeof(float) * 2 * (size_t)bp->pad_floats) != cudaSuccess) {
+        hd_batch_plan_destroy(bp);
+        return HD_ENOMEM;
+      }
+    }
     if (cudaMalloc(&bp->d_citems, sizeof(CItem) * citems.size()) != cudaSuccess) {
       hd_batch_plan_destroy(bp);
       return HD_ENOMEM;
     }
     cudaMemcpy(bp->d_citems, citems.data(), sizeof(CItem) * citems.size(), cudaMemcpyHostToDevice);
+    bp->d_citems_count = (int64_t)citems.size();
     if (bp->nstreams > 1) {
       int lo = 0, hi = 0;
       cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -233,6 +259,7 @@ extern "C" hd_status hd_batch_plan_destroy(hd_batch_plan* bp) {
   if (bp->d_plans) cudaFree(bp->d_plans);
   if (bp->d_acc) cudaFree(bp->d_acc);
   if (bp->d_citems) cudaFree(bp->d_citems);
+  if (bp->d_pad) cudaFree(bp->d_pad);
   for (int k = 0; k < kMaxClusterStreams; ++k) {
     if (bp->side[k]) cudaStreamDestroy(bp->side[k]);
     if (bp->join[k]) cudaEventDestroy(bp->join[k]);
@@ -248,6 +275,15 @@ extern "C" hd_status hd_conv1d_batched(hd_ctx* c, const hd_batch_plan* bp, const
   cudaSetDevice(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   const int ncc = (int)bp->cclasses.size();
+  if (bp->exp) {
+    // explicit padding materialised in memory first
+    float* pf = bp->d_pad;
+    float* pg = bp->d_pad + bp->pad_floats;
+    if (launch_pad_items(bp->d_citems, (int)bp->d_citems_count, bp->Lmax, f, g, pf, pg, st) != cudaSuccess)
+      return HD_ECUDA;
+    f = pf;
+    g = pg;
+  }
   if (bp->nstreams == 1) {
     for (int i = 0; i < ncc; ++i) {
       const ClusterClass& k = bp->cclasses[i];
@@ -255,7 +291,7 @@ extern "C" hd_status hd_conv1d_batched(hd_ctx* c, const hd_batch_plan* bp, const
       std::memset(&cl, 0, sizeof(cl));
       cl.items = bp->d_citems + k.first;
       cl.err = c->dev_err;
-      if (launch_rcm1d_cluster(cl, k.C, k.m, k.count, f, g, h, st) != cudaSuccess) return HD_ECUDA;
+      if (launch_rcm1d_cluster(cl, k.C, k.m, k.count, f, g, h, st, bp->exp) != cudaSuccess) return HD_ECUDA;
     }
   } else if (bp->nstreams > 1) {
     // fork: every cluster size on its own stream after the work already on
@@ -269,7 +305,7 @@ extern "C" hd_status hd_conv1d_batched(hd_ctx* c, const hd_batch_plan* bp, const
       std::memset(&cl, 0, sizeof(cl));
       cl.items = bp->d_citems + k.first;
       cl.err = c->dev_err;
-      if (launch_rcm1d_cluster(cl, k.C, k.m, k.count, f, g, h, bp->side[k.stream]) != cudaSuccess) return HD_ECUDA;
+      if (launch_rcm1d_cluster(cl, k.C, k.m, k.count, f, g, h, bp->side[k.stream], bp->exp) != cudaSuccess) return HD_ECUDA;
     }
     for (int s2 = 0; s2 < bp->nstreams; ++s2)
       if (cudaEventRecord(bp->join[s2], bp->side[s2]) != cudaSuccess ||

@@ -249,6 +249,8 @@ struct CtaState {
   float* h;
   int64_t off;
   int L, Lp, p, c;        // real length, packed length, blocks, rank in the cluster
+  int64_t off_in;         // offset of the item in the input arrays
+  int Lin, pin;           // real length of the input arrays' item and the blocks read
   bool in16, in8, out16;  // f + off and g + off 16- / 8-byte aligned; h + off 16-byte aligned
   const float2* tw;       // zeta_N^k, N = 2 C M
   const float2* tab;      // per-length table (Shape::TAB1 | TAB2 | product)
@@ -261,7 +263,11 @@ struct CtaState {
 // ---------------------------------------------------------------------------
 // the kernel's steps
 // ---------------------------------------------------------------------------
-template <int C, int R3>
+// EXP: the explicit-padding baseline on the same engine: the input arrays are
+// materialised zero-padded copies (real length 2L), every block t < q of them
+// is read (no block is known to be zero) and the q-point sum over t is the
+// full DFT, x_t and x_{t+C} combined before the two length-C DFTs.
+template <int C, int R3, bool EXP = false>
 struct Steps {
   using S = Shape<R3>;
   static constexpr int M = S::M;
@@ -273,19 +279,20 @@ struct Steps {
   static constexpr int SW3 = (SL >= 2 * T) ? 2 : 1; // s per phase-3 task
   static constexpr int NT3 = SL / SW3;
   static constexpr int U1 = (NT1 + T - 1) / T;      // phase-1 tasks per thread
+  static constexpr int NB = EXP ? 2 * C : C;        // blocks t read per s
 
   // ---- phase 1 ------------------------------------------------------------
   // Packed inputs x~_j, j = t M + s + w (w < 2), of array `which`; zero past Lp.
-  static __host__ __device__ __forceinline__ void load_task(const CtaState& x, int task, float2 (&v)[C][2]) {
+  static __host__ __device__ __forceinline__ void load_task(const CtaState& x, int task, float2 (&v)[NB][2]) {
     const int which = task / (SL / SW1);
     const int s = x.c * SL + (task - which * (SL / SW1)) * SW1;
-    const float* src = (which ? x.g : x.f) + x.off;
+    const float* src = (which ? x.g : x.f) + x.off_in;
 #pragma unroll
-    for (int t = 0; t < C; ++t) {
+    for (int t = 0; t < NB; ++t) {
       const int j = t * M + s;
       v[t][0] = v[t][1] = make_float2(0.f, 0.f);
-      if (t < x.p && SW1 == 1) {
-        const int rem = x.L - 2 * j;
+      if (t < x.pin && SW1 == 1) {
+        const int rem = x.Lin - 2 * j;
         if (rem >= 2 && x.in8) {
 #ifdef __CUDA_ARCH__
           v[t][0] = __ldg(reinterpret_cast<const float2*>(src + 2 * j));
@@ -296,8 +303,8 @@ struct Steps {
           if (rem > 0) v[t][0].x = ldgf(src + 2 * j);
           if (rem > 1) v[t][0].y = ldgf(src + 2 * j + 1);
         }
-      } else if (t < x.p) {
-        const int rem = x.L - 2 * j;  // real values left from 2j
+      } else if (t < x.pin) {
+        const int rem = x.Lin - 2 * j;  // real values left from 2j
         if (rem >= 4 && x.in16) {
 #ifdef __CUDA_ARCH__
           const float4 a = __ldg(reinterpret_cast<const float4*>(src + 2 * j));
@@ -327,17 +334,24 @@ struct Steps {
   }
 
   // Sum over t for every residue, pre-twiddle, store into the owners' arrays.
-  static __host__ __device__ __forceinline__ void scatter_task(const CtaState& x, int task, const float2 (&v)[C][2]) {
+  // The sum over t: e_t = x_t (+ x_{t+C}), o_t = zeta_q^t (x_t (- x_{t+C})).
+  static __host__ __device__ __forceinline__ void split_blocks(const float2 (&v)[NB][2], int w, float2* e, float2* o) {
+#pragma unroll
+    for (int t = 0; t < C; ++t) {
+      const float2 a = EXP ? cadd(v[t][w], v[t + (EXP ? C : 0)][w]) : v[t][w];
+      const float2 b = EXP ? csub(v[t][w], v[t + (EXP ? C : 0)][w]) : v[t][w];
+      e[t] = a;
+      o[t] = (t == 0) ? b : cmul(b, root32<1>(t * (16 / C)));  // zeta_q^t
+    }
+  }
+
+  static __host__ __device__ __forceinline__ void scatter_task(const CtaState& x, int task, const float2 (&v)[NB][2]) {
     const int which = task / (SL / SW1);
     const int s = x.c * SL + (task - which * (SL / SW1)) * SW1;
     if constexpr (SW1 == 1) {
       // one s, every residue stored as soon as it is formed
       float2 e[C], o[C];
-#pragma unroll
-      for (int t = 0; t < C; ++t) {
-        e[t] = v[t][0];
-        o[t] = (t == 0) ? v[t][0] : cmul(v[t][0], root32<1>(t * (16 / C)));
-      }
+      split_blocks(v, 0, e, o);
       dft_small<1, C>(e);
       dft_small<1, C>(o);
       const TwBases tb = twiddle_bases(x.tw, s);
@@ -355,11 +369,7 @@ struct Steps {
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
       float2 e[C], o[C];
-#pragma unroll
-      for (int t = 0; t < C; ++t) {
-        e[t] = v[t][w];
-        o[t] = (t == 0) ? v[t][w] : cmul(v[t][w], root32<1>(t * (16 / C)));  // zeta_q^t x_t
-      }
+      split_blocks(v, w, e, o);
       dft_small<1, C>(e);
       dft_small<1, C>(o);
       float2 wr[Q];

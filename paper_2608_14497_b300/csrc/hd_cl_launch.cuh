@@ -64,10 +64,12 @@ __device__ __forceinline__ void mbar_wait(unsigned bar, int* err) {
 // is running and its mbarriers are initialised before any remote store) and
 // once after the product (every CTA's G arrays, the gather buffers, are free).
 // A single CTA (C = 1) works in its own shared memory only.
-template <int C, int R3>
+// EXP: the explicit-padding baseline (f and g are zero-padded copies, item at
+// off_in, real length 2L).
+template <int C, int R3, bool EXP>
 __global__ void __launch_bounds__(Shape<R3>::T, Shape<R3>::MINB)
     k_rcm_cl(ClusterLaunch la, const float* f, const float* g, float* h) {
-  using K = Steps<C, R3>;
+  using K = Steps<C, R3, EXP>;
   constexpr int T = K::T;
   constexpr int M = K::M;
   extern __shared__ float4 smem_raw[];
@@ -88,7 +90,10 @@ __global__ void __launch_bounds__(Shape<R3>::T, Shape<R3>::MINB)
   // before the first remote store: arrive now, wait after the first loads
   if constexpr (C > 1) arrive_relaxed();
   CItem it = la.items ? la.items[blockIdx.x / C] : la.one_item;
-  if (!la.items) it.off += (int64_t)(blockIdx.x / C) * la.stride;
+  if (!la.items) {
+    it.off += (int64_t)(blockIdx.x / C) * la.stride;
+    it.off_in += (int64_t)(blockIdx.x / C) * (EXP ? 2 * la.stride : la.stride);
+  }
   // copy the pass twiddles to shared memory while phase 1 runs; 16-byte chunks
   for (int i = tid; i < Shape<R3>::TABS / 2; i += T) {
     const unsigned dst = (unsigned)__cvta_generic_to_shared(tws + 2 * i);
@@ -106,8 +111,11 @@ __global__ void __launch_bounds__(Shape<R3>::T, Shape<R3>::MINB)
   x.tw = it.tw;
   x.tab = it.tabm;
   x.arr = arr;
+  x.off_in = EXP ? it.off_in : it.off;
+  x.Lin = EXP ? 2 * it.L : it.L;
+  x.pin = EXP ? (it.L + M - 1) / M : it.p;
   {
-    const uintptr_t fa = (uintptr_t)(f + it.off), ga = (uintptr_t)(g + it.off), ha = (uintptr_t)(h + it.off);
+    const uintptr_t fa = (uintptr_t)(f + x.off_in), ga = (uintptr_t)(g + x.off_in), ha = (uintptr_t)(h + it.off);
     x.in16 = ((fa | ga) & 15) == 0;
     x.in8 = ((fa | ga) & 7) == 0;
     x.out16 = (ha & 15) == 0;
@@ -124,7 +132,7 @@ __global__ void __launch_bounds__(Shape<R3>::T, Shape<R3>::MINB)
   // ---- phase 1 (Eq. forwardr, inner sum), pushed to the owners: every
   // task's loads in flight first (8 / C tasks of C blocks x 2 values)
   {
-    float2 v[K::U1][C][2];
+    float2 v[K::U1][K::NB][2];
 #pragma unroll
     for (int u = 0; u < K::U1; ++u)
       if (K::NT1 % T == 0 || tid + u * T < K::NT1) K::load_task(x, tid + u * T, v[u]);
@@ -168,9 +176,9 @@ __global__ void __launch_bounds__(Shape<R3>::T, Shape<R3>::MINB)
 // Launch over `nitems` convolutions of the same (C, R3): grid nitems x C in
 // clusters of C CTAs (the cluster size is a launch attribute; 16 is beyond the
 // portable size and is allowed per kernel).
-template <int C, int R3>
+template <int C, int R3, bool EXP = false>
 cudaError_t launch(const ClusterLaunch& la, int nitems, const float* f, const float* g, float* h, cudaStream_t st) {
-  auto kern = k_rcm_cl<C, R3>;
+  auto kern = k_rcm_cl<C, R3, EXP>;
   cudaError_t e = smem_optin((const void*)kern, Shape<R3>::SMEM);
   if (e != cudaSuccess) return e;
   if constexpr (C > 8) {

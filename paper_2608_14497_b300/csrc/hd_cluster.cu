@@ -163,9 +163,18 @@ hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out) {
 }
 
 cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int C, int m, int nitems, const float* f, const float* g,
-                                 float* h, cudaStream_t st) {
+                                 float* h, cudaStream_t st, bool exp) {
   if (!cluster_instance(C, m) || nitems < 1) return cudaErrorInvalidValue;
   const int R3 = m / 256;
+  if (exp) {
+    switch (C) {
+      case 1: return R3 <= 6 ? launch_clx_c1(R3, cl, nitems, f, g, h, st) : launch_clx_c1b(R3, cl, nitems, f, g, h, st);
+      case 2: return launch_clx_c2(R3, cl, nitems, f, g, h, st);
+      case 4: return R3 <= 9 ? launch_clx_c4(R3, cl, nitems, f, g, h, st) : launch_clx_c4b(R3, cl, nitems, f, g, h, st);
+      case 8: return R3 <= 9 ? launch_clx_c8(R3, cl, nitems, f, g, h, st) : launch_clx_c8b(R3, cl, nitems, f, g, h, st);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (C) {
     case 1: return R3 <= 6 ? launch_cl_c1(R3, cl, nitems, f, g, h, st) : launch_cl_c1b(R3, cl, nitems, f, g, h, st);
     case 2: return launch_cl_c2(R3, cl, nitems, f, g, h, st);
@@ -174,6 +183,49 @@ cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int C, int m, int nite
     case 16: return launch_cl_c16(R3, cl, nitems, f, g, h, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// Zero-padded copies for the explicit-padding baseline: item i's L values at
+// off become [values, L zeros] at off_in (grid: x over 2 Lmax, y over items).
+__global__ void k_pad_items(const CItem* __restrict__ items, const float* __restrict__ f, const float* __restrict__ g,
+                            float* __restrict__ pf, float* __restrict__ pg) {
+  const CItem it = items[blockIdx.y];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 2 * (int64_t)it.L;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const bool in = k < it.L;
+    pf[it.off_in + k] = in ? f[it.off + k] : 0.f;
+    pg[it.off_in + k] = in ? g[it.off + k] : 0.f;
+  }
+}
+
+__global__ void k_pad_one(int64_t L, int64_t total, const float* __restrict__ f, const float* __restrict__ g,
+                          float* __restrict__ pf, float* __restrict__ pg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t item = i / (2 * L), k = i - item * 2 * L;
+    const bool in = k < L;
+    pf[i] = in ? f[item * L + k] : 0.f;
+    pg[i] = in ? g[item * L + k] : 0.f;
+  }
+}
+
+cudaError_t launch_pad_items(const CItem* items, int nitems, int Lmax, const float* f, const float* g, float* pf,
+                             float* pg, cudaStream_t st) {
+  const int bx = std::max(1, std::min(64, (2 * Lmax + 1023) / 1024));
+  for (int first = 0; first < nitems; first += 65535) {
+    const int n = std::min(65535, nitems - first);
+    k_pad_items<<<dim3(bx, n), 256, 0, st>>>(items + first, f, g, pf, pg);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_pad_one(int64_t L, int64_t batch, const float* f, const float* g, float* pf, float* pg,
+                           cudaStream_t st) {
+  const int64_t total = 2 * L * batch;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
+  k_pad_one<<<blocks, 256, 0, st>>>(L, total, f, g, pf, pg);
+  return cudaGetLastError();
 }
 
 }  // namespace hd

@@ -14,6 +14,7 @@ constexpr int kClusterMaxM = 4608;  // largest residue DFT length (M = 256 R3, R
 // One convolution: q = 2C residues of length m = 256 R3, p = ceil(Lp/m) <= C.
 struct CItem {
   int64_t off;
+  int64_t off_in;  // explicit-padding baseline: offset of the item in the padded inputs
   int32_t L, m, p, C;
   const float2* tw;    // zeta_N^k, N = 2 C m
   const float2* tabm;  // per-length table of the kernel's passes and product (cl::Shape)
@@ -37,9 +38,16 @@ bool cluster_instance(int C, int m);
 bool cluster_params(int64_t L, int* C, int* m, int* p, const ClusterTuning* tun = nullptr);
 // Time every built instance on synthetic batches (device scratch, ~50 MB).
 hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out);
-// Launch over `nitems` convolutions of the same (C, m) (clusters of C CTAs).
+// Launch over `nitems` convolutions of the same (C, m) (clusters of C CTAs);
+// exp: the explicit-padding baseline (f, g zero-padded copies, C <= 8).
 cudaError_t launch_rcm1d_cluster(const ClusterLaunch& cl, int C, int m, int nitems, const float* f,
-                                 const float* g, float* h, cudaStream_t st);
+                                 const float* g, float* h, cudaStream_t st, bool exp = false);
+// Zero-padded copies of the items of f and g (item i: L_i values at off_i
+// become 2 L_i values at off_in_i).
+cudaError_t launch_pad_items(const CItem* items, int nitems, int Lmax, const float* f, const float* g, float* pf,
+                             float* pg, cudaStream_t st);
+cudaError_t launch_pad_one(int64_t L, int64_t batch, const float* f, const float* g, float* pf, float* pg,
+                           cudaStream_t st);
 // Per-cluster-size dispatch over R3 = m / 256 (hd_cl_c*.cu); cudaErrorInvalidValue
 // for an instance that is not built.
 #define HD_CL_LAUNCHER(name)                                                                                   \
@@ -53,6 +61,13 @@ HD_CL_LAUNCHER(launch_cl_c4b)
 HD_CL_LAUNCHER(launch_cl_c8)
 HD_CL_LAUNCHER(launch_cl_c8b)
 HD_CL_LAUNCHER(launch_cl_c16)
+HD_CL_LAUNCHER(launch_clx_c1)
+HD_CL_LAUNCHER(launch_clx_c1b)
+HD_CL_LAUNCHER(launch_clx_c2)
+HD_CL_LAUNCHER(launch_clx_c4)
+HD_CL_LAUNCHER(launch_clx_c4b)
+HD_CL_LAUNCHER(launch_clx_c8)
+HD_CL_LAUNCHER(launch_clx_c8b)
 #undef HD_CL_LAUNCHER
 
 }  // namespace hd

@@ -97,8 +97,8 @@ def ladder_ceil(n):
 @pytest.mark.parametrize("L", [1, 2, 3, 5, 17, 100, 127, 1000, 3001, 5000, 8192, 12345, 20000, 70000])
 def test_ragged_lengths_default_plan(hd, algo, L):
     f, g = inputs.uniform_pair(L, seed=L)
-    if algo.startswith("explicit") and ladder_ceil(L) > 16384:
-        # the explicit baselines transform the padded row in one CTA
+    if algo == "explicit" and ladder_ceil(L) > 16384:
+        # the r2c explicit baseline transforms the padded row in one CTA
         with pytest.raises(hd.HDError) as e:
             run(hd, f, g, algo)
         assert e.value.status == hd.HD_EUNSUPPORTED
@@ -175,3 +175,11 @@ def test_composite_last_pass_lengths(hd, m, delta):
     f, g = inputs.uniform_pair(L, seed=500 + m + delta)
     ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
     assert rel_l2(run(hd, f, g, "hybridRCM"), ref) <= TOL
+
+
+@pytest.mark.parametrize("L", [9000, 20001, 40000, 65536, 70000, 73728])
+def test_explicit_rcm_long_lengths(hd, L):
+    """explicitRCM beyond one CTA: zero-padded copies on the cluster kernel."""
+    f, g = inputs.normal_pair(L, seed=700 + L)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    assert rel_l2(run(hd, f, g, "explicitRCM"), ref) <= TOL

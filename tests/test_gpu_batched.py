@@ -147,3 +147,30 @@ def test_batched_graph_replay_matches_eager(hd):
     for i in range(0, len(Ls), 7):
         a, b = off[i], off[i] + Ls[i]
         assert rel_l2(hh[a:b], ref[a:b]) <= TOL, (i, Ls[i])
+
+
+def test_batched_explicit_rcm_every_item(hd):
+    """The explicit-padding baseline as a batched plan (padded copies in the plan)."""
+    rng = np.random.default_rng(46)
+    Ls = np.concatenate([[1, 2, 3, 500, 9216, 9217, 73728], rng.integers(1, 70000, 40)]).astype(np.int64)
+    off, f, g = flat(Ls, 47)
+    plan = hd.BatchPlan(off, Ls, algo="explicitRCM")
+    tf, tg = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    h = plan(tf, tg).cpu().numpy()
+    ref = oracle.batch_conv1d(f, g, off, Ls, use_fft=True)
+    for i in range(len(Ls)):
+        a, b = off[i], off[i] + Ls[i]
+        assert rel_l2(h[a:b], ref[a:b]) <= TOL, (i, Ls[i])
+    # graph replay gives the eager result
+    h2 = torch.zeros_like(tf)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        plan(tf, tg, out=h2)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            plan(tf, tg, out=h2)
+    h2.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(h2.cpu().numpy(), h)
