@@ -101,6 +101,17 @@ hd_status hd_conv2d(hd_ctx* ctx, hd_algo algo, hd_prec prec, const float* f, con
 hd_status hd_conv3d(hd_ctx* ctx, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h,
                     int64_t L1, int64_t L2, int64_t L3, const hd_dim_params* prm, void* stream);
 
+/* Convolution with output extents K[0..ndim) (Sec. 2: any padding of at least
+ * 2L-1 per dimension dealiases every output of the linear convolution, so the
+ * same transforms yield h_k for 0 <= k_i < K_i, L_i <= K_i <= 2L_i - 1; K_i =
+ * 2L_i - 1 is the full linear convolution).  h holds prod(K) floats, row-major
+ * with extents K; K == NULL means K = L (hd_conv1d/2d/3d are this call).  h
+ * may alias f or g only when K = L.  Supported: every algorithm in 1D;
+ * hybridRCM, explicit and explicitRCM in 2D/3D (hybridCS in 2D/3D:
+ * HD_EUNSUPPORTED unless K = L).  HD_EINVAL for K outside [L, 2L-1]. */
+hd_status hd_conv_ext(hd_ctx* ctx, hd_algo algo, hd_prec prec, int ndim, const int64_t* L, const int64_t* K,
+                      const float* f, const float* g, float* h, const hd_dim_params* prm, void* stream);
+
 /* `batch` independent convolutions of equal extents Ls[0..ndim) stored back to
  * back in f, g and h (item b at offset b * prod(Ls)); the same result as one
  * hd_conv1d/2d/3d call per item.  hybridRCM in FP32 runs the whole batch in

@@ -27,7 +27,7 @@ PRECS = {"fp32": HD_FP32, "split_bf16": HD_SPLIT_BF16}
 EXPORTS = ("hd_create", "hd_destroy", "hd_conv1d", "hd_conv2d", "hd_conv3d", "hd_batch_plan_create",
            "hd_batch_plan_destroy", "hd_conv1d_batched", "hd_conv_adjoint", "hd_plan", "hd_last_device_error",
            "hd_strerror", "hd_last_error_string", "hd_conv1d_rcm_noalloc",
-           "hd_tuning_table", "hd_batch_plan_launches", "hd_conv_batch")
+           "hd_tuning_table", "hd_batch_plan_launches", "hd_conv_batch", "hd_conv_ext")
 
 
 class HDError(RuntimeError):
@@ -76,6 +76,7 @@ def load(build_if_missing=False):
         "hd_tuning_table": ([P, I32, P, P, P, P], I),
         "hd_batch_plan_launches": ([P, P], I),
         "hd_conv_batch": ([P, I, I, I, P, I32, P, P, P, P], I),
+        "hd_conv_ext": ([P, I, I, I, P, P, P, P, P, DP, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -147,6 +148,13 @@ def hd_conv1d_batched(ctx, plan, f_ptr, g_ptr, h_ptr, stream=0):
     return load().hd_conv1d_batched(ctx, plan, f_ptr, g_ptr, h_ptr, stream)
 
 
+def hd_conv_ext(ctx, algo, prec, Ls, Ks, f_ptr, g_ptr, h_ptr, prm=None, stream=0):
+    n = len(Ls)
+    la = (ctypes.c_int64 * n)(*[int(x) for x in Ls])
+    ka = (ctypes.c_int64 * n)(*[int(x) for x in Ks]) if Ks is not None else None
+    return load().hd_conv_ext(ctx, algo, prec, n, la, ka, f_ptr, g_ptr, h_ptr, _params(prm, n), stream)
+
+
 def hd_conv_batch(ctx, algo, prec, Ls, batch, f_ptr, g_ptr, h_ptr, stream=0):
     arr = (ctypes.c_int64 * len(Ls))(*[int(x) for x in Ls])
     return load().hd_conv_batch(ctx, algo, prec, len(Ls), arr, batch, f_ptr, g_ptr, h_ptr, stream)
@@ -202,13 +210,25 @@ def _check_tensor(t, name):
         raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
 
 
-def conv(f, g, algo="hybridRCM", params=None, out=None, prec="fp32"):
-    """h = first L per dimension of the linear convolution of f and g (1D/2D/3D)."""
+def conv(f, g, algo="hybridRCM", params=None, out=None, prec="fp32", out_extent=None):
+    """h = the linear convolution of f and g (1D/2D/3D), the first L outputs per
+    dimension, or the first K with out_extent=K (L <= K <= 2L-1; "full" for 2L-1)."""
     import torch
     _check_tensor(f, "f")
     _check_tensor(g, "g")
     if f.shape != g.shape or f.dim() not in (1, 2, 3):
         raise ValueError("f and g must share a 1D/2D/3D shape")
+    if out_extent is not None:
+        K = tuple(2 * n - 1 for n in f.shape) if out_extent == "full" else tuple(int(k) for k in (
+            out_extent if hasattr(out_extent, "__len__") else (out_extent,)))
+        h = torch.empty(K, dtype=f.dtype, device=f.device) if out is None else out
+        _check_tensor(h, "out")
+        if tuple(h.shape) != K:
+            raise ValueError("out must have the output extents")
+        st = hd_conv_ext(context(f.device.index), ALGOS[algo], PRECS[prec], tuple(f.shape), K, f.data_ptr(),
+                         g.data_ptr(), h.data_ptr(), params, _stream_ptr())
+        _check(st, f"conv_ext[{algo}]")
+        return h
     h = torch.empty_like(f) if out is None else out
     _check_tensor(h, "out")
     ctx = context(f.device.index)

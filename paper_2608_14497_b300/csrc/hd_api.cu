@@ -43,7 +43,8 @@ static int64_t next_smooth_even(int64_t n) {
 // prefers p = 1, q = 2 (a single explicit block, residues 0 and 1, both
 // self-paired) with the smallest 2,3,5-smooth m >= Lp; when 4m exceeds what one
 // CTA transforms at once it lowers m and raises p and q.
-hd_status resolve_rcm1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D* out) {
+hd_status resolve_rcm1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D* out, int64_t K) {
+  if (K <= 0) K = L;
   const int64_t Lp = ceil_div(L, 2);
   int64_t m, q;
   const int64_t mmax = (int64_t)kPts * 1024 / 4;
@@ -67,9 +68,9 @@ hd_status resolve_rcm1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D
   out->m = (int)m;
   out->q = (int)q;
   out->p = (int)ceil_div(Lp, m);
-  out->smem = rcm1d_smem_bytes((int)L, (int)m, false);
+  out->smem = rcm1d_smem_bytes((int)K, (int)m, false);
   out->gacc = out->smem > (size_t)c->max_smem;
-  if (out->gacc) out->smem = rcm1d_smem_bytes((int)L, (int)m, true);
+  if (out->gacc) out->smem = rcm1d_smem_bytes((int)K, (int)m, true);
   if (out->smem > (size_t)c->max_smem) return fail(HD_EUNSUPPORTED, "hybridRCM: shared memory too small");
   out->threads = threads_for_points(4 * m, kPts);
   return HD_OK;
@@ -77,7 +78,8 @@ hd_status resolve_rcm1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D
 
 // hybridCS: real length L, q m >= 2L-1, m even when q is even (Sec. 3.1.3).
 // The planner prefers q = 2 and the smallest even 2,3,5-smooth m >= L.
-hd_status resolve_cs1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D* out) {
+hd_status resolve_cs1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D* out, int64_t K) {
+  if (K <= 0) K = L;
   int64_t m, q;
   const int64_t mmax = (int64_t)kPts * 1024 / 2;
   if (prm && prm->m > 0) {
@@ -102,9 +104,9 @@ hd_status resolve_cs1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D*
   out->m = (int)m;
   out->q = (int)q;
   out->p = (int)ceil_div(L, m);
-  out->smem = cs1d_smem_bytes((int)L, (int)m, false);
+  out->smem = cs1d_smem_bytes((int)K, (int)m, false);
   out->gacc = out->smem > (size_t)c->max_smem;
-  if (out->gacc) out->smem = cs1d_smem_bytes((int)L, (int)m, true);
+  if (out->gacc) out->smem = cs1d_smem_bytes((int)K, (int)m, true);
   if (out->smem > (size_t)c->max_smem) return fail(HD_EUNSUPPORTED, "hybridCS: shared memory too small");
   out->threads = threads_for_points(2 * m, kPts);
   return HD_OK;
@@ -113,7 +115,7 @@ hd_status resolve_cs1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D*
 // hybridRCM with planner parameters: the cluster kernel, one item by value,
 // repeated `batch` times at a stride of L floats.
 static hd_status conv1d_rcm_cluster(hd_ctx* c, const float* f, const float* g, float* h, int64_t L, int C, int m,
-                                    int p, cudaStream_t st, int64_t batch = 1) {
+                                    int p, cudaStream_t st, int64_t batch = 1, int64_t K = 0) {
   hd_status terr = HD_OK;
   const float2* tw = c->tables.get((int64_t)2 * C * m, st, &terr);
   if (!tw) return fail(terr, "twiddle table allocation failed");
@@ -128,7 +130,9 @@ static hd_status conv1d_rcm_cluster(hd_ctx* c, const float* f, const float* g, f
   cl.one_item.tw = tw;
   cl.one_item.tabm = c->tables.get_pass_table(m, st, &terr);
   if (!cl.one_item.tabm) return fail(terr, "pass table allocation failed");
+  cl.one_item.K = (int32_t)K;
   cl.stride = L;
+  if (K > 0 && K != L && batch > 1) return fail(HD_EINVAL, "batched calls return the first L outputs");
   cudaError_t e = launch_rcm1d_cluster(cl, C, m, (int)batch, f, g, h, st);
   if (e != cudaSuccess) return cuda_fail(e, "cluster launch");
   return HD_OK;
@@ -138,7 +142,7 @@ static hd_status conv1d_rcm_cluster(hd_ctx* c, const float* f, const float* g, f
 // and g (real length 2L per item, in scratch), every block read, the full
 // q-point sums; `batch` items of length L back to back.
 static hd_status conv1d_explicit_cluster(hd_ctx* c, const float* f, const float* g, float* h, int64_t L, int C, int m,
-                                         int p, cudaStream_t st, int64_t batch = 1) {
+                                         int p, cudaStream_t st, int64_t batch = 1, int64_t K = 0) {
   hd_status terr = HD_OK;
   const float2* tw = c->tables.get((int64_t)2 * C * m, st, &terr);
   if (!tw) return fail(terr, "twiddle table allocation failed");
@@ -159,20 +163,22 @@ static hd_status conv1d_explicit_cluster(hd_ctx* c, const float* f, const float*
   cl.one_item.C = C;
   cl.one_item.tw = tw;
   cl.one_item.tabm = tabm;
+  cl.one_item.K = (int32_t)K;
   cl.stride = L;
+  if (K > 0 && K != L && batch > 1) return fail(HD_EINVAL, "batched calls return the first L outputs");
   e = launch_rcm1d_cluster(cl, C, m, (int)batch, pf, pg, h, st, true);
   if (e != cudaSuccess) return cuda_fail(e, "cluster launch");
   return HD_OK;
 }
 
 static hd_status conv1d_hybrid(hd_ctx* c, hd_algo algo, const float* f, const float* g, float* h, int64_t L,
-                               const hd_dim_params* prm, cudaStream_t st) {
+                               const hd_dim_params* prm, cudaStream_t st, int64_t K) {
   if (algo == HD_HYBRID_RCM && !(prm && prm->m > 0)) {
     int C, m, p;
-    if (cluster_params(L, &C, &m, &p)) return conv1d_rcm_cluster(c, f, g, h, L, C, m, p, st);
+    if (cluster_params(L, &C, &m, &p)) return conv1d_rcm_cluster(c, f, g, h, L, C, m, p, st, 1, K);
   }
   Params1D P;
-  hd_status s = (algo == HD_HYBRID_RCM) ? resolve_rcm1d(c, L, prm, &P) : resolve_cs1d(c, L, prm, &P);
+  hd_status s = (algo == HD_HYBRID_RCM) ? resolve_rcm1d(c, L, prm, &P, K) : resolve_cs1d(c, L, prm, &P, K);
   if (s != HD_OK) return s;
   hd_status terr = HD_OK;
   const float2* tw = c->tables.get((int64_t)P.q * P.m, st, &terr);
@@ -186,11 +192,12 @@ static hd_status conv1d_hybrid(hd_ctx* c, hd_algo algo, const float* f, const fl
   la.one.p = P.p;
   la.one.plan = 0;
   la.one.plan_half = (P.m % 2 == 0) ? 1 : -1;
+  la.one.K = (int32_t)K;
   la.one.tw = tw;
   factor_radices(P.m, &la.plan_m);
   if (P.m % 2 == 0) factor_radices(P.m / 2, &la.plan_half);
   if (P.gacc) {
-    const size_t bytes = (algo == HD_HYBRID_RCM) ? sizeof(float2) * (size_t)ceil_div(L, 2) : sizeof(float) * (size_t)L;
+    const size_t bytes = (algo == HD_HYBRID_RCM) ? sizeof(float2) * (size_t)ceil_div(K, 2) : sizeof(float) * (size_t)K;
     if (ensure_ws(c, bytes, st) != HD_OK) return fail(HD_ENOMEM, "workspace allocation failed");
     la.one.gacc = c->ws;
   }
@@ -283,24 +290,7 @@ hd_status hd_plan(hd_ctx* c, hd_algo algo, int64_t L, hd_dim_params* out) {
 
 hd_status hd_conv1d(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h, int64_t L,
                     const hd_dim_params* prm, void* stream) {
-  if (!c || !f || !g || !h) return fail(HD_EINVAL, "null argument");
-  if (L < 1) return fail(HD_EINVAL, "L < 1");
-  if (L > ((int64_t)1 << 28)) return fail(HD_EUNSUPPORTED, "L too large");
-  if (prec != HD_FP32) return fail(HD_EUNSUPPORTED, "1D path is FP32 only");
-  if (prm && (prm->m < 0 || prm->q < 0)) return fail(HD_EINVAL, "negative m or q");
-  cudaSetDevice(c->device);
-  cudaStream_t st = (cudaStream_t)stream;
-  switch (algo) {
-    case HD_HYBRID_RCM:
-    case HD_HYBRID_CS: return conv1d_hybrid(c, algo, f, g, h, L, prm, st);
-    case HD_EXPLICIT_RCM: {
-      int C, m, p;
-      if (cluster_params(L, &C, &m, &p) && C <= 8) return conv1d_explicit_cluster(c, f, g, h, L, C, m, p, st);
-      return explicit_nd(c, algo, 1, &L, f, g, h, st);
-    }
-    case HD_EXPLICIT: return explicit_nd(c, algo, 1, &L, f, g, h, st);
-  }
-  return fail(HD_EINVAL, "unknown algorithm");
+  return hd_conv_ext(c, algo, prec, 1, &L, nullptr, f, g, h, prm, stream);
 }
 
 hd_status hd_conv_batch(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const int64_t* Ls, int32_t batch,
@@ -334,6 +324,45 @@ hd_status hd_conv_batch(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const i
     if (s != HD_OK) return s;
   }
   return HD_OK;
+}
+
+hd_status hd_conv_ext(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const int64_t* L, const int64_t* K,
+                      const float* f, const float* g, float* h, const hd_dim_params* prm, void* stream) {
+  if (!c || !L || !f || !g || !h) return fail(HD_EINVAL, "null argument");
+  if (ndim < 1 || ndim > 3) return fail(HD_EINVAL, "ndim must be 1, 2 or 3");
+  int64_t Kx[3], n_in = 1, n_out = 1;
+  bool full = false;
+  for (int i = 0; i < ndim; ++i) {
+    if (L[i] < 1) return fail(HD_EINVAL, "L < 1");
+    Kx[i] = K ? K[i] : L[i];
+    if (Kx[i] < L[i] || Kx[i] > 2 * L[i] - 1) return fail(HD_EINVAL, "output extent K must satisfy L <= K <= 2L-1");
+    full = full || Kx[i] != L[i];
+    n_in *= L[i];
+    n_out *= Kx[i];
+  }
+  // a longer output is written while the inputs are still read
+  if (full && ((h < f + n_in && f < h + n_out) || (h < g + n_in && g < h + n_out)))
+    return fail(HD_EINVAL, "h may alias f or g only when K = L");
+  if (prm)
+    for (int i = 0; i < ndim; ++i)
+      if (prm[i].m < 0 || prm[i].q < 0) return fail(HD_EINVAL, "negative m or q");
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ndim > 1) return conv_nd_ext(c, algo, prec, f, g, h, ndim, L, Kx, prm, st);
+  const int64_t L0 = L[0], K0 = Kx[0];
+  if (L0 > ((int64_t)1 << 28)) return fail(HD_EUNSUPPORTED, "L too large");
+  if (prec != HD_FP32) return fail(HD_EUNSUPPORTED, "1D path is FP32 only");
+  switch (algo) {
+    case HD_HYBRID_RCM:
+    case HD_HYBRID_CS: return conv1d_hybrid(c, algo, f, g, h, L0, prm, st, K0);
+    case HD_EXPLICIT_RCM: {
+      int C, m, p;
+      if (cluster_params(L0, &C, &m, &p) && C <= 8) return conv1d_explicit_cluster(c, f, g, h, L0, C, m, p, st, 1, K0);
+      return explicit_nd(c, algo, 1, L, f, g, h, st, &K0);
+    }
+    case HD_EXPLICIT: return explicit_nd(c, algo, 1, L, f, g, h, st, &K0);
+  }
+  return fail(HD_EINVAL, "unknown algorithm");
 }
 
 hd_status hd_last_device_error(hd_ctx* c) {

@@ -251,6 +251,7 @@ struct CtaState {
   int L, Lp, p, c;        // real length, packed length, blocks, rank in the cluster
   int64_t off_in;         // offset of the item in the input arrays
   int Lin, pin;           // real length of the input arrays' item and the blocks read
+  int Lout, pout;         // real length of the output (L <= Lout <= 2L - 1) and the blocks written
   bool in16, in8, out16;  // f + off and g + off 16- / 8-byte aligned; h + off 16-byte aligned
   const float2* tw;       // zeta_N^k, N = 2 C M
   const float2* tab;      // per-length table (Shape::TAB1 | TAB2 | product)
@@ -646,13 +647,16 @@ struct Steps {
       float* hi = x.h + x.off;
 #pragma unroll
       for (int t = 0; t < C; ++t) {
-        if (t < x.p) {
-          const float2 ov = (t == 0) ? o[0] : cmul(o[t], root32<-1>(t * (16 / C)));
-          const float2 out = cscale(cadd(e[t], ov), sc);
-          const int j = t * M + s;
-          const int rem = x.L - 2 * j;
-          if (rem > 0) hi[2 * j] = out.x;
-          if (rem > 1) hi[2 * j + 1] = out.y;
+        const float2 ov = (t == 0) ? o[0] : cmul(o[t], root32<-1>(t * (16 / C)));
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {  // blocks t and t + C (zeta_q^{-C} = -1)
+          if (t + half * C < x.pout) {
+            const float2 out = cscale(half ? csub(e[t], ov) : cadd(e[t], ov), sc);
+            const int j = (t + half * C) * M + s;
+            const int rem = x.Lout - 2 * j;
+            if (rem > 0) hi[2 * j] = out.x;
+            if (rem > 1) hi[2 * j + 1] = out.y;
+          }
         }
       }
       return;
@@ -669,7 +673,7 @@ struct Steps {
         y[0][r] = buf[r * SL + sl];
       }
     }
-    float2 out[SW3][C];
+    float2 out[SW3][2 * C];  // blocks t < 2C; t >= C only for outputs beyond L
 #pragma unroll
     for (int w = 0; w < SW3; ++w) {
       float2 wr[Q];
@@ -687,14 +691,15 @@ struct Steps {
       for (int t = 0; t < C; ++t) {
         const float2 ov = (t == 0) ? o[0] : cmul(o[t], root32<-1>(t * (16 / C)));
         out[w][t] = cscale(cadd(e[t], ov), sc);
+        out[w][t + C] = cscale(csub(e[t], ov), sc);  // zeta_q^{-C t'} = (-1)^r
       }
     }
     float* hi = x.h + x.off;
 #pragma unroll
-    for (int t = 0; t < C; ++t) {
-      if (t < x.p) {
+    for (int t = 0; t < 2 * C; ++t) {
+      if (t < x.pout) {
         const int j = t * M + s;
-        const int rem = x.L - 2 * j;
+        const int rem = x.Lout - 2 * j;
         if constexpr (SW3 == 2) {
           if (rem >= 4 && x.out16) {
             *reinterpret_cast<float4*>(hi + 2 * j) = make_float4(out[0][t].x, out[0][t].y, out[1][t].x, out[1][t].y);

@@ -114,6 +114,8 @@ __global__ void __launch_bounds__(Shape<R3>::T, Shape<R3>::MINB)
   x.off_in = EXP ? it.off_in : it.off;
   x.Lin = EXP ? 2 * it.L : it.L;
   x.pin = EXP ? (it.L + M - 1) / M : it.p;
+  x.Lout = it.K > 0 ? it.K : it.L;
+  x.pout = ((x.Lout + 1) / 2 + M - 1) / M;
   {
     const uintptr_t fa = (uintptr_t)(f + x.off_in), ga = (uintptr_t)(g + x.off_in), ha = (uintptr_t)(h + it.off);
     x.in16 = ((fa | ga) & 15) == 0;

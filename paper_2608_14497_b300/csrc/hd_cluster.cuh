@@ -16,6 +16,8 @@ struct CItem {
   int64_t off;
   int64_t off_in;  // explicit-padding baseline: offset of the item in the padded inputs
   int32_t L, m, p, C;
+  int32_t K;           // real output length (L <= K <= 2L - 1; 0: K = L)
+  int32_t pad_;
   const float2* tw;    // zeta_N^k, N = 2 C m
   const float2* tabm;  // per-length table of the kernel's passes and product (cl::Shape)
 };

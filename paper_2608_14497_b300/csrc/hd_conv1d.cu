@@ -39,13 +39,15 @@ __global__ void __launch_bounds__(1024) k_rcm1d(Launch1D la, const float* f, con
   const int L = it.L, m = it.m, q = it.q, p = it.p;
   const int N = q * m;
   const int Lp = (L + 1) >> 1;
+  const int K = it.K > 0 ? it.K : L;  // real output length
+  const int Kp = (K + 1) >> 1;
   const float* fi = f + it.off;
   const float* gi = g + it.off;
   float* hi = h + it.off;
   float2* acc = it.gacc ? reinterpret_cast<float2*>(it.gacc) : sm;
-  float2* buf = it.gacc ? sm : sm + acc_slots(Lp);
+  float2* buf = it.gacc ? sm : sm + acc_slots(Kp);
   const float2* __restrict__ tw = it.tw;
-  for (int j = tid; j < Lp; j += T) acc[j] = make_float2(0.f, 0.f);
+  for (int j = tid; j < Kp; j += T) acc[j] = make_float2(0.f, 0.f);
   __syncthreads();
 
   for (int ra = 0; ra <= q / 2; ++ra) {
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(1024) k_rcm1d(Launch1D la, const float* f, con
     // Eq. accumulator: backward length-m DFTs of the products ...
     cta_fft<-1, PTS>(buf, m, nres, s_pl, tw, q);
     // ... then h_{r, j} = zeta_N^{-r j} w_r[j mod m], summed (Eq. accumulation).
-    for (int j = tid; j < Lp; j += T) {
+    for (int j = tid; j < Kp; j += T) {
       const int s = j % m;
       float2 v = cmul(F0[s], tw_get<-1>(tw, mulmod(ra, j, N)));
       if (!self) v = cadd(v, cmul(Fb[s], tw_get<-1>(tw, mulmod(rb, j, N))));
@@ -112,10 +114,10 @@ __global__ void __launch_bounds__(1024) k_rcm1d(Launch1D la, const float* f, con
     __syncthreads();
   }
   const float sc = 1.0f / (float)N;
-  for (int j = tid; j < Lp; j += T) {
+  for (int j = tid; j < Kp; j += T) {
     const float2 v = acc[j];
     hi[2 * j] = v.x * sc;
-    if (2 * j + 1 < L) hi[2 * j + 1] = v.y * sc;
+    if (2 * j + 1 < K) hi[2 * j + 1] = v.y * sc;
   }
 }
 
@@ -132,13 +134,14 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
   const int T = blockDim.x, tid = threadIdx.x;
   const int L = it.L, m = it.m, q = it.q, p = it.p;
   const int N = q * m;
+  const int K = it.K > 0 ? it.K : L;  // real output length
   const float* fi = f + it.off;
   const float* gi = g + it.off;
   float* hi = h + it.off;
   float* acc = it.gacc ? reinterpret_cast<float*>(it.gacc) : reinterpret_cast<float*>(sm);
-  float2* buf = it.gacc ? sm : sm + acc_slots((L + 1) >> 1);
+  float2* buf = it.gacc ? sm : sm + acc_slots((K + 1) >> 1);
   const float2* __restrict__ tw = it.tw;
-  for (int j = tid; j < L; j += T) acc[j] = 0.f;
+  for (int j = tid; j < K; j += T) acc[j] = 0.f;
   __syncthreads();
 
   const int nlow = (q + 1) / 2;                 // residues 0 .. ceil(q/2)-1
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
       __syncthreads();
       cta_fft<-1, PTS>(buf, n2, 1, s_ph, tw, 2 * q);
       // h_0 = 2 unpack(z''), repeated for every block t (Sec. 3.1.1).
-      for (int j = tid; j < L; j += T) {
+      for (int j = tid; j < K; j += T) {
         const int s = j % m;
         const float2 v = Z[s >> 1];
         acc[j] += 2.f * ((s & 1) ? v.y : v.x);
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
       for (int l = tid; l < m; l += T) buf[l] = cmul(buf[l], buf[m + l]);
       __syncthreads();
       cta_fft<-1, PTS>(buf, m, 1, s_pm, tw, q);
-      for (int j = tid; j < L; j += T) acc[j] += buf[j % m].x;
+      for (int j = tid; j < K; j += T) acc[j] += buf[j % m].x;
       __syncthreads();
     } else if (2 * r == q) {
       // Sec. 3.1.3: x_s = sum_t (-1)^t f_{tm+s}; W_b = zeta_2m^b (x_b + i x_{e+b})
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
       __syncthreads();
       cta_fft<-1, PTS>(buf, e, 1, s_ph, tw, 2 * q);
       // Eqs. wb / accumulateq2: w_b = zeta_2m^{-b} (...); (-1)^t 2Re w_b, (-1)^t 2Im w_b.
-      for (int j = tid; j < L; j += T) {
+      for (int j = tid; j < K; j += T) {
         const int t = j / m, s = j - t * m;
         const int b = s < e ? s : s - e;
         const float2 w = cmul(buf[b], tw_get<-1>(tw, b * qh));
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
       for (int l = tid; l < m; l += T) buf[l] = cmul(buf[l], buf[m + l]);
       __syncthreads();
       cta_fft<-1, PTS>(buf, m, 1, s_pm, tw, q);
-      for (int j = tid; j < L; j += T) {
+      for (int j = tid; j < K; j += T) {
         const float2 v = cmul(buf[j % m], tw_get<-1>(tw, mulmod(r, j, N)));
         acc[j] += 2.f * v.x;
       }
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
     }
   }
   const float sc = 1.0f / (float)N;
-  for (int j = tid; j < L; j += T) hi[j] = acc[j] * sc;
+  for (int j = tid; j < K; j += T) hi[j] = acc[j] * sc;
 }
 
 // ---------------------------------------------------------------------------

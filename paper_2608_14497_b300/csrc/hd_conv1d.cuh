@@ -31,8 +31,9 @@ struct Params1D {
   size_t smem = 0;
 };
 
-hd_status resolve_rcm1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D* out);
-hd_status resolve_cs1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D* out);
+// K: real output length (0: K = L); it sizes the accumulator.
+hd_status resolve_rcm1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D* out, int64_t K = 0);
+hd_status resolve_cs1d(hd_ctx* c, int64_t L, const hd_dim_params* prm, Params1D* out, int64_t K = 0);
 
 size_t rcm1d_smem_bytes(int L, int m, bool gacc);
 size_t cs1d_smem_bytes(int L, int m, bool gacc);

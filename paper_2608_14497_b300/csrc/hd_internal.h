@@ -19,7 +19,7 @@ struct Item1D {
   int32_t m, q, p;   // hybrid parameters (packed lengths for hybridRCM)
   int32_t plan;      // index of the length-m FFT plan
   int32_t plan_half; // index of the length-m/2 FFT plan (-1 if unused)
-  int32_t pad;
+  int32_t K;         // real output length (L <= K <= 2L - 1; 0: K = L)
   const float2* tw;  // zeta_N^k table, N = q m
   void* gacc;        // accumulator in global memory, or nullptr for shared memory
 };

@@ -232,25 +232,29 @@ static hd_status rcm_nd_forward(hd_ctx* c, int d, const int64_t* L, int64_t batc
 }
 
 // Backward outer passes from the outer spectra S to the real result.
-static hd_status rcm_nd_backward(hd_ctx* c, int d, const int64_t* L, int64_t batch, const RcmNdPlan& P,
+// Backward outer passes from the outer spectra S (rows of Kp = ceil(K_last/2)
+// packed values) to the real result of extents K (K = L: the first L
+// outputs per dimension).
+static hd_status rcm_nd_backward(hd_ctx* c, int d, const int64_t* K, int64_t batch, const RcmNdPlan& P,
                                  const float2* S, float2* T, float* z, int out_mode, cudaStream_t st, bool tc) {
-  const int Ln = (int)L[d - 1];
+  const int Kn = (int)K[d - 1];
+  const int64_t Kp = (K[d - 1] + 1) / 2;
   if (d == 2)
-    return col_bwd(c, S, z, out_mode, Ln, batch, (int)L[0], P.Lp, P.outer[0], 1.0f / (float)P.M0, st, 0, tc);
+    return col_bwd(c, S, z, out_mode, Kn, batch, (int)K[0], Kp, P.outer[0], 1.0f / (float)P.M0, st, 0, tc);
   hd_status s =
-      col_bwd(c, S, T, OUT_COMPLEX, 0, batch * P.M0, (int)L[1], P.Lp, P.outer[1], 1.0f / (float)P.M1, st, 0, tc);
+      col_bwd(c, S, T, OUT_COMPLEX, 0, batch * P.M0, (int)K[1], Kp, P.outer[1], 1.0f / (float)P.M1, st, 0, tc);
   if (s == HD_OK)
-    s = col_bwd(c, T, z, out_mode, Ln, batch, (int)L[0], L[1] * P.Lp, P.outer[0], 1.0f / (float)P.M0, st, P.Lp,
-                tc);
+    s = col_bwd(c, T, z, out_mode, Kn, batch, (int)K[0], K[1] * Kp, P.outer[0], 1.0f / (float)P.M0, st, Kp, tc);
   return s;
 }
 
-static RowGeom rcm_row_geom(int d, int64_t batch, const RcmNdPlan& P) {
+static RowGeom rcm_row_geom(int d, int64_t batch, const RcmNdPlan& P, int64_t Kp = 0) {
   RowGeom rg;
   std::memset(&rg, 0, sizeof(rg));
   rg.rpi = (int)(P.M0 * P.M1);
   rg.nrows = (int)(batch * P.M0 * P.M1);
   rg.Lrow = (int)P.Lp;
+  rg.Kout = (int)(Kp > 0 ? Kp : P.Lp);
   rg.m = P.row.m;
   rg.q = P.row.q;
   rg.p = P.row.p;
@@ -266,41 +270,49 @@ static RowGeom rcm_row_geom(int d, int64_t batch, const RcmNdPlan& P) {
 
 // hybridRCM in 2D/3D (Sec. 5) for `batch` problems stored back to back: outer
 // forward passes of f and g, C_1 on every row pair, outer backward passes.
+// K: output extents (nullptr: K = L; the first L outputs per dimension).
 static hd_status hybrid_rcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_params* prm, const float* f,
-                               const float* g, float* h, cudaStream_t st, bool tc = false, int64_t batch = 1) {
+                               const float* g, float* h, cudaStream_t st, bool tc = false, int64_t batch = 1,
+                               const int64_t* K = nullptr) {
+  if (!K) K = L;
   RcmNdPlan P;
   hd_status s = rcm_nd_plan(c, d, L, prm, &P, st, !tc);
   if (s != HD_OK) return s;
-  // scratch: F, G spectra [batch][M0][M1][Lp] plus (3D) the intermediates [batch][M0][L1][Lp]
+  const int64_t Kp = (K[d - 1] + 1) / 2;
+  const bool ext = Kp != P.Lp;  // longer rows: the row pass writes a separate buffer
+  // scratch: F, G spectra [batch][M0][M1][Lp], the row pass's output [..][Kp]
+  // when K > L, and (3D) the intermediates [batch][M0][max(L1, K1)][max(Lp, Kp)]
   const int64_t spec = batch * P.M0 * P.M1 * P.Lp;
-  const int64_t mid = d == 3 ? batch * P.M0 * L[1] * P.Lp : 0;
-  if (ensure_ws(c, sizeof(float2) * (size_t)(2 * spec + 2 * mid), st) != HD_OK) return HD_ENOMEM;
+  const int64_t out = ext ? batch * P.M0 * P.M1 * Kp : 0;
+  const int64_t mid = d == 3 ? batch * P.M0 * std::max(L[1], K[1]) * std::max(P.Lp, Kp) : 0;
+  if (ensure_ws(c, sizeof(float2) * (size_t)(2 * spec + out + 2 * mid), st) != HD_OK) return HD_ENOMEM;
   float2* SF = reinterpret_cast<float2*>(c->ws);
   float2* SG = SF + spec;
-  float2* TF = SG + spec;
+  float2* SO = ext ? SG + spec : SF;
+  float2* TF = SG + spec + out;
   float2* TG = TF + mid;
   s = rcm_nd_forward(c, d, L, batch, P, f, IN_PACKED_REAL, SF, TF, st, tc);
   if (s == HD_OK) s = rcm_nd_forward(c, d, L, batch, P, g, IN_PACKED_REAL, SG, TG, st, tc);
   if (s != HD_OK) return s;
   // rows: C_1 on each row pair; arrays per residue step: {A, C, B, D} x (1 or
   // 2 residues); with q <= 2 every residue is its own partner, so 4
-  const RowGeom rg = rcm_row_geom(d, batch, P);
+  const RowGeom rg = rcm_row_geom(d, batch, P, Kp);
   if (!tc && P.row.q == 2 && rows_cl_length(P.row.m)) {
     hd_status terr = HD_OK;
     const float2* tab = c->tables.get_pass_table(P.row.m, st, &terr);
     if (!tab) return terr;
-    HD_TRY(launch_rows_cl(P.row.m, (unsigned)rg.nrows, st, SF, SG, rg, 1.0f / (float)(P.row.q * P.row.m), P.row.tw,
-                          tab));
-    return rcm_nd_backward(c, d, L, batch, P, SF, TF, h, OUT_UNPACK_REAL, st, tc);
+    HD_TRY(launch_rows_cl(P.row.m, (unsigned)rg.nrows, st, SF, SG, SO, rg, 1.0f / (float)(P.row.q * P.row.m),
+                          P.row.tw, tab));
+    return rcm_nd_backward(c, d, K, batch, P, SO, TF, h, OUT_UNPACK_REAL, st, tc);
   }
   const int narr = P.row.q <= 2 ? 4 : 8;
   const Eng reng = pick_eng(tc, struct_length(P.row.m) && P.row.q <= 2);
-  const size_t smem = sizeof(float2) * ((size_t)acc_slots(2 * (int)P.Lp) + narr * (size_t)P.row.m);
+  const size_t smem = sizeof(float2) * ((size_t)acc_slots(2 * (int)Kp) + narr * (size_t)P.row.m);
   if (smem > (size_t)c->max_smem || narr * (int64_t)P.row.m > max_points(reng)) return HD_EUNSUPPORTED;
   const int T = eng_threads(reng, narr * (int64_t)P.row.m);
-  HD_TRY(launch_rows_rcm(reng, (unsigned)rg.nrows, T, smem, st, SF, SG, rg, 1.0f / (float)(P.row.q * P.row.m),
+  HD_TRY(launch_rows_rcm(reng, (unsigned)rg.nrows, T, smem, st, SF, SG, SO, rg, 1.0f / (float)(P.row.q * P.row.m),
                          P.row.tw, P.row.pl));
-  return rcm_nd_backward(c, d, L, batch, P, SF, TF, h, OUT_UNPACK_REAL, st, tc);
+  return rcm_nd_backward(c, d, K, batch, P, SO, TF, h, OUT_UNPACK_REAL, st, tc);
 }
 
 // The adjoint of hybridRCM 2D/3D for `batch` problems: U = outer spectra of
@@ -437,7 +449,7 @@ static hd_status hybrid_cs_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_p
 }
 
 hd_status explicit_nd(hd_ctx* c, hd_algo algo, int d, const int64_t* Lin, const float* f, const float* g, float* h,
-                      cudaStream_t st) {
+                      cudaStream_t st, const int64_t* Kin) {
   // padded extents: 2L per dimension (real); explicitRCM packs the last one to
   // an even packed length (Alg. 4 needs it even)
   // (each padded length is 2 x the smallest length {1, 3, 5, 9} x 2^a >= L, so
@@ -532,11 +544,14 @@ hd_status explicit_nd(hd_ctx* c, hd_algo algo, int d, const int64_t* Lin, const 
     io.src = SF;
     io.dst = h;
     io.src_stride = bins;
-    io.Lkeep = (int)L[2];
+    // outputs kept per dimension: K (default L), 2L-1 at most, within the padded 2 ladder(L)
+    int64_t K[3] = {1, 1, 1};
+    for (int i = 0; i < d; ++i) K[3 - d + i] = Kin ? Kin[i] : Lin[i];
+    io.Lkeep = (int)K[2];
     io.crop_rows_outer[0] = Mo0;
     io.crop_rows_outer[1] = Mo1;
-    io.keep_rows_outer[0] = L[0];
-    io.keep_rows_outer[1] = L[1];
+    io.keep_rows_outer[0] = K[0];
+    io.keep_rows_outer[1] = K[1];
     // the unnormalised inverse returns n Mo0 Mo1 times the convolution, for
     // both the real (pack after U^{-1}) and the packed (RCM) forms
     io.scale = (float)(1.0 / ((double)Mo0 * (double)Mo1 * (double)n));
@@ -557,34 +572,38 @@ hd_status conv_nd_batch_rcm(hd_ctx* c, int d, const int64_t* L, int64_t batch, c
 }
 }  // namespace hd
 
-static hd_status conv_nd(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h, int d,
-                         const int64_t* L, const hd_dim_params* prm, void* stream) {
-  if (!c || !f || !g || !h) return HD_EINVAL;
+namespace hd {
+// 2D/3D with output extents K (validated by the caller: L <= K <= 2L-1).
+hd_status conv_nd_ext(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h, int d,
+                      const int64_t* L, const int64_t* K, const hd_dim_params* prm, cudaStream_t st) {
   for (int i = 0; i < d; ++i)
-    if (L[i] < 1 || L[i] > (1 << 20)) return L[i] < 1 ? HD_EINVAL : HD_EUNSUPPORTED;
+    if (L[i] > (1 << 20)) return fail(HD_EUNSUPPORTED, "L too large");
+  bool full = false;
+  for (int i = 0; i < d; ++i) full = full || K[i] != L[i];
   // split precision: the radix-16 passes of hybridRCM's 2D/3D kernels on tensor cores
-  if (prec == HD_SPLIT_BF16 && algo != HD_HYBRID_RCM) return HD_EUNSUPPORTED;
-  if (prec != HD_FP32 && prec != HD_SPLIT_BF16) return HD_EINVAL;
-  cudaSetDevice(c->device);
-  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == HD_SPLIT_BF16 && algo != HD_HYBRID_RCM) return fail(HD_EUNSUPPORTED, "split precision: hybridRCM only");
+  if (prec != HD_FP32 && prec != HD_SPLIT_BF16) return fail(HD_EINVAL, "unknown precision");
   switch (algo) {
-    case HD_HYBRID_RCM: return hybrid_rcm_nd(c, d, L, prm, f, g, h, st, prec == HD_SPLIT_BF16);
-    case HD_HYBRID_CS: return hybrid_cs_nd(c, d, L, prm, f, g, h, st);
+    case HD_HYBRID_RCM: return hybrid_rcm_nd(c, d, L, prm, f, g, h, st, prec == HD_SPLIT_BF16, 1, K);
+    case HD_HYBRID_CS:
+      if (full) return fail(HD_EUNSUPPORTED, "hybridCS in 2D/3D returns the first L outputs only");
+      return hybrid_cs_nd(c, d, L, prm, f, g, h, st);
     case HD_EXPLICIT:
-    case HD_EXPLICIT_RCM: return explicit_nd(c, algo, d, L, f, g, h, st);
+    case HD_EXPLICIT_RCM: return explicit_nd(c, algo, d, L, f, g, h, st, K);
   }
-  return HD_EINVAL;
+  return fail(HD_EINVAL, "unknown algorithm");
 }
+}  // namespace hd
 
 extern "C" {
 hd_status hd_conv2d(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h, int64_t L1,
                     int64_t L2, const hd_dim_params* prm, void* stream) {
   const int64_t L[2] = {L1, L2};
-  return conv_nd(c, algo, prec, f, g, h, 2, L, prm, stream);
+  return hd_conv_ext(c, algo, prec, 2, L, nullptr, f, g, h, prm, stream);
 }
 hd_status hd_conv3d(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h, int64_t L1,
                     int64_t L2, int64_t L3, const hd_dim_params* prm, void* stream) {
   const int64_t L[3] = {L1, L2, L3};
-  return conv_nd(c, algo, prec, f, g, h, 3, L, prm, stream);
+  return hd_conv_ext(c, algo, prec, 3, L, nullptr, f, g, h, prm, stream);
 }
 }

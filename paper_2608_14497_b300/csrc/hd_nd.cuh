@@ -5,8 +5,11 @@
 #include "hd_internal.h"
 
 namespace hd {
+// K: output extents per dimension (nullptr: K = L).
 hd_status explicit_nd(hd_ctx* c, hd_algo algo, int d, const int64_t* L, const float* f, const float* g, float* h,
-                      cudaStream_t st);
+                      cudaStream_t st, const int64_t* K = nullptr);
+hd_status conv_nd_ext(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, const float* g, float* h, int d,
+                      const int64_t* L, const int64_t* K, const hd_dim_params* prm, cudaStream_t st);
 // hybridRCM 2D/3D over `batch` problems of extents L stored back to back.
 hd_status conv_nd_batch_rcm(hd_ctx* c, int d, const int64_t* L, int64_t batch, const float* f, const float* g,
                             float* h, cudaStream_t st);

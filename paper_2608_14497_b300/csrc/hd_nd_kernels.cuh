@@ -425,6 +425,7 @@ struct RowGeom {
   int nd;           // number of outer dimensions (1 or 2)
   int om[2], oq[2]; // outer (m, q) per outer dimension
   int rpi;          // rows per item: rows pair only inside their own item
+  int Kout;         // output row length (complex; >= Lrow for outputs beyond L)
 };
 
 __device__ __forceinline__ int row_partner(int row, const RowGeom& g) {
@@ -436,8 +437,8 @@ __device__ __forceinline__ int row_partner(int row, const RowGeom& g) {
 }
 
 template <int PTS, bool TC, bool SE>
-__global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_rows_rcm(float2* F, const float2* __restrict__ G, RowGeom rg, float scale,
-                                                   const float2* __restrict__ tw, FftPlan pl) {
+__global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_rows_rcm(float2* F, const float2* __restrict__ G, float2* O,
+                                                   RowGeom rg, float scale, const float2* __restrict__ tw, FftPlan pl) {
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   const int row = blockIdx.x;
@@ -445,13 +446,13 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_rows_rcm(float2* F,
   if (prow < row) return;
   const bool selfrow = (prow == row);
   const int T = blockDim.x, tid = threadIdx.x;
-  const int Lr = rg.Lrow, m = rg.m, q = rg.q, p = rg.p, N = q * m;
+  const int Lr = rg.Lrow, Kr = rg.Kout, m = rg.m, q = rg.q, p = rg.p, N = q * m;
   const int nrow = selfrow ? 1 : 2;
-  float2* acc = sm;                          // nrow x Lr
-  float2* buf = sm + acc_slots(nrow * Lr);   // arrays of m
+  float2* acc = sm;                          // nrow x Kr (outputs)
+  float2* buf = sm + acc_slots(nrow * Kr);   // arrays of m
   const float2* src[4] = {F + (int64_t)row * Lr, F + (int64_t)prow * Lr, G + (int64_t)row * Lr,
                           G + (int64_t)prow * Lr};
-  for (int idx = tid; idx < nrow * Lr; idx += T) acc[idx] = make_float2(0.f, 0.f);
+  for (int idx = tid; idx < nrow * Kr; idx += T) acc[idx] = make_float2(0.f, 0.f);
   __syncthreads();
   auto residue_pass = [&](int ra) __attribute__((always_inline)) {
     const int rb = (q - ra) % q;
@@ -525,8 +526,8 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_rows_rcm(float2* F,
     __syncthreads();
     // inverse: A arrays (and C arrays) hold the products
     fft_sel<-1, PTS, TC, SE>(buf, m, selfrow ? nres : 2 * nres, pl, tw, q);
-    for (int idx = tid; idx < nrow * Lr; idx += T) {
-      const int rr = idx / Lr, j = idx - rr * Lr;
+    for (int idx = tid; idx < nrow * Kr; idx += T) {
+      const int rr = idx / Kr, j = idx - rr * Kr;
       const int s = j % m;
       float2 v = cmul(arrp(rr, 0)[s], tw_get<-1>(tw, modmul(ra, j, N)));
       if (!selfres) v = cadd(v, cmul(arrp(rr, 1)[s], tw_get<-1>(tw, modmul(rb, j, N))));
@@ -541,9 +542,9 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_rows_rcm(float2* F,
   } else {
     for (int ra = 0; ra <= q / 2; ++ra) residue_pass(ra);
   }
-  for (int idx = tid; idx < nrow * Lr; idx += T) {
-    const int rr = idx / Lr, j = idx - rr * Lr;
-    F[(int64_t)(rr ? prow : row) * Lr + j] = cscale(acc[idx], scale);
+  for (int idx = tid; idx < nrow * Kr; idx += T) {
+    const int rr = idx / Kr, j = idx - rr * Kr;
+    O[(int64_t)(rr ? prow : row) * Kr + j] = cscale(acc[idx], scale);
   }
 }
 
@@ -845,13 +846,14 @@ cudaError_t launch_col_fwd_cs(Eng e, unsigned grid, int T, size_t smem, cudaStre
 cudaError_t launch_col_bwd_cs(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, const float2* Y, float* Z,
                               int64_t B, int W, int Lout, int m, int q, float scale, const float2* tw, FftPlan pl_m,
                               FftPlan pl_h);
+// O: output rows (rg.Kout per row); O = F (in place) when Kout = Lrow.
 cudaError_t launch_rows_rcm(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, float2* F, const float2* G,
-                            RowGeom rg, float scale, const float2* tw, FftPlan pl);
+                            float2* O, RowGeom rg, float scale, const float2* tw, FftPlan pl);
 // Row pass of hybridRCM on the compile-time engine (hd_nd_rowscl.cu): rows of
 // residue length m = 256 R3 (rows_cl_length), q = 2.
 bool rows_cl_length(int m);
-cudaError_t launch_rows_cl(int m, unsigned grid, cudaStream_t st, float2* F, const float2* G, RowGeom rg, float scale,
-                           const float2* tw, const float2* tab);
+cudaError_t launch_rows_cl(int m, unsigned grid, cudaStream_t st, float2* F, const float2* G, float2* O, RowGeom rg,
+                           float scale, const float2* tw, const float2* tab);
 cudaError_t launch_rows_adj_cl(int m, unsigned grid, cudaStream_t st, float2* F, float2* G, const float2* U,
                                RowGeom rg, float scale, int outs, const float2* tw, const float2* tab);
 cudaError_t launch_rows_adj(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, float2* F, float2* G,

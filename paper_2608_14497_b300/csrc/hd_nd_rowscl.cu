@@ -11,16 +11,16 @@ bool rows_cl_length(int m) {
   return R3 == 1 || R3 == 2 || R3 == 3 || R3 == 4 || R3 == 5 || R3 == 6 || R3 == 8;
 }
 
-cudaError_t launch_rows_cl(int m, unsigned grid, cudaStream_t st, float2* F, const float2* G, RowGeom rg, float scale,
-                           const float2* tw, const float2* tab) {
+cudaError_t launch_rows_cl(int m, unsigned grid, cudaStream_t st, float2* F, const float2* G, float2* O, RowGeom rg,
+                           float scale, const float2* tw, const float2* tab) {
   switch (m / 256) {
-    case 1: return rows::launch_rows<1>(grid, st, F, G, rg, scale, tw, tab);
-    case 2: return rows::launch_rows<2>(grid, st, F, G, rg, scale, tw, tab);
-    case 3: return rows::launch_rows<3>(grid, st, F, G, rg, scale, tw, tab);
-    case 4: return rows::launch_rows<4>(grid, st, F, G, rg, scale, tw, tab);
-    case 5: return rows::launch_rows<5>(grid, st, F, G, rg, scale, tw, tab);
-    case 6: return rows::launch_rows<6>(grid, st, F, G, rg, scale, tw, tab);
-    case 8: return rows::launch_rows<8>(grid, st, F, G, rg, scale, tw, tab);
+    case 1: return rows::launch_rows<1>(grid, st, F, G, O, rg, scale, tw, tab);
+    case 2: return rows::launch_rows<2>(grid, st, F, G, O, rg, scale, tw, tab);
+    case 3: return rows::launch_rows<3>(grid, st, F, G, O, rg, scale, tw, tab);
+    case 4: return rows::launch_rows<4>(grid, st, F, G, O, rg, scale, tw, tab);
+    case 5: return rows::launch_rows<5>(grid, st, F, G, O, rg, scale, tw, tab);
+    case 6: return rows::launch_rows<6>(grid, st, F, G, O, rg, scale, tw, tab);
+    case 8: return rows::launch_rows<8>(grid, st, F, G, O, rg, scale, tw, tab);
   }
   return cudaErrorInvalidValue;
 }

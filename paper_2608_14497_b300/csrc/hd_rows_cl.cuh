@@ -11,7 +11,8 @@
 // with M - 1 - l; the partner values come from the partner row, or from the
 // same row when the row is its own partner), the backward transforms of the
 // two products (Eq. accumulator), and h~_s = (w_0[s] + zeta_{2M}^{-s} w_1[s]) /
-// (2M) written back over F's rows (Eq. accumulation).
+// (2M) written to the output rows (over F's rows, or a separate buffer of
+// longer rows for outputs beyond L; Eq. accumulation).
 //
 // Shared arrays, M complex each, layout of hd_cl_kernel.cuh (phys): for a row
 // pair [F row r0, F row r1, F partner r0, F partner r1, G row r0, G row r1,
@@ -95,19 +96,24 @@ struct RowSteps {
     }
   }
 
-  // h~_s = (w_0[s] + zeta_{2M}^{-s} w_1[s]) * scale for s < Lp, written to row x.
-  static __device__ __forceinline__ void store_row(float2* __restrict__ x, int Lp, const float2* a0,
+  // h~_s = (w_0[s] + zeta_{2M}^{-s} w_1[s]) * scale and, for outputs beyond M,
+  // h~_{M+s} = (w_0[s] - zeta_{2M}^{-s} w_1[s]) * scale (zeta_{2M}^{-M} = -1),
+  // for positions < Kp, written to row x.
+  static __device__ __forceinline__ void store_row(float2* __restrict__ x, int Kp, const float2* a0,
                                                    const float2* __restrict__ tw, float scale, int tid) {
 #pragma unroll 2
     for (int k = tid; k < M / 2; k += T) {
       const int s = 2 * k;
-      if (s >= Lp) continue;
+      if (s >= Kp) continue;
       float2 w00, w01, w10, w11;
       cl::lds4(a0 + phys(s), w00, w01);
       cl::lds4(a0 + M + phys(s), w10, w11);
       const float4 w = cl::ldg4(tw + s);
-      x[s] = cscale(cadd(w00, cmul(w10, make_float2(w.x, -w.y))), scale);
-      if (s + 1 < Lp) x[s + 1] = cscale(cadd(w01, cmul(w11, make_float2(w.z, -w.w))), scale);
+      const float2 t0 = cmul(w10, make_float2(w.x, -w.y)), t1 = cmul(w11, make_float2(w.z, -w.w));
+      x[s] = cscale(cadd(w00, t0), scale);
+      if (s + 1 < Kp) x[s + 1] = cscale(cadd(w01, t1), scale);
+      if (M + s < Kp) x[M + s] = cscale(csub(w00, t0), scale);
+      if (M + s + 1 < Kp) x[M + s + 1] = cscale(csub(w01, t1), scale);
     }
   }
 };
@@ -115,8 +121,8 @@ struct RowSteps {
 // One row pair per CTA (rows whose partner precedes them exit at once).
 template <int R3>
 __global__ void __launch_bounds__(RowShape<R3>::T, RowShape<R3>::MINB)
-    k_rows_cl(float2* F, const float2* __restrict__ G, RowGeom rg, float scale, const float2* __restrict__ tw,
-              const float2* __restrict__ tab) {
+    k_rows_cl(float2* F, const float2* __restrict__ G, float2* O, RowGeom rg, float scale,
+              const float2* __restrict__ tw, const float2* __restrict__ tab) {
   using S = RowSteps<R3>;
   using K = typename S::K;
   constexpr int M = S::M, T = S::T;
@@ -131,7 +137,7 @@ __global__ void __launch_bounds__(RowShape<R3>::T, RowShape<R3>::MINB)
     const unsigned dst = (unsigned)__cvta_generic_to_shared(tws + 2 * i);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(tab + 2 * i) : "memory");
   }
-  const int Lp = rg.Lrow;
+  const int Lp = rg.Lrow, Kp = rg.Kout;
   const float2* zt = tab + cl::Shape<R3>::TABZ;
   if (prow == row) {
     // the row is its own partner: the one-CTA convolution of the cluster kernel
@@ -158,7 +164,7 @@ __global__ void __launch_bounds__(RowShape<R3>::T, RowShape<R3>::MINB)
     __syncthreads();
     K::template pass1<-1, 2, 1>(arr, tid, tws);
     __syncthreads();
-    S::store_row(F + (int64_t)row * Lp, Lp, arr, tw, scale, tid);
+    S::store_row(O + (int64_t)row * Kp, Kp, arr, tw, scale, tid);
     return;
   }
   S::load_row(F + (int64_t)row * Lp, Lp, arr, tw, tid);
@@ -181,8 +187,8 @@ __global__ void __launch_bounds__(RowShape<R3>::T, RowShape<R3>::MINB)
   __syncthreads();
   K::template pass1<-1, 4, 1>(arr, tid, tws);
   __syncthreads();
-  S::store_row(F + (int64_t)row * Lp, Lp, arr, tw, scale, tid);
-  S::store_row(F + (int64_t)prow * Lp, Lp, arr + 2 * M, tw, scale, tid);
+  S::store_row(O + (int64_t)row * Kp, Kp, arr, tw, scale, tid);
+  S::store_row(O + (int64_t)prow * Kp, Kp, arr + 2 * M, tw, scale, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -348,12 +354,12 @@ cudaError_t launch_rows_adj(unsigned grid, cudaStream_t st, float2* F, float2* G
 }
 
 template <int R3>
-cudaError_t launch_rows(unsigned grid, cudaStream_t st, float2* F, const float2* G, RowGeom rg, float scale,
+cudaError_t launch_rows(unsigned grid, cudaStream_t st, float2* F, const float2* G, float2* O, RowGeom rg, float scale,
                         const float2* tw, const float2* tab) {
   auto k = k_rows_cl<R3>;
   cudaError_t e = smem_optin((const void*)k, RowShape<R3>::SMEM);
   if (e != cudaSuccess) return e;
-  k<<<grid, RowShape<R3>::T, RowShape<R3>::SMEM, st>>>(F, G, rg, scale, tw, tab);
+  k<<<grid, RowShape<R3>::T, RowShape<R3>::SMEM, st>>>(F, G, O, rg, scale, tw, tab);
   return cudaGetLastError();
 }
 
