@@ -121,6 +121,22 @@ hd_status hd_conv_ext(hd_ctx* ctx, hd_algo algo, hd_prec prec, int ndim, const i
 hd_status hd_conv_batch(hd_ctx* ctx, hd_algo algo, hd_prec prec, int ndim, const int64_t* Ls, int32_t batch,
                         const float* f, const float* g, float* h, void* stream);
 
+/* hybridRCM in 1D through three kernels (Sec. 2; the block sums of Eq.
+ * forwardr and the accumulation of Eq. accumulation as q-point DFTs over the
+ * blocks, App. A): for q residues of length M, stage A transforms f and g over
+ * the blocks for every s < M, stage B (one CTA per residue pair) runs the
+ * length-M DFTs, the RCM product and the backward DFTs, stage C transforms
+ * back over the residues and unpacks.  hd_conv1d, hd_conv_ext and
+ * hd_conv_batch take this path for hybridRCM lengths beyond the cluster
+ * kernel (L > 73728) when prm is NULL; this call runs it for any L.
+ * `batch` items of L floats back to back in f and g, of K floats in h (K = 0
+ * means K = L; L <= K <= 2L-1).  M in {512, 1024, 2048, 4096, 4608}, q even,
+ * 2 <= q <= 1024, q M >= L; M = q = 0 lets the planner choose.  Scratch:
+ * 24 q M bytes per item (batches run in chunks of at most 1 GiB).  h may alias
+ * f or g only when K = L.  Errors as hd_conv1d. */
+hd_status hd_conv1d_staged(hd_ctx* ctx, int64_t L, int64_t K, int32_t M, int32_t q, int32_t batch, const float* f,
+                           const float* g, float* h, void* stream);
+
 /* Batched 1D convolutions of uneven lengths.  A plan is built on the host
  * from HOST arrays: item i occupies floats [offsets[i], offsets[i] + L[i]) of
  * f, g and h (items must not overlap).  The planner picks (m, q) per length
@@ -159,7 +175,8 @@ hd_status hd_conv_adjoint(hd_ctx* ctx, hd_algo algo, int ndim, const int64_t* Ls
                           void* stream);
 
 /* The planner's (m, q) for one dimension of real length L and `algo`
- * (HD_HYBRID_RCM reports packed lengths). */
+ * (HD_HYBRID_RCM reports packed lengths; beyond the cluster kernel, the (M, q)
+ * of the three-kernel path of hd_conv1d_staged). */
 hd_status hd_plan(hd_ctx* ctx, hd_algo algo, int64_t L, hd_dim_params* out);
 
 /* The batched planner's autotuner table (filled by the first hybridRCM batch

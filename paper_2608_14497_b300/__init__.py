@@ -27,7 +27,7 @@ PRECS = {"fp32": HD_FP32, "split_bf16": HD_SPLIT_BF16}
 EXPORTS = ("hd_create", "hd_destroy", "hd_conv1d", "hd_conv2d", "hd_conv3d", "hd_batch_plan_create",
            "hd_batch_plan_destroy", "hd_conv1d_batched", "hd_conv_adjoint", "hd_plan", "hd_last_device_error",
            "hd_strerror", "hd_last_error_string", "hd_conv1d_rcm_noalloc",
-           "hd_tuning_table", "hd_batch_plan_launches", "hd_conv_batch", "hd_conv_ext")
+           "hd_tuning_table", "hd_batch_plan_launches", "hd_conv_batch", "hd_conv_ext", "hd_conv1d_staged")
 
 
 class HDError(RuntimeError):
@@ -77,6 +77,7 @@ def load(build_if_missing=False):
         "hd_batch_plan_launches": ([P, P], I),
         "hd_conv_batch": ([P, I, I, I, P, I32, P, P, P, P], I),
         "hd_conv_ext": ([P, I, I, I, P, P, P, P, P, DP, P], I),
+        "hd_conv1d_staged": ([P, I64, I64, I32, I32, I32, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -158,6 +159,10 @@ def hd_conv_ext(ctx, algo, prec, Ls, Ks, f_ptr, g_ptr, h_ptr, prm=None, stream=0
 def hd_conv_batch(ctx, algo, prec, Ls, batch, f_ptr, g_ptr, h_ptr, stream=0):
     arr = (ctypes.c_int64 * len(Ls))(*[int(x) for x in Ls])
     return load().hd_conv_batch(ctx, algo, prec, len(Ls), arr, batch, f_ptr, g_ptr, h_ptr, stream)
+
+
+def hd_conv1d_staged(ctx, L, K, M, q, batch, f_ptr, g_ptr, h_ptr, stream=0):
+    return load().hd_conv1d_staged(ctx, L, K, M, q, batch, f_ptr, g_ptr, h_ptr, stream)
 
 
 def hd_conv_adjoint(ctx, algo, Ls, batch, gh_ptr, f_ptr, g_ptr, gf_ptr, gg_ptr, stream=0):
@@ -257,6 +262,28 @@ def conv_batch(f, g, ndim, algo="hybridRCM", out=None):
     st = hd_conv_batch(ctx, ALGOS[algo], HD_FP32, tuple(f.shape[1:]), f.shape[0], f.data_ptr(), g.data_ptr(),
                        h.data_ptr(), _stream_ptr())
     _check(st, "conv_batch")
+    return h
+
+
+def conv_staged(f, g, M=0, q=0, out_extent=None, out=None):
+    """hybridRCM in 1D through the three-kernel path (hd_conv1d_staged): f and
+    g of shape (L,) or (batch, L); (M, q) = (0, 0) lets the planner choose."""
+    import torch
+    _check_tensor(f, "f")
+    _check_tensor(g, "g")
+    if f.shape != g.shape or f.dim() not in (1, 2):
+        raise ValueError("f and g must share a (L,) or (batch, L) shape")
+    L = f.shape[-1]
+    batch = f.shape[0] if f.dim() == 2 else 1
+    K = L if out_extent is None else (2 * L - 1 if out_extent == "full" else int(out_extent))
+    shape = (K,) if f.dim() == 1 else (batch, K)
+    h = torch.empty(shape, dtype=f.dtype, device=f.device) if out is None else out
+    _check_tensor(h, "out")
+    if tuple(h.shape) != shape:
+        raise ValueError("out must have the output extents")
+    st = hd_conv1d_staged(context(f.device.index), L, K, M, q, batch, f.data_ptr(), g.data_ptr(), h.data_ptr(),
+                          _stream_ptr())
+    _check(st, "conv_staged")
     return h
 
 

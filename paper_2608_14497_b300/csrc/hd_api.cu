@@ -176,6 +176,8 @@ static hd_status conv1d_hybrid(hd_ctx* c, hd_algo algo, const float* f, const fl
   if (algo == HD_HYBRID_RCM && !(prm && prm->m > 0)) {
     int C, m, p;
     if (cluster_params(L, &C, &m, &p)) return conv1d_rcm_cluster(c, f, g, h, L, C, m, p, st, 1, K);
+    int M, q;
+    if (staged_params(L, &M, &q)) return conv1d_staged(c, f, g, h, L, K, M, q, 1, st);
   }
   Params1D P;
   hd_status s = (algo == HD_HYBRID_RCM) ? resolve_rcm1d(c, L, prm, &P, K) : resolve_cs1d(c, L, prm, &P, K);
@@ -276,6 +278,12 @@ hd_status hd_plan(hd_ctx* c, hd_algo algo, int64_t L, hd_dim_params* out) {
         out->q = 2 * C;
         return HD_OK;
       }
+      int M, q;
+      if (staged_params(L, &M, &q)) {
+        out->m = M;
+        out->q = q;
+        return HD_OK;
+      }
       s = resolve_rcm1d(c, L, nullptr, &P);
       break;
     }
@@ -308,6 +316,8 @@ hd_status hd_conv_batch(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const i
     int C, m, p;
     if (batch < (1 << 24) && cluster_params(Ls[0], &C, &m, &p))
       return conv1d_rcm_cluster(c, f, g, h, Ls[0], C, m, p, st, batch);
+    int M, q;
+    if (staged_params(Ls[0], &M, &q)) return conv1d_staged(c, f, g, h, Ls[0], Ls[0], M, q, batch, st);
   }
   if (prec == HD_FP32 && algo == HD_EXPLICIT_RCM && ndim == 1) {
     int C, m, p;
@@ -324,6 +334,25 @@ hd_status hd_conv_batch(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const i
     if (s != HD_OK) return s;
   }
   return HD_OK;
+}
+
+hd_status hd_conv1d_staged(hd_ctx* c, int64_t L, int64_t K, int32_t M, int32_t q, int32_t batch, const float* f,
+                           const float* g, float* h, void* stream) {
+  if (!c || !f || !g || !h || batch < 1) return fail(HD_EINVAL, "staged path: null argument or batch < 1");
+  if (L < 1 || L > ((int64_t)1 << 28)) return fail(HD_EINVAL, "staged path: L out of range");
+  if (K == 0) K = L;
+  if (K < L || K > 2 * L - 1) return fail(HD_EINVAL, "output extent K must satisfy L <= K <= 2L-1");
+  const int64_t n_in = L * batch, n_out = K * batch;
+  if (K != L && ((h < f + n_in && f < h + n_out) || (h < g + n_in && g < h + n_out)))
+    return fail(HD_EINVAL, "h may alias f or g only when K = L");
+  int Mx = M, qx = q;
+  if (M == 0 && q == 0) {
+    if (!staged_params(L, &Mx, &qx)) return fail(HD_EUNSUPPORTED, "staged path: L beyond 1024 x 4608");
+  } else if (M <= 0 || q <= 0) {
+    return fail(HD_EINVAL, "staged path: give both M and q, or neither");
+  }
+  cudaSetDevice(c->device);
+  return conv1d_staged(c, f, g, h, L, K, Mx, qx, batch, (cudaStream_t)stream);
 }
 
 hd_status hd_conv_ext(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const int64_t* L, const int64_t* K,

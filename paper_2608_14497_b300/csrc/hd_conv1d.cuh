@@ -43,4 +43,10 @@ cudaError_t launch_rcm1d(const Launch1D& la, int nitems, int threads, size_t sme
 cudaError_t launch_cs1d(const Launch1D& la, int nitems, int threads, size_t smem, const float* f,
                         const float* g, float* h, cudaStream_t st);
 
+// Three-kernel hybridRCM path (hd_staged.cu): planner (false beyond its range)
+// and the call for `batch` items of L floats (h: K floats per item).
+bool staged_params(int64_t L, int* M, int* q);
+hd_status conv1d_staged(hd_ctx* c, const float* f, const float* g, float* h, int64_t L, int64_t K, int M, int q,
+                        int64_t batch, cudaStream_t st);
+
 }  // namespace hd

@@ -1,0 +1,502 @@
+// hd_staged.cu -- hybridRCM in 1D through three kernels (the many-block path):
+// the form of Sec. 2 for lengths whose q residues do not fit one cluster of
+// CTAs (L > 73728), or for any length when called with explicit (M, q).
+//
+// With q residues of length M (N = q M >= L) and p = ceil(Lp / M) <= q/2
+// blocks of the packed input (Lp = ceil(L/2), Eq. complexPacking):
+//   stage A  for every s < M and both inputs, the q-point DFT over the blocks
+//            t of x~_{tM+s} (the inner sums of Eq. forwardr for every residue
+//            r at once: the pre-processing FFT over blocks of App. A, which
+//            replaces p q direct multiply-adds by an FFT when p is large),
+//            times zeta_N^{rs}, written as Y_r[s];
+//   stage B  for every residue pair {c, q-c} (c = 0: the self-paired residues
+//            0 and q/2), the length-M DFTs of Y_r (Eq. forwardr), the RCM
+//            product (Eqs. Hr and Hr-conj) and the backward DFTs (Eq.
+//            accumulator), written as w_r[s];
+//   stage C  for every s, zeta_N^{-rs} w_r[s] and the backward q-point DFT
+//            over r (Eq. accumulation, the post-processing FFT of App. A),
+//            scaled by 1/N and unpacked to the real output of K samples.
+// Stages A and C run their q-point DFTs on the CTA-level Stockham engine
+// (hd_fft.cuh) over W consecutive s per CTA, so that each global access
+// covers W consecutive complex values; stage B runs the compile-time engine of
+// the cluster kernel (hd_cl_kernel.cuh) with one CTA per residue pair.  The
+// intermediates Y_f, Y_g and w (24 N bytes per item) live in the context's
+// workspace; batches run in chunks whose workspace stays under 1 GiB.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "hd_cl_kernel.cuh"
+#include "hd_conv1d.cuh"
+#include "hd_fft.cuh"
+#include "hd_internal.h"
+
+namespace hd {
+namespace staged {
+
+constexpr int kThreads = 256;                  // stages A and C
+constexpr int kPoints = kThreads * kPts;       // q-point DFT points per CTA (W q <= kPoints)
+constexpr int kMaxQ = 1024;
+constexpr int kR3[] = {2, 4, 8, 16, 18};       // stage-B residue lengths M = 256 R3
+constexpr int kLo = 64;                        // stage-B twiddles: zeta_N^{rs} = hi_r[s / 64] lo_r[s mod 64]
+#ifndef HD_STAGED_MINB
+#define HD_STAGED_MINB 4
+#endif
+constexpr int kMinB = HD_STAGED_MINB;          // resident CTAs per SM of stages A and C (structured engine)
+
+struct Geo {
+  int M, q, p;       // residue length, residues, input blocks
+  int W, ldb;        // s per CTA in stages A and C (a power of two), shared-memory stride of one s
+  int N;             // q M
+  int L, K;          // real input and output lengths
+  int64_t in_stride, out_stride;  // floats between items of f/g and of h
+};
+
+// The q-point DFTs of stages A and C on W arrays at stride ldb with the
+// zeta_q table: the structured engine (inlined passes) for its lengths, else
+// the plan-driven one.
+template <int SIGN, bool SE>
+__device__ __forceinline__ void q_dft(float2* buf, const Geo& G, const FftPlan& pq, const float2* __restrict__ tq) {
+  if constexpr (SE) cta_fft_struct<SIGN, kPts>(buf, G.ldb, G.W, G.q, tq, 1);
+  else cta_fft<SIGN, kPts>(buf, G.ldb, G.W, pq, tq, 1);
+}
+
+__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// Programmatic dependent launch between the stages: a stage lets the next one
+// be scheduled once all of its CTAs are running (launch_dependents), and the
+// next stage does its set-up (tables) before it waits for the previous grid to
+// complete and flush its writes (wait).  The wait returns when the previous
+// grid ends; it is not a spin on memory.
+__device__ __forceinline__ void allow_next_stage() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void wait_prev_stage() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Stages A and C move the W x q tile of a CTA between global memory (W
+// consecutive s of each row t or r: contiguous) and shared memory (one array
+// of q per s) in tasks of V consecutive s of one row: task id = tid + k
+// kThreads covers row id mod q and the s chunk id / q, so consecutive lanes
+// take consecutive rows (conflict-free shared accesses at any stride) and
+// each lane moves V complex values with 16-byte accesses.  Every load of a
+// loop is issued before the first store.
+
+// Stage A: grid (M / W, 2 inputs, items).  Y[item][which][r M + s] =
+// sum_{t < p} zeta_q^{rt} x~_{tM+s}: the q-point DFT over the blocks; the
+// pre-twiddle zeta_N^{rs} of Eq. forwardr is applied in stage B.
+template <bool SE, int V>
+__global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_a(const float* __restrict__ f, const float* __restrict__ g,
+                                                       float2* __restrict__ Y, Geo G, const float2* __restrict__ tq,
+                                                       FftPlan pq) {
+  constexpr int KT = kPts / V;  // tasks per thread (W q <= kPts kThreads)
+  extern __shared__ float4 smem_raw[];
+  float2* buf = reinterpret_cast<float2*>(smem_raw);  // buf[w ldb + t]
+  allow_next_stage();
+  const int which = blockIdx.y;
+  const float* x = (which ? g : f) + blockIdx.z * G.in_stride;
+  const int s0 = blockIdx.x * G.W;
+  const int q = G.q, M = G.M, ldb = G.ldb, nt = G.q * (G.W / V);
+  const DivF dq = make_div(q);
+  const bool vec = aligned16(x);
+  float2 v[KT][V];
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int id = threadIdx.x + k * kThreads;
+    const int wc = fdiv(id, dq), t = id - wc * q;
+#pragma unroll
+    for (int i = 0; i < V; ++i) v[k][i] = make_float2(0.f, 0.f);
+    if (id < nt && t < G.p) {
+      const int j0 = t * M + s0 + wc * V;  // packed index of the task's first value
+      const float* src = x + 2 * j0;
+      if (vec && 2 * (j0 + V) <= G.L) {
+#pragma unroll
+        for (int i = 0; i < V; i += 2) {
+          const float4 a = __ldg(reinterpret_cast<const float4*>(src) + i / 2);
+          v[k][i] = make_float2(a.x, a.y);
+          v[k][i + 1] = make_float2(a.z, a.w);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+          const int e = 2 * (j0 + i);
+          if (e < G.L) v[k][i].x = __ldg(src + 2 * i);
+          if (e + 1 < G.L) v[k][i].y = __ldg(src + 2 * i + 1);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int id = threadIdx.x + k * kThreads;
+    const int wc = fdiv(id, dq), t = id - wc * q;
+    if (id < nt) {
+#pragma unroll
+      for (int i = 0; i < V; ++i) buf[(wc * V + i) * ldb + t] = v[k][i];
+    }
+  }
+  __syncthreads();
+  q_dft<1, SE>(buf, G, pq, tq);
+  float2* Yw = Y + ((int64_t)blockIdx.z * 2 + which) * G.N;
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int id = threadIdx.x + k * kThreads;
+    const int wc = fdiv(id, dq), r = id - wc * q;
+    if (id < nt) {
+      float4* dst = reinterpret_cast<float4*>(Yw + r * M + s0 + wc * V);
+#pragma unroll
+      for (int i = 0; i < V; i += 2) {
+        const float2 a = buf[(wc * V + i) * ldb + r], b = buf[(wc * V + i + 1) * ldb + r];
+        dst[i / 2] = make_float4(a.x, a.y, b.x, b.y);
+      }
+    }
+  }
+}
+
+// Stage C: grid (M / W, items).  h~_{tM+s} = (1/N) sum_r zeta_q^{-rt} w'_r[s]
+// for the K output samples, where w'_r[s] = zeta_N^{-rs} w_r[s] comes from
+// stage B (same task mapping as stage A).
+template <bool SE, int V>
+__global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_c(const float2* __restrict__ Wr, float* __restrict__ h, Geo G,
+                                                       const float2* __restrict__ tq, FftPlan pq) {
+  constexpr int KT = kPts / V;
+  extern __shared__ float4 smem_raw[];
+  float2* buf = reinterpret_cast<float2*>(smem_raw);
+  const int s0 = blockIdx.x * G.W;
+  const int q = G.q, M = G.M, ldb = G.ldb, nt = G.q * (G.W / V);
+  const DivF dq = make_div(q);
+  const float2* Wi = Wr + (int64_t)blockIdx.z * G.N;
+  wait_prev_stage();
+  float2 v[KT][V];
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int id = threadIdx.x + k * kThreads;
+    const int wc = fdiv(id, dq), r = id - wc * q;
+    if (id < nt) {
+      const float4* src = reinterpret_cast<const float4*>(Wi + r * M + s0 + wc * V);
+#pragma unroll
+      for (int i = 0; i < V; i += 2) {
+        const float4 a = src[i / 2];
+        v[k][i] = make_float2(a.x, a.y);
+        v[k][i + 1] = make_float2(a.z, a.w);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int id = threadIdx.x + k * kThreads;
+    const int wc = fdiv(id, dq), r = id - wc * q;
+    if (id < nt) {
+#pragma unroll
+      for (int i = 0; i < V; ++i) buf[(wc * V + i) * ldb + r] = v[k][i];
+    }
+  }
+  __syncthreads();
+  q_dft<-1, SE>(buf, G, pq, tq);
+  const float sc = 1.0f / (float)G.N;
+  const int Kp = (G.K + 1) >> 1;
+  const int pout = (Kp + M - 1) / M;  // <= q since K <= 2L - 1 < 2N
+  float* hi = h + blockIdx.z * G.out_stride;
+  const bool vec = aligned16(hi);
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int id = threadIdx.x + k * kThreads;
+    const int wc = fdiv(id, dq), t = id - wc * q;
+    if (id < nt && t < pout) {
+      const int j0 = t * M + s0 + wc * V;
+      float* dst = hi + 2 * j0;
+      if (vec && 2 * (j0 + V) <= G.K) {
+#pragma unroll
+        for (int i = 0; i < V; i += 2) {
+          const float2 a = buf[(wc * V + i) * ldb + t], b = buf[(wc * V + i + 1) * ldb + t];
+          reinterpret_cast<float4*>(dst)[i / 2] = make_float4(a.x * sc, a.y * sc, b.x * sc, b.y * sc);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+          const int e = 2 * (j0 + i);
+          const float2 a = buf[(wc * V + i) * ldb + t];
+          if (e < G.K) dst[2 * i] = a.x * sc;
+          if (e + 1 < G.K) dst[2 * i + 1] = a.y * sc;
+        }
+      }
+    }
+  }
+}
+
+// Stage B: grid (q/2, items); CTA c holds residues c and q - c (c = 0:
+// residues 0 and q/2) of both inputs in the four arrays [F_a, F_b, G_a, G_b]
+// of the compile-time engine, in the same layout as one CTA of the cluster
+// kernel with C = q/2.  It applies the pre-twiddle zeta_N^{rs} of Eq.
+// forwardr on the way in and the post-twiddle zeta_N^{-rs} of Eq.
+// accumulation on the way out, from two small tables per residue in shared
+// memory (zeta_N^{rs} = zeta_N^{64 r (s / 64)} zeta_N^{r (s mod 64)}, both
+// entries rounded once from FP64), and writes w'_c and w'_{q-c}.
+template <int R3>
+struct StageB {
+  static constexpr int M = cl::Shape<R3>::M;
+  static constexpr int NX = kLo + M / kLo;  // split-twiddle entries per residue
+  static constexpr size_t SMEM = cl::Shape<R3>::SMEM + sizeof(float2) * 2 * NX;
+};
+
+template <int R3>
+__device__ __forceinline__ float2 split_tw(const float2* tx, int s) {
+  return cmul(tx[kLo + s / kLo], tx[s % kLo]);
+}
+
+template <int R3>
+__global__ void __launch_bounds__(cl::Shape<R3>::T, cl::Shape<R3>::MINB)
+    k_stage_b(const float2* __restrict__ Y, float2* __restrict__ Wr, Geo G, const float2* __restrict__ tw,
+              const float2* __restrict__ tab) {
+  using K = cl::Steps<1, R3>;
+  using S = cl::Shape<R3>;
+  constexpr int M = S::M, T = S::T, NX = StageB<R3>::NX;
+  extern __shared__ float4 smem_raw[];
+  float2* arr = reinterpret_cast<float2*>(smem_raw);
+  float2* tws = arr + 4 * M;
+  float2* tx = tws + S::TABS;  // [lo_a | hi_a | lo_b | hi_b]
+  const int tid = threadIdx.x;
+  const int c = blockIdx.x, q = G.q;
+  const int rb = (c == 0) ? q / 2 : q - c;
+  for (int i = tid; i < S::TABS / 2; i += T) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(tws + 2 * i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(tab + 2 * i) : "memory");
+  }
+  for (int i = tid; i < 2 * NX; i += T) {
+    const int rr = i < NX ? c : rb, u = i < NX ? i : i - NX;
+    tx[i] = __ldg(tw + (u < kLo ? rr * u : rr * kLo * (u - kLo)));  // < r M <= N
+  }
+  allow_next_stage();
+  wait_prev_stage();
+  const float2* YF = Y + (int64_t)blockIdx.z * 2 * G.N;
+  const float2* YG = YF + G.N;
+  float2* Wi = Wr + (int64_t)blockIdx.z * G.N;
+  {
+    constexpr int U = M / 2 / T;  // 4: all sixteen loads in flight before the first store
+    const float2* src[4] = {YF + c * M, YF + rb * M, YG + c * M, YG + rb * M};
+    float4 v[4][U];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < U; ++i) v[a][i] = cl::ldg4(src[a] + 2 * (tid + i * T));
+    __syncthreads();  // split twiddles
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int s = 2 * (tid + i * T);
+        const float2* t = tx + (a & 1) * NX;
+        cl::sts4(arr + a * M + cl::phys(s), cmul(make_float2(v[a][i].x, v[a][i].y), split_tw<R3>(t, s)),
+                 cmul(make_float2(v[a][i].z, v[a][i].w), split_tw<R3>(t, s + 1)));
+      }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  K::template pass1<1, 4, 2>(arr, tid, tws);
+  __syncthreads();
+  K::template pass2<1, 4, 2>(arr, tid, tws);
+  __syncthreads();
+  K::template pass3<1, 4>(arr, tid);
+  __syncthreads();
+  {
+    float2* Fa = arr;
+    float2* Fb = arr + M;
+    float2* Ga = arr + 2 * M;
+    float2* Gb = arr + 3 * M;
+    const float2* zt = tab + S::TABZ;  // zeta_M^{P^-1(p)}
+    if (c > 0) {
+      // residue c at position p pairs with residue q - c at position M-1-p
+      const float2 zr = __ldg(tw + c);
+      for (int k = tid; k < M / 2; k += T) {
+        const int p = 2 * k, pp = M - 2 - p;
+        float2 A0, A1, B0, B1, C0, C1, D0, D1;
+        cl::lds4(Fa + cl::phys(p), A0, A1);
+        cl::lds4(Ga + cl::phys(p), B0, B1);
+        cl::lds4(Fb + cl::phys(pp), C1, C0);
+        cl::lds4(Gb + cl::phys(pp), D1, D0);
+        const float4 z = cl::ldg4(zt + p);
+        K::rcm_pair(A0, B0, C0, D0, K::rcm_factor(make_float2(z.x, z.y), zr), false);
+        K::rcm_pair(A1, B1, C1, D1, K::rcm_factor(make_float2(z.z, z.w), zr), false);
+        cl::sts4(Fa + cl::phys(p), A0, A1);
+        cl::sts4(Fb + cl::phys(pp), C1, C0);
+      }
+    } else {
+      // residue q/2: position p pairs with M-1-p of the same residue
+      const float2 zc = __ldg(tw + q / 2);
+      for (int k = tid; k < M / 4; k += T) {
+        const int p = 2 * k, pp = M - 2 - p;
+        float2 A0, A1, B0, B1, C0, C1, D0, D1;
+        cl::lds4(Fb + cl::phys(p), A0, A1);
+        cl::lds4(Gb + cl::phys(p), B0, B1);
+        cl::lds4(Fb + cl::phys(pp), C1, C0);
+        cl::lds4(Gb + cl::phys(pp), D1, D0);
+        const float4 z = cl::ldg4(zt + p);
+        K::rcm_pair(A0, B0, C0, D0, K::rcm_factor(make_float2(z.x, z.y), zc), false);
+        K::rcm_pair(A1, B1, C1, D1, K::rcm_factor(make_float2(z.z, z.w), zc), false);
+        cl::sts4(Fb + cl::phys(p), A0, A1);
+        cl::sts4(Fb + cl::phys(pp), C1, C0);
+      }
+      // residue 0: frequency l pairs with (M - l) mod M
+      for (int p = tid; p < M; p += T) {
+        const int l = cl::digit_freq(p, R3);
+        const int ls = (l == 0) ? 0 : M - l;
+        if (l > ls) continue;
+        const int ps = cl::digit_pos(ls, R3);
+        float2 A = Fa[cl::phys(p)], B = Ga[cl::phys(p)];
+        float2 Ac = Fa[cl::phys(ps)], Bc = Ga[cl::phys(ps)];
+        const bool self = (ls == l);
+        K::rcm_pair(A, B, Ac, Bc, K::rcm_factor(cl::ldg2(zt + p), make_float2(1.f, 0.f)), self);
+        Fa[cl::phys(p)] = A;
+        if (!self) Fa[cl::phys(ps)] = Ac;
+      }
+    }
+  }
+  __syncthreads();
+  K::template pass3<-1, 2>(arr, tid);
+  __syncthreads();
+  K::template pass2<-1, 2, 1>(arr, tid, tws);
+  __syncthreads();
+  K::template pass1<-1, 2, 1>(arr, tid, tws);
+  __syncthreads();
+  for (int k = tid; k < M / 2; k += T) {
+    const int s = 2 * k;
+    float2 a0, a1, b0, b1;
+    cl::lds4(arr + cl::phys(s), a0, a1);
+    cl::lds4(arr + M + cl::phys(s), b0, b1);
+    a0 = cmul(a0, cconj(split_tw<R3>(tx, s)));
+    a1 = cmul(a1, cconj(split_tw<R3>(tx, s + 1)));
+    b0 = cmul(b0, cconj(split_tw<R3>(tx + NX, s)));
+    b1 = cmul(b1, cconj(split_tw<R3>(tx + NX, s + 1)));
+    *reinterpret_cast<float4*>(Wi + c * M + s) = make_float4(a0.x, a0.y, a1.x, a1.y);
+    *reinterpret_cast<float4*>(Wi + rb * M + s) = make_float4(b0.x, b0.y, b1.x, b1.y);
+  }
+}
+
+// Launch of a stage that may start while the previous one drains (its
+// kernel waits for the previous grid before reading the previous output).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_after(void (*k)(KArgs...), dim3 grid, unsigned threads, size_t smem, cudaStream_t st,
+                                Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+template <int R3>
+static cudaError_t launch_b(dim3 grid, cudaStream_t st, const float2* Y, float2* Wr, const Geo& G, const float2* tw,
+                            const float2* tab) {
+  auto k = k_stage_b<R3>;
+  cudaError_t e = smem_optin((const void*)k, StageB<R3>::SMEM);
+  if (e != cudaSuccess) return e;
+  return launch_after(k, grid, cl::Shape<R3>::T, StageB<R3>::SMEM, st, Y, Wr, G, tw, tab);
+}
+
+static cudaError_t launch_b_any(int R3, dim3 grid, cudaStream_t st, const float2* Y, float2* Wr, const Geo& G,
+                                const float2* tw, const float2* tab) {
+  switch (R3) {
+    case 2: return launch_b<2>(grid, st, Y, Wr, G, tw, tab);
+    case 4: return launch_b<4>(grid, st, Y, Wr, G, tw, tab);
+    case 8: return launch_b<8>(grid, st, Y, Wr, G, tw, tab);
+    case 16: return launch_b<16>(grid, st, Y, Wr, G, tw, tab);
+    case 18: return launch_b<18>(grid, st, Y, Wr, G, tw, tab);
+  }
+  return cudaErrorInvalidValue;
+}
+
+static bool stage_b_length(int M) {
+  for (int r : kR3)
+    if (256 * r == M) return true;
+  return false;
+}
+
+// Largest power of two W <= min(kPoints / q, 256): the s per CTA of stages A and C.
+static int s_per_cta(int q) {
+  int w = 1;
+  while (2 * w * q <= kPoints && 2 * w <= 256) w *= 2;
+  return w;
+}
+
+}  // namespace staged
+
+// Planner of the staged path: the smallest stage-B length M = 256 R3 whose
+// residue count q (the smallest length {1, 3, 5, 9} x 2^a >= max(16, L / M),
+// which the structured engine transforms) is at most 512, else at most 1024;
+// false if L is beyond 1024 * 4608.
+bool staged_params(int64_t L, int* M, int* q) {
+  for (int cap : {512, staged::kMaxQ}) {
+    for (int r : staged::kR3) {
+      const int64_t mm = 256 * r;
+      const int64_t qq = ladder_ceil(std::max<int64_t>(16, (L + mm - 1) / mm));
+      if (qq <= cap) {
+        *M = (int)mm;
+        *q = (int)qq;
+        return true;
+      }
+    }
+  }
+  return false;
+}
+
+hd_status conv1d_staged(hd_ctx* c, const float* f, const float* g, float* h, int64_t L, int64_t K, int M, int q,
+                        int64_t batch, cudaStream_t st) {
+  using namespace staged;
+  if (K <= 0) K = L;
+  if (!stage_b_length(M)) return fail(HD_EINVAL, "staged path: M must be 512, 1024, 2048, 4096 or 4608");
+  if (q < 2 || q % 2 || q > kMaxQ) return fail(HD_EINVAL, "staged path: q must be even, 2 <= q <= 1024");
+  if ((int64_t)q * M < L) return fail(HD_EINVAL, "staged path needs q M >= L");
+  Geo G;
+  G.M = M;
+  G.q = q;
+  G.N = q * M;
+  G.p = (int)(((L + 1) / 2 + M - 1) / M);
+  G.W = s_per_cta(q);  // >= 4 for q <= 1024
+  const bool se = struct_length(q);
+  const bool v8 = G.W >= 8;
+  G.ldb = q;  // the structured engine keeps its swizzle inside whole 16-element blocks of each array
+  G.L = (int)L;
+  G.K = (int)K;
+  G.in_stride = L;
+  G.out_stride = K;
+  hd_status terr = HD_OK;
+  const float2* tw = c->tables.get(G.N, st, &terr);
+  if (!tw) return fail(terr, "twiddle table allocation failed");
+  const float2* tab = c->tables.get_pass_table(M, st, &terr);
+  if (!tab) return fail(terr, "pass table allocation failed");
+  const float2* tq = c->tables.get(q, st, &terr);
+  if (!tq) return fail(terr, "twiddle table allocation failed");
+  FftPlan pq;
+  if (!factor_radices(q, &pq)) return fail(HD_EINVAL, "bad residue count");
+  const size_t per_item = sizeof(float2) * 3 * (size_t)G.N;
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(batch, 65535),
+                                                                 ((int64_t)1 << 30) / (int64_t)per_item));
+  if (ensure_ws(c, per_item * (size_t)chunk, st) != HD_OK) return fail(HD_ENOMEM, "workspace allocation failed");
+  float2* Y = reinterpret_cast<float2*>(c->ws);  // [item][f, g][N]
+  const size_t smem_ac = sizeof(float2) * (size_t)G.W * G.ldb;
+  auto ka = se ? (v8 ? k_stage_a<true, 8> : k_stage_a<true, 4>) : (v8 ? k_stage_a<false, 8> : k_stage_a<false, 4>);
+  auto kc = se ? (v8 ? k_stage_c<true, 8> : k_stage_c<true, 4>) : (v8 ? k_stage_c<false, 8> : k_stage_c<false, 4>);
+  cudaError_t e = smem_optin((const void*)ka, smem_ac);
+  if (e == cudaSuccess) e = smem_optin((const void*)kc, smem_ac);
+  if (e != cudaSuccess) return cuda_fail(e, "shared memory opt-in");
+  for (int64_t b0 = 0; b0 < batch; b0 += chunk) {
+    const unsigned nb = (unsigned)std::min(chunk, batch - b0);
+    float2* Wr = Y + 2 * (int64_t)nb * G.N;  // [item][N]
+    const float* fi = f + b0 * L;
+    const float* gi = g + b0 * L;
+    float* hi = h + b0 * K;
+    ka<<<dim3(M / G.W, 2, nb), kThreads, smem_ac, st>>>(fi, gi, Y, G, tq, pq);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "staged path: stage A launch");
+    e = launch_b_any(M / 256, dim3(q / 2, 1, nb), st, Y, Wr, G, tw, tab);
+    if (e != cudaSuccess) return cuda_fail(e, "staged path: stage B launch");
+    e = launch_after(kc, dim3(M / G.W, 1, nb), kThreads, smem_ac, st, (const float2*)Wr, hi, G, tq, pq);
+    if (e != cudaSuccess) return cuda_fail(e, "staged path: stage C launch");
+  }
+  return HD_OK;
+}
+
+}  // namespace hd
