@@ -10,7 +10,8 @@ Two layers:
 * ``hdoracle.c`` (loaded through ctypes): the plain definition of the result.
   O1 ``direct_conv`` is direct FP64 summation, O1' ``direct_corr`` the adjoint
   correlation, O2 ``fft_conv`` an explicitly zero-padded radix-2 FFT
-  convolution written from scratch.
+  convolution written from scratch; ``direct_conv_multi``/``fft_conv_multi``
+  the same two for n >= 2 1D arrays of possibly different lengths.
 * ``steps.py``: an FP64 NumPy transcription of the paper's equations step by
   step (residue transforms, conjugate-symmetry cases, implicit packing, the RCM
   operator and its multidimensional form), used to pin intermediate quantities
@@ -41,6 +42,10 @@ def _load():
         lib.hd_direct_conv_points.restype = ctypes.c_int
         lib.hd_batch_conv1d.argtypes = [ctypes.c_int64, P, P, P, P, P, ctypes.c_int]
         lib.hd_batch_conv1d.restype = ctypes.c_int
+        for name in ("hd_direct_conv_multi", "hd_fft_conv_multi"):
+            fn = getattr(lib, name)
+            fn.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, P]
+            fn.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -124,3 +129,30 @@ def batch_conv1d(f, g, offsets, lengths, use_fft=True):
     if rc:
         raise ValueError(f"hd_batch_conv1d failed ({rc})")
     return h
+
+
+def _multi(name, xs, K):
+    xs = [np.ascontiguousarray(x, dtype=np.float64) for x in xs]
+    if len(xs) < 2 or any(x.ndim != 1 for x in xs):
+        raise ValueError("need n >= 2 one-dimensional arrays")
+    L = np.array([len(x) for x in xs], dtype=np.int64)
+    S = int(L.sum() - len(xs) + 1)
+    K = int(L.max()) if K is None else int(K)
+    ptrs = (ctypes.c_void_p * len(xs))(*[x.ctypes.data for x in xs])
+    h = np.empty(K, dtype=np.float64)
+    rc = getattr(_load(), name)(len(xs), _ptr(L), ptrs, K, _ptr(h))
+    if rc:
+        raise ValueError(f"{name} failed ({rc}); K must satisfy 1 <= K <= {S}")
+    return h
+
+
+def direct_conv_multi(xs, K=None):
+    """O1m: x^1 * ... * x^n (1D, lengths may differ), first K outputs
+    (default max L_i; K = sum L_i - n + 1 is the whole convolution), by
+    direct FP64 summation one array after the other."""
+    return _multi("hd_direct_conv_multi", xs, K)
+
+
+def fft_conv_multi(xs, K=None):
+    """O2m: the same through one zero-padded FP64 FFT of every array."""
+    return _multi("hd_fft_conv_multi", xs, K)

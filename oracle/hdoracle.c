@@ -18,6 +18,17 @@
  *                        complex FFT (own code), pointwise product, inverse,
  *                        crop.  Any padded length >= 2L-1 gives the same
  *                        linear convolution, so no mixed radix is needed.
+ *   O1m/O2m hd_direct_conv_multi / hd_fft_conv_multi
+ *                        1D convolution of n >= 2 arrays of possibly
+ *                        different lengths L_1..L_n (Sec. 4.1, convolutions
+ *                        of more than two arrays; Sec. 7, arrays of
+ *                        different sizes): h = x^1 * ... * x^n, whose
+ *                        support is S = sum L_i - n + 1 samples; the first K
+ *                        (1 <= K <= S) are returned.  O1m convolves directly,
+ *                        one array after the other, keeping the full
+ *                        intermediate result; O2m pads every array to one
+ *                        power of two >= S, multiplies the n spectra and
+ *                        inverts.
  *
  * Shapes: arrays are row-major with the last dimension contiguous.  The
  * input extents are L[0..d-1]; the output extents K[0..d-1] satisfy
@@ -259,4 +270,83 @@ int hd_batch_conv1d(int64_t n, const int64_t *off, const int64_t *Ls,
     bad |= rc;
   }
   return bad;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O1m / O2m: 1D convolution of n arrays of possibly different lengths.     */
+/* ------------------------------------------------------------------------ */
+
+static int64_t multi_support(int n, const int64_t *L) {
+  int64_t S = 1;
+  for (int i = 0; i < n; ++i) S += L[i] - 1;
+  return S;
+}
+
+int hd_direct_conv_multi(int n, const int64_t *L, const double *const *x, int64_t K, double *h) {
+  if (n < 2) return 1;
+  for (int i = 0; i < n; ++i)
+    if (L[i] < 1 || !x[i]) return 1;
+  const int64_t S = multi_support(n, L);
+  if (K < 1 || K > S) return 1;
+  double *acc = (double *)calloc((size_t)S, sizeof(double));
+  double *tmp = (double *)calloc((size_t)S, sizeof(double));
+  if (!acc || !tmp) {
+    free(acc);
+    free(tmp);
+    return 2;
+  }
+  /* acc = x^1; then acc <- acc * x^i (full linear convolution) for i >= 2 */
+  int64_t len = L[0];
+  memcpy(acc, x[0], sizeof(double) * (size_t)L[0]);
+  for (int i = 1; i < n; ++i) {
+    const int64_t out = len + L[i] - 1;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < out; ++k) {
+      double sum = 0.0;
+      const int64_t j0 = k - (L[i] - 1) > 0 ? k - (L[i] - 1) : 0;
+      const int64_t j1 = k < len - 1 ? k : len - 1;
+      for (int64_t j = j0; j <= j1; ++j) sum += acc[j] * x[i][k - j];
+      tmp[k] = sum;
+    }
+    memcpy(acc, tmp, sizeof(double) * (size_t)out);
+    len = out;
+  }
+  memcpy(h, acc, sizeof(double) * (size_t)K);
+  free(acc);
+  free(tmp);
+  return 0;
+}
+
+int hd_fft_conv_multi(int n, const int64_t *L, const double *const *x, int64_t K, double *h) {
+  if (n < 2) return 1;
+  for (int i = 0; i < n; ++i)
+    if (L[i] < 1 || !x[i]) return 1;
+  const int64_t S = multi_support(n, L);
+  if (K < 1 || K > S) return 1;
+  const int64_t P = next_pow2(S);
+  double *acc = (double *)calloc((size_t)(2 * P), sizeof(double));
+  double *X = (double *)calloc((size_t)(2 * P), sizeof(double));
+  if (!acc || !X) {
+    free(acc);
+    free(X);
+    return 2;
+  }
+  for (int64_t j = 0; j < L[0]; ++j) acc[2 * j] = x[0][j];
+  fft_pow2(acc, P, 1, +1);
+  for (int i = 1; i < n; ++i) {
+    memset(X, 0, sizeof(double) * (size_t)(2 * P));
+    for (int64_t j = 0; j < L[i]; ++j) X[2 * j] = x[i][j];
+    fft_pow2(X, P, 1, +1);
+    for (int64_t k = 0; k < P; ++k) {
+      const double ar = acc[2 * k], ai = acc[2 * k + 1];
+      const double br = X[2 * k], bi = X[2 * k + 1];
+      acc[2 * k] = ar * br - ai * bi;
+      acc[2 * k + 1] = ar * bi + ai * br;
+    }
+  }
+  fft_pow2(acc, P, 1, -1);
+  for (int64_t k = 0; k < K; ++k) h[k] = acc[2 * k] / (double)P;
+  free(acc);
+  free(X);
+  return 0;
 }

@@ -410,3 +410,80 @@ def test_planted_batch_offset_mistake_is_caught():
     assert not _check_batch(h_bad, f, g, off, Ls)
     h_off = oracle.batch_conv1d(f, g, off + 1, Ls, use_fft=True)  # every item one place late
     assert not _check_batch(h_off, f, g, off, Ls)
+
+
+# --- O1m / O2m: n >= 2 arrays of possibly different lengths (Sec. 4.1; Sec. 7) ---
+def _int_multi(rng, lengths):
+    return [rng.integers(-8, 9, L) for L in lengths]
+
+
+def _exact_multi(xs):
+    """Repeated exact int64 convolution (SciPy direct method, integer dtype)."""
+    acc = xs[0]
+    for x in xs[1:]:
+        acc = scipy.signal.convolve(acc, x, method="direct")
+    return acc
+
+
+def _multi_matches(h, xs_int, K):
+    return np.array_equal(h, _exact_multi(xs_int)[:K].astype(float))
+
+
+@pytest.mark.parametrize("lengths", [(37, 5), (5, 37), (1, 9), (4096, 64), (300, 300), (17, 1, 9), (64, 33, 7, 12)])
+def test_multi_integer_exact(lengths):
+    rng = np.random.default_rng(30 + sum(lengths))
+    xi = _int_multi(rng, lengths)
+    S = sum(lengths) - len(lengths) + 1
+    xs = [x.astype(float) for x in xi]
+    for K in (max(lengths), S):
+        assert _multi_matches(oracle.direct_conv_multi(xs, K), xi, K)
+        h2 = oracle.fft_conv_multi(xs, K)
+        assert np.abs(h2 - _exact_multi(xi)[:K]).max() < 1e-6
+    assert len(oracle.direct_conv_multi(xs)) == max(lengths)  # default K = max L_i
+
+
+def test_multi_three_geometric_closed_form():
+    """x^i_j = a_i^j: for k below every length, the sum over j1 + j2 + j3 = k of
+    a^j1 b^j2 c^j3 has the partial-fraction closed form sum_i a_i^{k+2} /
+    prod_{l != i} (a_i - a_l)."""
+    a, b, c = 0.9995, -0.999, 0.5
+    L = (300, 200, 250)
+    xs = [r ** np.arange(n, dtype=np.float64) for r, n in zip((a, b, c), L)]
+    k = np.arange(200, dtype=np.float64)
+    ref = (a ** (k + 2) / ((a - b) * (a - c)) + b ** (k + 2) / ((b - a) * (b - c)) +
+           c ** (k + 2) / ((c - a) * (c - b)))
+    for fn in (oracle.direct_conv_multi, oracle.fft_conv_multi):
+        assert rel_l2(fn(xs, 200), ref) < 1e-12
+
+
+def test_multi_delta_shifts():
+    rng = np.random.default_rng(33)
+    f = rng.standard_normal(50)
+    d3 = np.zeros(4)
+    d3[3] = 1.0
+    d5 = np.zeros(6)
+    d5[5] = 1.0
+    S = 50 + 4 + 6 - 2
+    ref = np.zeros(S)
+    ref[8:58] = f
+    for fn in (oracle.direct_conv_multi, oracle.fft_conv_multi):
+        assert np.abs(fn([d3, f, d5], S) - ref).max() < 1e-13
+
+
+def test_multi_rejects_bad_extent():
+    with pytest.raises(ValueError):
+        oracle.direct_conv_multi([np.ones(4), np.ones(3)], 7)  # support is 6
+    with pytest.raises(ValueError):
+        oracle.fft_conv_multi([np.ones(4)], 4)
+
+
+def test_planted_multi_reversed_operand_is_caught(monkeypatch):
+    """An oracle that read one array back to front (a transposed operand)
+    fails the integer pin."""
+    rng = np.random.default_rng(34)
+    xi = _int_multi(rng, (40, 7, 9))
+    xs = [x.astype(float) for x in xi]
+    orig = oracle._multi
+    monkeypatch.setattr(oracle, "_multi", lambda name, ys, K: orig(name, [ys[0], ys[1][::-1]] + list(ys[2:]), K))
+    S = 40 + 7 + 9 - 2
+    assert not _multi_matches(oracle.direct_conv_multi(xs, S), xi, S)
