@@ -137,6 +137,26 @@ hd_status hd_conv_batch(hd_ctx* ctx, hd_algo algo, hd_prec prec, int ndim, const
 hd_status hd_conv1d_staged(hd_ctx* ctx, int64_t L, int64_t K, int32_t M, int32_t q, int32_t batch, const float* f,
                            const float* g, float* h, void* stream);
 
+/* Convolution of n real 1D arrays of possibly different lengths on the same
+ * three kernels: h_k = (x^1 * x^2 * ... * x^n)_k for 0 <= k < K.
+ * n >= 3 is the implicitly packed convolution of more than two arrays
+ * (Sec. 4.1: R^1 = F^1, R^j = R^{j-1} RCM F^j by Eqs. Akn, Rnk and RnMk);
+ * unequal lengths (e.g. a long signal and a short kernel) follow Sec. 7: each
+ * array is folded over its own number of blocks p_i = ceil(ceil(L_i/2) / M),
+ * with M and q shared, so no array is padded to another's length.
+ *   x: HOST array of n DEVICE pointers, x[i] holding L[i] floats; L: host
+ *   array of n lengths (1 <= L_i <= 2^28); 2 <= n <= 16.
+ *   K: output length, 1 <= K <= S = sum L_i - n + 1 (S is the whole linear
+ *   convolution); K = 0 means max L_i.
+ *   M in {512, 1024, 2048, 4096, 4608}, q even, 2 <= q <= 1024, 2 q M >= S;
+ *   M = q = 0 lets the planner choose (HD_EUNSUPPORTED when S > 2 x 1024 x
+ *   4608).
+ *   h: DEVICE buffer of K floats; it may alias any input (every input is read
+ *   by the first kernel, h is written by the last).
+ * Scratch: 8 (n + 1) q M bytes.  Errors as hd_conv1d. */
+hd_status hd_conv1d_multi(hd_ctx* ctx, int32_t n, const float* const* x, const int64_t* L, int64_t K, int32_t M,
+                          int32_t q, float* h, void* stream);
+
 /* Batched 1D convolutions of uneven lengths.  A plan is built on the host
  * from HOST arrays: item i occupies floats [offsets[i], offsets[i] + L[i]) of
  * f, g and h (items must not overlap).  The planner picks (m, q) per length

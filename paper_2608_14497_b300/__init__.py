@@ -27,7 +27,8 @@ PRECS = {"fp32": HD_FP32, "split_bf16": HD_SPLIT_BF16}
 EXPORTS = ("hd_create", "hd_destroy", "hd_conv1d", "hd_conv2d", "hd_conv3d", "hd_batch_plan_create",
            "hd_batch_plan_destroy", "hd_conv1d_batched", "hd_conv_adjoint", "hd_plan", "hd_last_device_error",
            "hd_strerror", "hd_last_error_string", "hd_conv1d_rcm_noalloc",
-           "hd_tuning_table", "hd_batch_plan_launches", "hd_conv_batch", "hd_conv_ext", "hd_conv1d_staged")
+           "hd_tuning_table", "hd_batch_plan_launches", "hd_conv_batch", "hd_conv_ext", "hd_conv1d_staged",
+           "hd_conv1d_multi")
 
 
 class HDError(RuntimeError):
@@ -78,6 +79,7 @@ def load(build_if_missing=False):
         "hd_conv_batch": ([P, I, I, I, P, I32, P, P, P, P], I),
         "hd_conv_ext": ([P, I, I, I, P, P, P, P, P, DP, P], I),
         "hd_conv1d_staged": ([P, I64, I64, I32, I32, I32, P, P, P, P], I),
+        "hd_conv1d_multi": ([P, I32, P, P, I64, I32, I32, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -163,6 +165,13 @@ def hd_conv_batch(ctx, algo, prec, Ls, batch, f_ptr, g_ptr, h_ptr, stream=0):
 
 def hd_conv1d_staged(ctx, L, K, M, q, batch, f_ptr, g_ptr, h_ptr, stream=0):
     return load().hd_conv1d_staged(ctx, L, K, M, q, batch, f_ptr, g_ptr, h_ptr, stream)
+
+
+def hd_conv1d_multi(ctx, x_ptrs, Ls, K, M, q, h_ptr, stream=0):
+    n = len(x_ptrs)
+    xa = (ctypes.c_void_p * n)(*x_ptrs)
+    la = (ctypes.c_int64 * n)(*[int(v) for v in Ls])
+    return load().hd_conv1d_multi(ctx, n, xa, la, K, M, q, h_ptr, stream)
 
 
 def hd_conv_adjoint(ctx, algo, Ls, batch, gh_ptr, f_ptr, g_ptr, gf_ptr, gg_ptr, stream=0):
@@ -284,6 +293,27 @@ def conv_staged(f, g, M=0, q=0, out_extent=None, out=None):
     st = hd_conv1d_staged(context(f.device.index), L, K, M, q, batch, f.data_ptr(), g.data_ptr(), h.data_ptr(),
                           _stream_ptr())
     _check(st, "conv_staged")
+    return h
+
+
+def conv_multi(xs, out_extent=None, M=0, q=0, out=None):
+    """x^1 * ... * x^n for 1D float32 CUDA tensors of possibly different
+    lengths (hd_conv1d_multi); out_extent: K (default max L_i) or "full"."""
+    import torch
+    for i, x in enumerate(xs):
+        _check_tensor(x, f"xs[{i}]")
+        if x.dim() != 1:
+            raise ValueError("conv_multi takes 1D tensors")
+    Ls = [x.shape[0] for x in xs]
+    S = sum(Ls) - len(Ls) + 1
+    K = max(Ls) if out_extent is None else (S if out_extent == "full" else int(out_extent))
+    h = torch.empty(K, dtype=torch.float32, device=xs[0].device) if out is None else out
+    _check_tensor(h, "out")
+    if tuple(h.shape) != (K,):
+        raise ValueError("out must hold K floats")
+    st = hd_conv1d_multi(context(xs[0].device.index), [x.data_ptr() for x in xs], Ls, K, M, q, h.data_ptr(),
+                         _stream_ptr())
+    _check(st, "conv_multi")
     return h
 
 

@@ -355,6 +355,29 @@ hd_status hd_conv1d_staged(hd_ctx* c, int64_t L, int64_t K, int32_t M, int32_t q
   return conv1d_staged(c, f, g, h, L, K, Mx, qx, batch, (cudaStream_t)stream);
 }
 
+hd_status hd_conv1d_multi(hd_ctx* c, int32_t n, const float* const* x, const int64_t* L, int64_t K, int32_t M,
+                          int32_t q, float* h, void* stream) {
+  if (!c || !x || !L || !h) return fail(HD_EINVAL, "n-ary convolution: null argument");
+  if (n < 2 || n > 16) return fail(HD_EINVAL, "n-ary convolution: 2 <= n <= 16 arrays");
+  int64_t S = 1, Lmax = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!x[i]) return fail(HD_EINVAL, "n-ary convolution: null array");
+    if (L[i] < 1 || L[i] > ((int64_t)1 << 28)) return fail(HD_EINVAL, "n-ary convolution: L_i out of range");
+    S += L[i] - 1;
+    Lmax = L[i] > Lmax ? L[i] : Lmax;
+  }
+  if (K == 0) K = Lmax;
+  if (K < 1 || K > S) return fail(HD_EINVAL, "n-ary convolution: K must satisfy 1 <= K <= sum L_i - n + 1");
+  int Mx = M, qx = q;
+  if (M == 0 && q == 0) {
+    if (!staged_params((S + 1) / 2, &Mx, &qx)) return fail(HD_EUNSUPPORTED, "n-ary convolution: sum of lengths too large");
+  } else if (M <= 0 || q <= 0) {
+    return fail(HD_EINVAL, "n-ary convolution: give both M and q, or neither");
+  }
+  cudaSetDevice(c->device);
+  return conv1d_multi(c, n, x, L, K, Mx, qx, h, (cudaStream_t)stream);
+}
+
 hd_status hd_conv_ext(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const int64_t* L, const int64_t* K,
                       const float* f, const float* g, float* h, const hd_dim_params* prm, void* stream) {
   if (!c || !L || !f || !g || !h) return fail(HD_EINVAL, "null argument");

@@ -22,6 +22,16 @@
 // the cluster kernel (hd_cl_kernel.cuh) with one CTA per residue pair.  The
 // intermediates Y_f, Y_g and w (24 N bytes per item) live in the context's
 // workspace; batches run in chunks whose workspace stays under 1 GiB.
+//
+// The same three kernels convolve n >= 2 arrays x^1..x^n of different
+// lengths L_i (Sec. 4.1, convolutions of more than two arrays: R^1 = F^1,
+// R^j = R^{j-1} RCM F^j by Eqs. Akn, Rnk and RnMk, which are the binary RCM
+// product with R^{j-1} in place of F; Sec. 7, arrays of different sizes:
+// every array is folded over its own p_i = ceil(ceil(L_i/2) / M) blocks with
+// the shared (M, q)).  The convolution has S = sum L_i - n + 1 samples, so
+// 2 q M >= S dealiases every output.  Stage A transforms every array, stage B
+// multiplies the n spectra of a residue pair one after the other, stage C is
+// unchanged.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,12 +55,23 @@ constexpr int kLo = 64;                        // stage-B twiddles: zeta_N^{rs} 
 #endif
 constexpr int kMinB = HD_STAGED_MINB;          // resident CTAs per SM of stages A and C (structured engine)
 
+constexpr int kMaxIn = 16;                     // arrays of one n-ary convolution
+
 struct Geo {
-  int M, q, p;       // residue length, residues, input blocks
+  int M, q;          // residue length, residues
   int W, ldb;        // s per CTA in stages A and C (a power of two), shared-memory stride of one s
   int N;             // q M
-  int L, K;          // real input and output lengths
-  int64_t in_stride, out_stride;  // floats between items of f/g and of h
+  int K;             // real output length
+  int nin;           // arrays convolved (2 for f * g)
+  int64_t out_stride;  // floats between items of h
+};
+
+// The input arrays: x[i] holds items of L[i] floats back to back (batches of
+// the binary equal-length case); p[i] = ceil(ceil(L[i]/2) / M) blocks.
+struct Inputs {
+  const float* x[kMaxIn];
+  int L[kMaxIn];
+  int p[kMaxIn];
 };
 
 // The q-point DFTs of stages A and C on W arrays at stride ldb with the
@@ -80,19 +101,19 @@ __device__ __forceinline__ void wait_prev_stage() { asm volatile("griddepcontrol
 // each lane moves V complex values with 16-byte accesses.  Every load of a
 // loop is issued before the first store.
 
-// Stage A: grid (M / W, 2 inputs, items).  Y[item][which][r M + s] =
-// sum_{t < p} zeta_q^{rt} x~_{tM+s}: the q-point DFT over the blocks; the
+// Stage A: grid (M / W, n inputs, items).  Y[item][i][r M + s] =
+// sum_{t < p_i} zeta_q^{rt} x~^i_{tM+s}: the q-point DFT over the blocks; the
 // pre-twiddle zeta_N^{rs} of Eq. forwardr is applied in stage B.
 template <bool SE, int V>
-__global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_a(const float* __restrict__ f, const float* __restrict__ g,
-                                                       float2* __restrict__ Y, Geo G, const float2* __restrict__ tq,
-                                                       FftPlan pq) {
+__global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_a(const Inputs in, float2* __restrict__ Y, Geo G,
+                                                       const float2* __restrict__ tq, FftPlan pq) {
   constexpr int KT = kPts / V;  // tasks per thread (W q <= kPts kThreads)
   extern __shared__ float4 smem_raw[];
   float2* buf = reinterpret_cast<float2*>(smem_raw);  // buf[w ldb + t]
   allow_next_stage();
   const int which = blockIdx.y;
-  const float* x = (which ? g : f) + blockIdx.z * G.in_stride;
+  const int Li = in.L[which], pi = in.p[which];
+  const float* __restrict__ x = in.x[which] + (int64_t)blockIdx.z * Li;
   const int s0 = blockIdx.x * G.W;
   const int q = G.q, M = G.M, ldb = G.ldb, nt = G.q * (G.W / V);
   const DivF dq = make_div(q);
@@ -104,10 +125,10 @@ __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_a(const floa
     const int wc = fdiv(id, dq), t = id - wc * q;
 #pragma unroll
     for (int i = 0; i < V; ++i) v[k][i] = make_float2(0.f, 0.f);
-    if (id < nt && t < G.p) {
+    if (id < nt && t < pi) {
       const int j0 = t * M + s0 + wc * V;  // packed index of the task's first value
       const float* src = x + 2 * j0;
-      if (vec && 2 * (j0 + V) <= G.L) {
+      if (vec && 2 * (j0 + V) <= Li) {
 #pragma unroll
         for (int i = 0; i < V; i += 2) {
           const float4 a = __ldg(reinterpret_cast<const float4*>(src) + i / 2);
@@ -118,8 +139,8 @@ __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_a(const floa
 #pragma unroll
         for (int i = 0; i < V; ++i) {
           const int e = 2 * (j0 + i);
-          if (e < G.L) v[k][i].x = __ldg(src + 2 * i);
-          if (e + 1 < G.L) v[k][i].y = __ldg(src + 2 * i + 1);
+          if (e < Li) v[k][i].x = __ldg(src + 2 * i);
+          if (e + 1 < Li) v[k][i].y = __ldg(src + 2 * i + 1);
         }
       }
     }
@@ -135,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_a(const floa
   }
   __syncthreads();
   q_dft<1, SE>(buf, G, pq, tq);
-  float2* Yw = Y + ((int64_t)blockIdx.z * 2 + which) * G.N;
+  float2* Yw = Y + ((int64_t)blockIdx.z * G.nin + which) * G.N;
 #pragma unroll
   for (int k = 0; k < KT; ++k) {
     const int id = threadIdx.x + k * kThreads;
@@ -242,6 +263,89 @@ __device__ __forceinline__ float2 split_tw(const float2* tx, int s) {
   return cmul(tx[kLo + s / kLo], tx[s % kLo]);
 }
 
+// NA arrays of residues (c, rb, c, rb, ...) from Y into consecutive slots of
+// the engine's layout, times zeta_N^{rs}: all loads are issued before the
+// first store (SYNC: a barrier between them, for the twiddle tables).
+template <int R3, int NA, bool SYNC>
+__device__ __forceinline__ void load_twiddled(float2* dst, const float2* const (&src)[NA], const float2* tx, int tid) {
+  constexpr int M = cl::Shape<R3>::M, T = cl::Shape<R3>::T, NX = StageB<R3>::NX;
+  constexpr int U = M / 2 / T;  // 4
+  float4 v[NA][U];
+#pragma unroll
+  for (int a = 0; a < NA; ++a)
+#pragma unroll
+    for (int i = 0; i < U; ++i) v[a][i] = cl::ldg4(src[a] + 2 * (tid + i * T));
+  if constexpr (SYNC) __syncthreads();
+#pragma unroll
+  for (int a = 0; a < NA; ++a)
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const int s = 2 * (tid + i * T);
+      const float2* t = tx + (a & 1) * NX;
+      cl::sts4(dst + a * M + cl::phys(s), cmul(make_float2(v[a][i].x, v[a][i].y), split_tw<R3>(t, s)),
+               cmul(make_float2(v[a][i].z, v[a][i].w), split_tw<R3>(t, s + 1)));
+    }
+}
+
+// The RCM product of one residue pair on the digit-reversed spectra in the
+// slots [R_a, R_b, X_a, X_b]: R <- R RCM X (Eqs. Hr and Hr-conj; with R^{j-1}
+// and F^j, Eqs. Akn, Rnk and RnMk).  Residue c at position p pairs with
+// residue q - c at position M-1-p; for c = 0, residue q/2 pairs p with M-1-p
+// of itself and residue 0 pairs frequency l with (M - l) mod M.
+template <int R3>
+__device__ __forceinline__ void pair_product(float2* arr, int c, int q, const float2* __restrict__ tw,
+                                             const float2* __restrict__ zt, int tid) {
+  using K = cl::Steps<1, R3>;
+  constexpr int M = cl::Shape<R3>::M, T = cl::Shape<R3>::T;
+  float2* Fa = arr;
+  float2* Fb = arr + M;
+  float2* Ga = arr + 2 * M;
+  float2* Gb = arr + 3 * M;
+  if (c > 0) {
+    const float2 zr = __ldg(tw + c);
+    for (int k = tid; k < M / 2; k += T) {
+      const int p = 2 * k, pp = M - 2 - p;
+      float2 A0, A1, B0, B1, C0, C1, D0, D1;
+      cl::lds4(Fa + cl::phys(p), A0, A1);
+      cl::lds4(Ga + cl::phys(p), B0, B1);
+      cl::lds4(Fb + cl::phys(pp), C1, C0);
+      cl::lds4(Gb + cl::phys(pp), D1, D0);
+      const float4 z = cl::ldg4(zt + p);
+      K::rcm_pair(A0, B0, C0, D0, K::rcm_factor(make_float2(z.x, z.y), zr), false);
+      K::rcm_pair(A1, B1, C1, D1, K::rcm_factor(make_float2(z.z, z.w), zr), false);
+      cl::sts4(Fa + cl::phys(p), A0, A1);
+      cl::sts4(Fb + cl::phys(pp), C1, C0);
+    }
+  } else {
+    const float2 zc = __ldg(tw + q / 2);
+    for (int k = tid; k < M / 4; k += T) {
+      const int p = 2 * k, pp = M - 2 - p;
+      float2 A0, A1, B0, B1, C0, C1, D0, D1;
+      cl::lds4(Fb + cl::phys(p), A0, A1);
+      cl::lds4(Gb + cl::phys(p), B0, B1);
+      cl::lds4(Fb + cl::phys(pp), C1, C0);
+      cl::lds4(Gb + cl::phys(pp), D1, D0);
+      const float4 z = cl::ldg4(zt + p);
+      K::rcm_pair(A0, B0, C0, D0, K::rcm_factor(make_float2(z.x, z.y), zc), false);
+      K::rcm_pair(A1, B1, C1, D1, K::rcm_factor(make_float2(z.z, z.w), zc), false);
+      cl::sts4(Fb + cl::phys(p), A0, A1);
+      cl::sts4(Fb + cl::phys(pp), C1, C0);
+    }
+    for (int p = tid; p < M; p += T) {
+      const int l = cl::digit_freq(p, R3);
+      const int ls = (l == 0) ? 0 : M - l;
+      if (l > ls) continue;
+      const int ps = cl::digit_pos(ls, R3);
+      float2 A = Fa[cl::phys(p)], B = Ga[cl::phys(p)];
+      float2 Ac = Fa[cl::phys(ps)], Bc = Ga[cl::phys(ps)];
+      const bool self = (ls == l);
+      K::rcm_pair(A, B, Ac, Bc, K::rcm_factor(cl::ldg2(zt + p), make_float2(1.f, 0.f)), self);
+      Fa[cl::phys(p)] = A;
+      if (!self) Fa[cl::phys(ps)] = Ac;
+    }
+  }
+}
+
 template <int R3>
 __global__ void __launch_bounds__(cl::Shape<R3>::T, cl::Shape<R3>::MINB)
     k_stage_b(const float2* __restrict__ Y, float2* __restrict__ Wr, Geo G, const float2* __restrict__ tw,
@@ -256,6 +360,7 @@ __global__ void __launch_bounds__(cl::Shape<R3>::T, cl::Shape<R3>::MINB)
   const int tid = threadIdx.x;
   const int c = blockIdx.x, q = G.q;
   const int rb = (c == 0) ? q / 2 : q - c;
+  const float2* zt = tab + S::TABZ;  // zeta_M^{P^-1(p)}
   for (int i = tid; i < S::TABS / 2; i += T) {
     const unsigned dst = (unsigned)__cvta_generic_to_shared(tws + 2 * i);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(tab + 2 * i) : "memory");
@@ -266,27 +371,11 @@ __global__ void __launch_bounds__(cl::Shape<R3>::T, cl::Shape<R3>::MINB)
   }
   allow_next_stage();
   wait_prev_stage();
-  const float2* YF = Y + (int64_t)blockIdx.z * 2 * G.N;
-  const float2* YG = YF + G.N;
+  const float2* Y0 = Y + (int64_t)blockIdx.z * G.nin * G.N;
   float2* Wi = Wr + (int64_t)blockIdx.z * G.N;
   {
-    constexpr int U = M / 2 / T;  // 4: all sixteen loads in flight before the first store
-    const float2* src[4] = {YF + c * M, YF + rb * M, YG + c * M, YG + rb * M};
-    float4 v[4][U];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int i = 0; i < U; ++i) v[a][i] = cl::ldg4(src[a] + 2 * (tid + i * T));
-    __syncthreads();  // split twiddles
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int i = 0; i < U; ++i) {
-        const int s = 2 * (tid + i * T);
-        const float2* t = tx + (a & 1) * NX;
-        cl::sts4(arr + a * M + cl::phys(s), cmul(make_float2(v[a][i].x, v[a][i].y), split_tw<R3>(t, s)),
-                 cmul(make_float2(v[a][i].z, v[a][i].w), split_tw<R3>(t, s + 1)));
-      }
+    const float2* const src[4] = {Y0 + c * M, Y0 + rb * M, Y0 + G.N + c * M, Y0 + G.N + rb * M};
+    load_twiddled<R3, 4, true>(arr, src, tx, tid);
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
@@ -296,58 +385,21 @@ __global__ void __launch_bounds__(cl::Shape<R3>::T, cl::Shape<R3>::MINB)
   __syncthreads();
   K::template pass3<1, 4>(arr, tid);
   __syncthreads();
-  {
-    float2* Fa = arr;
-    float2* Fb = arr + M;
-    float2* Ga = arr + 2 * M;
-    float2* Gb = arr + 3 * M;
-    const float2* zt = tab + S::TABZ;  // zeta_M^{P^-1(p)}
-    if (c > 0) {
-      // residue c at position p pairs with residue q - c at position M-1-p
-      const float2 zr = __ldg(tw + c);
-      for (int k = tid; k < M / 2; k += T) {
-        const int p = 2 * k, pp = M - 2 - p;
-        float2 A0, A1, B0, B1, C0, C1, D0, D1;
-        cl::lds4(Fa + cl::phys(p), A0, A1);
-        cl::lds4(Ga + cl::phys(p), B0, B1);
-        cl::lds4(Fb + cl::phys(pp), C1, C0);
-        cl::lds4(Gb + cl::phys(pp), D1, D0);
-        const float4 z = cl::ldg4(zt + p);
-        K::rcm_pair(A0, B0, C0, D0, K::rcm_factor(make_float2(z.x, z.y), zr), false);
-        K::rcm_pair(A1, B1, C1, D1, K::rcm_factor(make_float2(z.z, z.w), zr), false);
-        cl::sts4(Fa + cl::phys(p), A0, A1);
-        cl::sts4(Fb + cl::phys(pp), C1, C0);
-      }
-    } else {
-      // residue q/2: position p pairs with M-1-p of the same residue
-      const float2 zc = __ldg(tw + q / 2);
-      for (int k = tid; k < M / 4; k += T) {
-        const int p = 2 * k, pp = M - 2 - p;
-        float2 A0, A1, B0, B1, C0, C1, D0, D1;
-        cl::lds4(Fb + cl::phys(p), A0, A1);
-        cl::lds4(Gb + cl::phys(p), B0, B1);
-        cl::lds4(Fb + cl::phys(pp), C1, C0);
-        cl::lds4(Gb + cl::phys(pp), D1, D0);
-        const float4 z = cl::ldg4(zt + p);
-        K::rcm_pair(A0, B0, C0, D0, K::rcm_factor(make_float2(z.x, z.y), zc), false);
-        K::rcm_pair(A1, B1, C1, D1, K::rcm_factor(make_float2(z.z, z.w), zc), false);
-        cl::sts4(Fb + cl::phys(p), A0, A1);
-        cl::sts4(Fb + cl::phys(pp), C1, C0);
-      }
-      // residue 0: frequency l pairs with (M - l) mod M
-      for (int p = tid; p < M; p += T) {
-        const int l = cl::digit_freq(p, R3);
-        const int ls = (l == 0) ? 0 : M - l;
-        if (l > ls) continue;
-        const int ps = cl::digit_pos(ls, R3);
-        float2 A = Fa[cl::phys(p)], B = Ga[cl::phys(p)];
-        float2 Ac = Fa[cl::phys(ps)], Bc = Ga[cl::phys(ps)];
-        const bool self = (ls == l);
-        K::rcm_pair(A, B, Ac, Bc, K::rcm_factor(cl::ldg2(zt + p), make_float2(1.f, 0.f)), self);
-        Fa[cl::phys(p)] = A;
-        if (!self) Fa[cl::phys(ps)] = Ac;
-      }
-    }
+  pair_product<R3>(arr, c, q, tw, zt, tid);
+  // arrays 3..n: R^j = R^{j-1} RCM F^j with F^j in the second pair of slots
+  for (int i = 2; i < G.nin; ++i) {
+    __syncthreads();
+    const float2* Yi = Y0 + (int64_t)i * G.N;
+    const float2* const src[2] = {Yi + c * M, Yi + rb * M};
+    load_twiddled<R3, 2, false>(arr + 2 * M, src, tx, tid);
+    __syncthreads();
+    K::template pass1<1, 2, 2>(arr + 2 * M, tid, tws);
+    __syncthreads();
+    K::template pass2<1, 2, 2>(arr + 2 * M, tid, tws);
+    __syncthreads();
+    K::template pass3<1, 2>(arr + 2 * M, tid);
+    __syncthreads();
+    pair_product<R3>(arr, c, q, tw, zt, tid);
   }
   __syncthreads();
   K::template pass3<-1, 2>(arr, tid);
@@ -443,26 +495,29 @@ bool staged_params(int64_t L, int* M, int* q) {
   return false;
 }
 
-hd_status conv1d_staged(hd_ctx* c, const float* f, const float* g, float* h, int64_t L, int64_t K, int M, int q,
-                        int64_t batch, cudaStream_t st) {
-  using namespace staged;
-  if (K <= 0) K = L;
+namespace staged {
+
+// The three stages for `batch` items (n arrays each, item b of array i at
+// in.x[i] + b L_i, output item b at h + b K); S = sum L_i - n + 1 <= 2 q M.
+static hd_status run(hd_ctx* c, Inputs in, int nin, float* h, int64_t K, int M, int q, int64_t batch,
+                     cudaStream_t st) {
+  int64_t S = 1;
+  for (int i = 0; i < nin; ++i) S += in.L[i] - 1;
   if (!stage_b_length(M)) return fail(HD_EINVAL, "staged path: M must be 512, 1024, 2048, 4096 or 4608");
   if (q < 2 || q % 2 || q > kMaxQ) return fail(HD_EINVAL, "staged path: q must be even, 2 <= q <= 1024");
-  if ((int64_t)q * M < L) return fail(HD_EINVAL, "staged path needs q M >= L");
+  if (2 * (int64_t)q * M < S) return fail(HD_EINVAL, "staged path needs 2 q M >= sum L_i - n + 1 (q M >= L for two arrays of length L)");
   Geo G;
   G.M = M;
   G.q = q;
   G.N = q * M;
-  G.p = (int)(((L + 1) / 2 + M - 1) / M);
   G.W = s_per_cta(q);  // >= 4 for q <= 1024
   const bool se = struct_length(q);
   const bool v8 = G.W >= 8;
   G.ldb = q;  // the structured engine keeps its swizzle inside whole 16-element blocks of each array
-  G.L = (int)L;
   G.K = (int)K;
-  G.in_stride = L;
+  G.nin = nin;
   G.out_stride = K;
+  for (int i = 0; i < nin; ++i) in.p[i] = (int)(((int64_t)(in.L[i] + 1) / 2 + M - 1) / M);
   hd_status terr = HD_OK;
   const float2* tw = c->tables.get(G.N, st, &terr);
   if (!tw) return fail(terr, "twiddle table allocation failed");
@@ -472,11 +527,11 @@ hd_status conv1d_staged(hd_ctx* c, const float* f, const float* g, float* h, int
   if (!tq) return fail(terr, "twiddle table allocation failed");
   FftPlan pq;
   if (!factor_radices(q, &pq)) return fail(HD_EINVAL, "bad residue count");
-  const size_t per_item = sizeof(float2) * 3 * (size_t)G.N;
+  const size_t per_item = sizeof(float2) * (size_t)(nin + 1) * (size_t)G.N;
   const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(batch, 65535),
                                                                  ((int64_t)1 << 30) / (int64_t)per_item));
   if (ensure_ws(c, per_item * (size_t)chunk, st) != HD_OK) return fail(HD_ENOMEM, "workspace allocation failed");
-  float2* Y = reinterpret_cast<float2*>(c->ws);  // [item][f, g][N]
+  float2* Y = reinterpret_cast<float2*>(c->ws);  // [item][array][N]
   const size_t smem_ac = sizeof(float2) * (size_t)G.W * G.ldb;
   auto ka = se ? (v8 ? k_stage_a<true, 8> : k_stage_a<true, 4>) : (v8 ? k_stage_a<false, 8> : k_stage_a<false, 4>);
   auto kc = se ? (v8 ? k_stage_c<true, 8> : k_stage_c<true, 4>) : (v8 ? k_stage_c<false, 8> : k_stage_c<false, 4>);
@@ -485,11 +540,11 @@ hd_status conv1d_staged(hd_ctx* c, const float* f, const float* g, float* h, int
   if (e != cudaSuccess) return cuda_fail(e, "shared memory opt-in");
   for (int64_t b0 = 0; b0 < batch; b0 += chunk) {
     const unsigned nb = (unsigned)std::min(chunk, batch - b0);
-    float2* Wr = Y + 2 * (int64_t)nb * G.N;  // [item][N]
-    const float* fi = f + b0 * L;
-    const float* gi = g + b0 * L;
+    float2* Wr = Y + (int64_t)nin * nb * G.N;  // [item][N]
+    Inputs ic = in;
+    for (int i = 0; i < nin; ++i) ic.x[i] = in.x[i] + b0 * in.L[i];
     float* hi = h + b0 * K;
-    ka<<<dim3(M / G.W, 2, nb), kThreads, smem_ac, st>>>(fi, gi, Y, G, tq, pq);
+    ka<<<dim3(M / G.W, nin, nb), kThreads, smem_ac, st>>>(ic, Y, G, tq, pq);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "staged path: stage A launch");
     e = launch_b_any(M / 256, dim3(q / 2, 1, nb), st, Y, Wr, G, tw, tab);
     if (e != cudaSuccess) return cuda_fail(e, "staged path: stage B launch");
@@ -497,6 +552,28 @@ hd_status conv1d_staged(hd_ctx* c, const float* f, const float* g, float* h, int
     if (e != cudaSuccess) return cuda_fail(e, "staged path: stage C launch");
   }
   return HD_OK;
+}
+
+}  // namespace staged
+
+hd_status conv1d_staged(hd_ctx* c, const float* f, const float* g, float* h, int64_t L, int64_t K, int M, int q,
+                        int64_t batch, cudaStream_t st) {
+  staged::Inputs in = {};
+  in.x[0] = f;
+  in.x[1] = g;
+  in.L[0] = in.L[1] = (int)L;
+  return staged::run(c, in, 2, h, K > 0 ? K : L, M, q, batch, st);
+}
+
+hd_status conv1d_multi(hd_ctx* c, int n, const float* const* x, const int64_t* L, int64_t K, int M, int q,
+                       float* h, cudaStream_t st) {
+  if (n < 2 || n > staged::kMaxIn) return fail(HD_EINVAL, "n-ary convolution: 2 <= n <= 16 arrays");
+  staged::Inputs in = {};
+  for (int i = 0; i < n; ++i) {
+    in.x[i] = x[i];
+    in.L[i] = (int)L[i];
+  }
+  return staged::run(c, in, n, h, K, M, q, 1, st);
 }
 
 }  // namespace hd
