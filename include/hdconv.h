@@ -24,6 +24,15 @@
  *                    block with no block skipped.
  *   HD_HYBRID_CS     hybrid dealiasing with conjugate symmetries (Sec. 3).
  *   HD_HYBRID_RCM    hybrid dealiasing with implicit packing (Sec. 4).
+ *   HD_HYBRID_CSRCM  the combination Sec. 6.3 proposes: the residues of
+ *                    hybridCS, with residue 0 computed by implicit packing
+ *                    (packed length-m/2 DFTs multiplied by the RCM operator,
+ *                    Eq. RCM, with no unpack/pack step) and residue q/2 by
+ *                    the implicitly packed half-length transform of Eqs.
+ *                    forwardq2/accumulateq2, so every residue is computed on
+ *                    its own (no r, q-r pairing).  1D only (single calls,
+ *                    hd_conv_ext and batched plans); parameters and planner
+ *                    as HD_HYBRID_CS.
  *
  * Memory: every array argument of a compute call is a DEVICE pointer owned
  * by the caller (row-major, last dimension contiguous, FP32).  h may equal f
@@ -67,7 +76,13 @@ typedef enum {
   HD_EUNSUPPORTED = 5
 } hd_status;
 
-typedef enum { HD_EXPLICIT = 0, HD_EXPLICIT_RCM = 1, HD_HYBRID_CS = 2, HD_HYBRID_RCM = 3 } hd_algo;
+typedef enum {
+  HD_EXPLICIT = 0,
+  HD_EXPLICIT_RCM = 1,
+  HD_HYBRID_CS = 2,
+  HD_HYBRID_RCM = 3,
+  HD_HYBRID_CSRCM = 4 /* combined CS+RCM (1D): see the algorithm list above */
+} hd_algo;
 
 /* Arithmetic of the DFT stages.  HD_FP32 everywhere; HD_SPLIT_BF16 runs the
  * radix-16 stages of the 3D path on tensor cores with hi/lo bfloat16 operands

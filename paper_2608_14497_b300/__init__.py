@@ -16,11 +16,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhdconv.so")
 
 HD_OK, HD_EINVAL, HD_ENOMEM, HD_ECUDA, HD_ETIMEOUT, HD_EUNSUPPORTED = range(6)
-HD_EXPLICIT, HD_EXPLICIT_RCM, HD_HYBRID_CS, HD_HYBRID_RCM = range(4)
+HD_EXPLICIT, HD_EXPLICIT_RCM, HD_HYBRID_CS, HD_HYBRID_RCM, HD_HYBRID_CSRCM = range(5)
 HD_FP32, HD_SPLIT_BF16 = range(2)
 
 ALGOS = {"explicit": HD_EXPLICIT, "explicitRCM": HD_EXPLICIT_RCM, "hybridCS": HD_HYBRID_CS,
-         "hybridRCM": HD_HYBRID_RCM}
+         "hybridRCM": HD_HYBRID_RCM, "hybridCSRCM": HD_HYBRID_CSRCM}
 PRECS = {"fp32": HD_FP32, "split_bf16": HD_SPLIT_BF16}
 
 # Every symbol include/hdconv.h declares.
@@ -369,7 +369,8 @@ def hd_conv_fn(f, g, algo="hybridRCM"):
 
 class BatchPlan:
     """Host-built plan of many 1D convolutions of uneven lengths on flat arrays
-    (algo: hybridRCM, hybridCS, or explicitRCM, the explicit-padding baseline)."""
+    (algo: hybridRCM, hybridCS, hybridCSRCM, or explicitRCM, the explicit-padding
+    baseline)."""
 
     def __init__(self, offsets, lengths, algo="hybridRCM", device=None):
         self.ctx = context(device)

@@ -204,7 +204,7 @@ static hd_status conv1d_hybrid(hd_ctx* c, hd_algo algo, const float* f, const fl
     la.one.gacc = c->ws;
   }
   cudaError_t e = (algo == HD_HYBRID_RCM) ? launch_rcm1d(la, 1, P.threads, P.smem, f, g, h, st)
-                                          : launch_cs1d(la, 1, P.threads, P.smem, f, g, h, st);
+                                          : launch_cs1d(la, 1, P.threads, P.smem, f, g, h, st, algo == HD_HYBRID_CSRCM);
   if (e != cudaSuccess) return cuda_fail(e, "conv1d launch");
   return HD_OK;
 }
@@ -287,7 +287,8 @@ hd_status hd_plan(hd_ctx* c, hd_algo algo, int64_t L, hd_dim_params* out) {
       s = resolve_rcm1d(c, L, nullptr, &P);
       break;
     }
-    case HD_HYBRID_CS: s = resolve_cs1d(c, L, nullptr, &P); break;
+    case HD_HYBRID_CS:
+    case HD_HYBRID_CSRCM: s = resolve_cs1d(c, L, nullptr, &P); break;
     default: return fail(HD_EINVAL, "hd_plan: hybrid algorithms only");
   }
   if (s != HD_OK) return s;
@@ -406,7 +407,8 @@ hd_status hd_conv_ext(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const int
   if (prec != HD_FP32) return fail(HD_EUNSUPPORTED, "1D path is FP32 only");
   switch (algo) {
     case HD_HYBRID_RCM:
-    case HD_HYBRID_CS: return conv1d_hybrid(c, algo, f, g, h, L0, prm, st, K0);
+    case HD_HYBRID_CS:
+    case HD_HYBRID_CSRCM: return conv1d_hybrid(c, algo, f, g, h, L0, prm, st, K0);
     case HD_EXPLICIT_RCM: {
       int C, m, p;
       if (cluster_params(L0, &C, &m, &p) && C <= 8) return conv1d_explicit_cluster(c, f, g, h, L0, C, m, p, st, 1, K0);

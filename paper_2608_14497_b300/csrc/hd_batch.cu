@@ -70,7 +70,8 @@ using namespace hd;
 extern "C" hd_status hd_batch_plan_create(hd_ctx* c, hd_algo algo, int32_t n, const int64_t* offsets,
                                           const int32_t* Ls, hd_batch_plan** out) {
   if (!c || !offsets || !Ls || !out || n < 1) return HD_EINVAL;
-  if (algo != HD_HYBRID_RCM && algo != HD_HYBRID_CS && algo != HD_EXPLICIT_RCM) return HD_EUNSUPPORTED;
+  if (algo != HD_HYBRID_RCM && algo != HD_HYBRID_CS && algo != HD_HYBRID_CSRCM && algo != HD_EXPLICIT_RCM)
+    return HD_EUNSUPPORTED;
   const bool exp = (algo == HD_EXPLICIT_RCM);
   cudaSetDevice(c->device);
   struct HostItem {
@@ -318,7 +319,8 @@ extern "C" hd_status hd_conv1d_batched(hd_ctx* c, const hd_batch_plan* bp, const
     la.items = bp->d_items + lc.first;
     la.plans = bp->d_plans;
     cudaError_t e = (bp->algo == HD_HYBRID_RCM) ? launch_rcm1d(la, lc.count, lc.threads, lc.smem, f, g, h, st)
-                                                : launch_cs1d(la, lc.count, lc.threads, lc.smem, f, g, h, st);
+                                                : launch_cs1d(la, lc.count, lc.threads, lc.smem, f, g, h, st,
+                                                              bp->algo == HD_HYBRID_CSRCM);
     if (e != cudaSuccess) return HD_ECUDA;
   }
   return HD_OK;

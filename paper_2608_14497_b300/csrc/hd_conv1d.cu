@@ -15,6 +15,13 @@
 //            1..ceil(q/2)-1 by complex DFTs with 2 Re accumulation, residue
 //            q/2 by the half-length packing of Eqs. forwardq2, wb and
 //            accumulateq2; Eq. real-accumulation combines them.
+//            RCM0 = true is the combined CS+RCM form of Sec. 6.3: residue 0
+//            keeps the packed length-m/2 DFTs but multiplies the packed
+//            spectra with the RCM operator (Eq. RCM of packed length m/2)
+//            instead of unpacking, multiplying and packing again; residue
+//            q/2 is already an implicitly packed half-length transform whose
+//            even-index products need no partner (Eq. realq2symmetry), so
+//            every residue is computed on its own.
 //
 // All arithmetic is FP32 with FP64-generated twiddle tables.  The accumulator
 // lives in shared memory, or in a global scratch area when it does not fit
@@ -121,7 +128,7 @@ __global__ void __launch_bounds__(1024) k_rcm1d(Launch1D la, const float* f, con
   }
 }
 
-template <int PTS>
+template <int PTS, bool RCM0>
 __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, const float* g, float* h) {
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
@@ -165,10 +172,25 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
       }
       __syncthreads();
       cta_fft<1, PTS>(buf, n2, 2, s_ph, tw, 2 * q);
-      // Eq. fourierUnpack for F and G, pointwise product, Eq. fourierPack;
-      // pairs (k, n2 - k) with Z_{n2} = Z_0 and zeta_m^k = tw[k q].
       float2* Z = buf;
       float2* Y = buf + n2;
+      if constexpr (RCM0) {
+        // Eq. RCM on the packed spectra (packed length n2): for the pair
+        // (k, kc = (n2 - k) mod n2), alpha = (Z_k - conj Z_kc)(Y_k - conj Y_kc)
+        // (1 + zeta_n2^k) / 4, Z_k <- Z_k Y_k - alpha, Z_kc <- Z_kc Y_kc - conj alpha
+        // (zeta_n2^k = zeta_m^{2k} = tw[2 k q]).
+        for (int k = tid; k <= n2 / 2; k += T) {
+          const int kc = (n2 - k) % n2;
+          const float2 zk = Z[k], zc = Z[kc], yk = Y[k], yc = Y[kc];
+          const float2 w = tw_get<1>(tw, 2 * k * q);
+          const float2 fac = make_float2(0.25f * (1.f + w.x), 0.25f * w.y);
+          const float2 alpha = cmul(cmul(csub(zk, cconj(zc)), csub(yk, cconj(yc))), fac);
+          Z[k] = csub(cmul(zk, yk), alpha);
+          if (kc != k) Z[kc] = csub(cmul(zc, yc), cconj(alpha));
+        }
+      } else {
+      // Eq. fourierUnpack for F and G, pointwise product, Eq. fourierPack;
+      // pairs (k, n2 - k) with Z_{n2} = Z_0 and zeta_m^k = tw[k q].
       for (int k = tid; k <= n2 / 2; k += T) {
         const int kc = n2 - k;
         const float2 zk = Z[k], zc = Z[kc % n2], yk = Y[k], yc = Y[kc % n2];
@@ -183,6 +205,7 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
         Z[k] = cscale(cadd(cadd(Hk, cconj(Hc)), cmul_i<1>(cmul(csub(Hk, cconj(Hc)), cconj(wk)))), 0.5f);
         if (kc < n2 && kc != k)
           Z[kc] = cscale(cadd(cadd(Hc, cconj(Hk)), cmul_i<1>(cmul(csub(Hc, cconj(Hk)), cconj(wc)))), 0.5f);
+      }
       }
       __syncthreads();
       cta_fft<-1, PTS>(buf, n2, 1, s_ph, tw, 2 * q);
@@ -311,10 +334,11 @@ cudaError_t launch_rcm1d(const Launch1D& la, int nitems, int threads, size_t sme
 }
 
 cudaError_t launch_cs1d(const Launch1D& la, int nitems, int threads, size_t smem, const float* f, const float* g,
-                        float* h, cudaStream_t st) {
-  cudaError_t e = allow_smem(k_cs1d<kPts>, smem);
+                        float* h, cudaStream_t st, bool rcm0) {
+  auto k = rcm0 ? k_cs1d<kPts, true> : k_cs1d<kPts, false>;
+  cudaError_t e = allow_smem(k, smem);
   if (e != cudaSuccess) return e;
-  k_cs1d<kPts><<<nitems, threads, smem, st>>>(la, f, g, h);
+  k<<<nitems, threads, smem, st>>>(la, f, g, h);
   return cudaGetLastError();
 }
 

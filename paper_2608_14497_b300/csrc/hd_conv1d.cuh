@@ -40,8 +40,9 @@ size_t cs1d_smem_bytes(int L, int m, bool gacc);
 int threads_for_points(int64_t points, int pts);
 cudaError_t launch_rcm1d(const Launch1D& la, int nitems, int threads, size_t smem, const float* f,
                          const float* g, float* h, cudaStream_t st);
+// rcm0: the combined CS+RCM form (residue 0 by the RCM operator on packed spectra)
 cudaError_t launch_cs1d(const Launch1D& la, int nitems, int threads, size_t smem, const float* f,
-                        const float* g, float* h, cudaStream_t st);
+                        const float* g, float* h, cudaStream_t st, bool rcm0 = false);
 
 // Three-kernel hybridRCM path (hd_staged.cu): planner (false beyond its range)
 // and the call for `batch` items of L floats (h: K floats per item).

@@ -590,6 +590,7 @@ hd_status conv_nd_ext(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, con
       return hybrid_cs_nd(c, d, L, prm, f, g, h, st);
     case HD_EXPLICIT:
     case HD_EXPLICIT_RCM: return explicit_nd(c, algo, d, L, f, g, h, st, K);
+    case HD_HYBRID_CSRCM: return fail(HD_EUNSUPPORTED, "hybridCSRCM is built for 1D");
   }
   return fail(HD_EINVAL, "unknown algorithm");
 }
