@@ -136,21 +136,27 @@ hd_status hd_conv_ext(hd_ctx* ctx, hd_algo algo, hd_prec prec, int ndim, const i
 hd_status hd_conv_batch(hd_ctx* ctx, hd_algo algo, hd_prec prec, int ndim, const int64_t* Ls, int32_t batch,
                         const float* f, const float* g, float* h, void* stream);
 
-/* hybridRCM in 1D through three kernels (Sec. 2; the block sums of Eq.
- * forwardr and the accumulation of Eq. accumulation as q-point DFTs over the
- * blocks, App. A): for q residues of length M, stage A transforms f and g over
- * the blocks for every s < M, stage B (one CTA per residue pair) runs the
- * length-M DFTs, the RCM product and the backward DFTs, stage C transforms
- * back over the residues and unpacks.  hd_conv1d, hd_conv_ext and
- * hd_conv_batch take this path for hybridRCM lengths beyond the cluster
- * kernel (L > 73728) when prm is NULL; this call runs it for any L.
- * `batch` items of L floats back to back in f and g, of K floats in h (K = 0
- * means K = L; L <= K <= 2L-1).  M in {512, 1024, 2048, 4096, 4608}, q even,
- * 2 <= q <= 1024, q M >= L; M = q = 0 lets the planner choose.  Scratch:
- * 24 q M bytes per item (batches run in chunks of at most 1 GiB).  h may alias
- * f or g only when K = L.  Errors as hd_conv1d. */
-hd_status hd_conv1d_staged(hd_ctx* ctx, int64_t L, int64_t K, int32_t M, int32_t q, int32_t batch, const float* f,
-                           const float* g, float* h, void* stream);
+/* 1D hybrid convolution through three kernels, for long lengths (the block
+ * sums of Eq. forwardr and the accumulation of Eqs. accumulation /
+ * real-accumulation as q-point DFTs over the blocks: the inner loop of App. A
+ * and of the complex case it cites): for q residues of length M, stage A
+ * transforms f and g over the blocks for every s < M, stage B (one CTA per
+ * residue pair for hybridRCM, per residue r <= q/2 for hybridCS) runs the
+ * length-M DFTs, the product (RCM, Eqs. Hr/Hr-conj; or pointwise) and the
+ * backward DFTs, stage C transforms back over the residues and unpacks
+ * (hybridRCM) or takes the real part (hybridCS, Eq. real-accumulation).
+ * hd_conv1d, hd_conv_ext and hd_conv_batch take this path when prm is NULL
+ * for hybridRCM lengths beyond the cluster kernel (L > 73728) and hybridCS
+ * lengths beyond one CTA (L > 8192); this call runs it for any L.
+ *   algo: HD_HYBRID_RCM (needs q M >= L) or HD_HYBRID_CS (needs q M >= 2L-1).
+ *   `batch` items of L floats back to back in f and g, of K floats in h
+ *   (K = 0 means K = L; L <= K <= 2L-1).  M in {512, 1024, 2048, 4096,
+ *   4608}, q even, 2 <= q <= 1024; M = q = 0 lets the planner choose.
+ * Scratch: 24 q M bytes per item (hybridRCM), 12 (q + 2) M (hybridCS); batches
+ * run in chunks of at most 1 GiB.  h may alias f or g only when K = L.
+ * Errors as hd_conv1d. */
+hd_status hd_conv1d_staged(hd_ctx* ctx, hd_algo algo, int64_t L, int64_t K, int32_t M, int32_t q, int32_t batch,
+                           const float* f, const float* g, float* h, void* stream);
 
 /* Convolution of n real 1D arrays of possibly different lengths on the same
  * three kernels: h_k = (x^1 * x^2 * ... * x^n)_k for 0 <= k < K.

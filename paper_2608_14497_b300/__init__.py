@@ -78,7 +78,7 @@ def load(build_if_missing=False):
         "hd_batch_plan_launches": ([P, P], I),
         "hd_conv_batch": ([P, I, I, I, P, I32, P, P, P, P], I),
         "hd_conv_ext": ([P, I, I, I, P, P, P, P, P, DP, P], I),
-        "hd_conv1d_staged": ([P, I64, I64, I32, I32, I32, P, P, P, P], I),
+        "hd_conv1d_staged": ([P, I, I64, I64, I32, I32, I32, P, P, P, P], I),
         "hd_conv1d_multi": ([P, I32, P, P, I64, I32, I32, P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -163,8 +163,8 @@ def hd_conv_batch(ctx, algo, prec, Ls, batch, f_ptr, g_ptr, h_ptr, stream=0):
     return load().hd_conv_batch(ctx, algo, prec, len(Ls), arr, batch, f_ptr, g_ptr, h_ptr, stream)
 
 
-def hd_conv1d_staged(ctx, L, K, M, q, batch, f_ptr, g_ptr, h_ptr, stream=0):
-    return load().hd_conv1d_staged(ctx, L, K, M, q, batch, f_ptr, g_ptr, h_ptr, stream)
+def hd_conv1d_staged(ctx, algo, L, K, M, q, batch, f_ptr, g_ptr, h_ptr, stream=0):
+    return load().hd_conv1d_staged(ctx, algo, L, K, M, q, batch, f_ptr, g_ptr, h_ptr, stream)
 
 
 def hd_conv1d_multi(ctx, x_ptrs, Ls, K, M, q, h_ptr, stream=0):
@@ -274,9 +274,10 @@ def conv_batch(f, g, ndim, algo="hybridRCM", out=None):
     return h
 
 
-def conv_staged(f, g, M=0, q=0, out_extent=None, out=None):
-    """hybridRCM in 1D through the three-kernel path (hd_conv1d_staged): f and
-    g of shape (L,) or (batch, L); (M, q) = (0, 0) lets the planner choose."""
+def conv_staged(f, g, M=0, q=0, out_extent=None, out=None, algo="hybridRCM"):
+    """hybridRCM or hybridCS in 1D through the three-kernel path
+    (hd_conv1d_staged): f and g of shape (L,) or (batch, L); (M, q) = (0, 0)
+    lets the planner choose."""
     import torch
     _check_tensor(f, "f")
     _check_tensor(g, "g")
@@ -290,8 +291,8 @@ def conv_staged(f, g, M=0, q=0, out_extent=None, out=None):
     _check_tensor(h, "out")
     if tuple(h.shape) != shape:
         raise ValueError("out must have the output extents")
-    st = hd_conv1d_staged(context(f.device.index), L, K, M, q, batch, f.data_ptr(), g.data_ptr(), h.data_ptr(),
-                          _stream_ptr())
+    st = hd_conv1d_staged(context(f.device.index), ALGOS[algo], L, K, M, q, batch, f.data_ptr(), g.data_ptr(),
+                          h.data_ptr(), _stream_ptr())
     _check(st, "conv_staged")
     return h
 

@@ -32,6 +32,10 @@ namespace hd {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// hybridCS lengths one CTA transforms with q = 2 (m <= 8192); longer ones run
+// the three-kernel path (App. A), unless the caller gives (m, q).
+constexpr int64_t kCsOneCta = 8192;
+
 static int64_t next_smooth_even(int64_t n) {
   int64_t m = next_smooth(n < 2 ? 2 : n);
   while (m % 2) m = next_smooth(m + 1);
@@ -179,6 +183,10 @@ static hd_status conv1d_hybrid(hd_ctx* c, hd_algo algo, const float* f, const fl
     int M, q;
     if (staged_params(L, &M, &q)) return conv1d_staged(c, f, g, h, L, K, M, q, 1, st);
   }
+  if (algo == HD_HYBRID_CS && !(prm && prm->m > 0) && L > kCsOneCta) {
+    int M, q;
+    if (staged_params(2 * L - 1, &M, &q)) return conv1d_staged(c, f, g, h, L, K, M, q, 1, st, true);
+  }
   Params1D P;
   hd_status s = (algo == HD_HYBRID_RCM) ? resolve_rcm1d(c, L, prm, &P, K) : resolve_cs1d(c, L, prm, &P, K);
   if (s != HD_OK) return s;
@@ -288,6 +296,16 @@ hd_status hd_plan(hd_ctx* c, hd_algo algo, int64_t L, hd_dim_params* out) {
       break;
     }
     case HD_HYBRID_CS:
+      if (L > kCsOneCta) {
+        int M, q;
+        if (staged_params(2 * L - 1, &M, &q)) {
+          out->m = M;
+          out->q = q;
+          return HD_OK;
+        }
+      }
+      s = resolve_cs1d(c, L, nullptr, &P);
+      break;
     case HD_HYBRID_CSRCM: s = resolve_cs1d(c, L, nullptr, &P); break;
     default: return fail(HD_EINVAL, "hd_plan: hybrid algorithms only");
   }
@@ -320,6 +338,11 @@ hd_status hd_conv_batch(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const i
     int M, q;
     if (staged_params(Ls[0], &M, &q)) return conv1d_staged(c, f, g, h, Ls[0], Ls[0], M, q, batch, st);
   }
+  if (prec == HD_FP32 && algo == HD_HYBRID_CS && ndim == 1 && Ls[0] > kCsOneCta) {
+    int M, q;
+    if (staged_params(2 * Ls[0] - 1, &M, &q))
+      return conv1d_staged(c, f, g, h, Ls[0], Ls[0], M, q, batch, st, true);
+  }
   if (prec == HD_FP32 && algo == HD_EXPLICIT_RCM && ndim == 1) {
     int C, m, p;
     if (batch < (1 << 24) && cluster_params(Ls[0], &C, &m, &p) && C <= 8)
@@ -337,9 +360,11 @@ hd_status hd_conv_batch(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const i
   return HD_OK;
 }
 
-hd_status hd_conv1d_staged(hd_ctx* c, int64_t L, int64_t K, int32_t M, int32_t q, int32_t batch, const float* f,
-                           const float* g, float* h, void* stream) {
+hd_status hd_conv1d_staged(hd_ctx* c, hd_algo algo, int64_t L, int64_t K, int32_t M, int32_t q, int32_t batch,
+                           const float* f, const float* g, float* h, void* stream) {
   if (!c || !f || !g || !h || batch < 1) return fail(HD_EINVAL, "staged path: null argument or batch < 1");
+  if (algo != HD_HYBRID_RCM && algo != HD_HYBRID_CS) return fail(HD_EINVAL, "staged path: hybridRCM or hybridCS");
+  const bool cs = (algo == HD_HYBRID_CS);
   if (L < 1 || L > ((int64_t)1 << 28)) return fail(HD_EINVAL, "staged path: L out of range");
   if (K == 0) K = L;
   if (K < L || K > 2 * L - 1) return fail(HD_EINVAL, "output extent K must satisfy L <= K <= 2L-1");
@@ -348,12 +373,12 @@ hd_status hd_conv1d_staged(hd_ctx* c, int64_t L, int64_t K, int32_t M, int32_t q
     return fail(HD_EINVAL, "h may alias f or g only when K = L");
   int Mx = M, qx = q;
   if (M == 0 && q == 0) {
-    if (!staged_params(L, &Mx, &qx)) return fail(HD_EUNSUPPORTED, "staged path: L beyond 1024 x 4608");
+    if (!staged_params(cs ? 2 * L - 1 : L, &Mx, &qx)) return fail(HD_EUNSUPPORTED, "staged path: L too large");
   } else if (M <= 0 || q <= 0) {
     return fail(HD_EINVAL, "staged path: give both M and q, or neither");
   }
   cudaSetDevice(c->device);
-  return conv1d_staged(c, f, g, h, L, K, Mx, qx, batch, (cudaStream_t)stream);
+  return conv1d_staged(c, f, g, h, L, K, Mx, qx, batch, (cudaStream_t)stream, cs);
 }
 
 hd_status hd_conv1d_multi(hd_ctx* c, int32_t n, const float* const* x, const int64_t* L, int64_t K, int32_t M,

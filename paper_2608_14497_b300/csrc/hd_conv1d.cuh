@@ -47,8 +47,9 @@ cudaError_t launch_cs1d(const Launch1D& la, int nitems, int threads, size_t smem
 // Three-kernel hybridRCM path (hd_staged.cu): planner (false beyond its range)
 // and the call for `batch` items of L floats (h: K floats per item).
 bool staged_params(int64_t L, int* M, int* q);
+// cs: hybridCS (real residues; needs q M >= 2L - 1) instead of hybridRCM (q M >= L).
 hd_status conv1d_staged(hd_ctx* c, const float* f, const float* g, float* h, int64_t L, int64_t K, int M, int q,
-                        int64_t batch, cudaStream_t st);
+                        int64_t batch, cudaStream_t st, bool cs = false);
 // n arrays x[i] of L[i] floats (2 <= n <= 16) through the same kernels.
 hd_status conv1d_multi(hd_ctx* c, int n, const float* const* x, const int64_t* L, int64_t K, int M, int q,
                        float* h, cudaStream_t st);

@@ -63,6 +63,7 @@ struct Geo {
   int N;             // q M
   int K;             // real output length
   int nin;           // arrays convolved (2 for f * g)
+  int rows;          // residues stored per array: q (hybridRCM), q/2 + 1 (hybridCS, Hermitian in r)
   int64_t out_stride;  // floats between items of h
 };
 
@@ -104,7 +105,9 @@ __device__ __forceinline__ void wait_prev_stage() { asm volatile("griddepcontrol
 // Stage A: grid (M / W, n inputs, items).  Y[item][i][r M + s] =
 // sum_{t < p_i} zeta_q^{rt} x~^i_{tM+s}: the q-point DFT over the blocks; the
 // pre-twiddle zeta_N^{rs} of Eq. forwardr is applied in stage B.
-template <bool SE, int V>
+// CS: real unpacked input (hybridCS, Sec. 3 with App. A), x_t[s] = f_{tM+s};
+// the DFT over t of real data is Hermitian in r, so rows r <= q/2 are kept.
+template <bool SE, int V, bool CS>
 __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_a(const Inputs in, float2* __restrict__ Y, Geo G,
                                                        const float2* __restrict__ tq, FftPlan pq) {
   constexpr int KT = kPts / V;  // tasks per thread (W q <= kPts kThreads)
@@ -125,7 +128,24 @@ __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_a(const Inpu
     const int wc = fdiv(id, dq), t = id - wc * q;
 #pragma unroll
     for (int i = 0; i < V; ++i) v[k][i] = make_float2(0.f, 0.f);
-    if (id < nt && t < pi) {
+    if (CS && id < nt && t < pi) {
+      const int j0 = t * M + s0 + wc * V;  // real index of the task's first value
+      const float* src = x + j0;
+      if (vec && j0 + V <= Li) {
+#pragma unroll
+        for (int i = 0; i < V; i += 4) {
+          const float4 a = __ldg(reinterpret_cast<const float4*>(src) + i / 4);
+          v[k][i].x = a.x;
+          v[k][i + 1].x = a.y;
+          v[k][i + 2].x = a.z;
+          v[k][i + 3].x = a.w;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+          if (j0 + i < Li) v[k][i].x = __ldg(src + i);
+      }
+    } else if (!CS && id < nt && t < pi) {
       const int j0 = t * M + s0 + wc * V;  // packed index of the task's first value
       const float* src = x + 2 * j0;
       if (vec && 2 * (j0 + V) <= Li) {
@@ -156,12 +176,12 @@ __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_a(const Inpu
   }
   __syncthreads();
   q_dft<1, SE>(buf, G, pq, tq);
-  float2* Yw = Y + ((int64_t)blockIdx.z * G.nin + which) * G.N;
+  float2* Yw = Y + ((int64_t)blockIdx.z * G.nin + which) * G.rows * M;
 #pragma unroll
   for (int k = 0; k < KT; ++k) {
     const int id = threadIdx.x + k * kThreads;
     const int wc = fdiv(id, dq), r = id - wc * q;
-    if (id < nt) {
+    if (id < nt && r < G.rows) {
       float4* dst = reinterpret_cast<float4*>(Yw + r * M + s0 + wc * V);
 #pragma unroll
       for (int i = 0; i < V; i += 2) {
@@ -175,7 +195,9 @@ __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_a(const Inpu
 // Stage C: grid (M / W, items).  h~_{tM+s} = (1/N) sum_r zeta_q^{-rt} w'_r[s]
 // for the K output samples, where w'_r[s] = zeta_N^{-rs} w_r[s] comes from
 // stage B (same task mapping as stage A).
-template <bool SE, int V>
+// CS: rows r > q/2 are the conjugates of rows q - r (Eq. hrHerm), and the
+// output is the real part, one real sample per (t, s) (Eq. real-accumulation).
+template <bool SE, int V, bool CS>
 __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_c(const float2* __restrict__ Wr, float* __restrict__ h, Geo G,
                                                        const float2* __restrict__ tq, FftPlan pq) {
   constexpr int KT = kPts / V;
@@ -184,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_c(const floa
   const int s0 = blockIdx.x * G.W;
   const int q = G.q, M = G.M, ldb = G.ldb, nt = G.q * (G.W / V);
   const DivF dq = make_div(q);
-  const float2* Wi = Wr + (int64_t)blockIdx.z * G.N;
+  const float2* Wi = Wr + (int64_t)blockIdx.z * G.rows * M;
   wait_prev_stage();
   float2 v[KT][V];
 #pragma unroll
@@ -192,12 +214,13 @@ __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_c(const floa
     const int id = threadIdx.x + k * kThreads;
     const int wc = fdiv(id, dq), r = id - wc * q;
     if (id < nt) {
-      const float4* src = reinterpret_cast<const float4*>(Wi + r * M + s0 + wc * V);
+      const bool mirror = CS && r >= G.rows;  // r > q/2: conj of row q - r
+      const float4* src = reinterpret_cast<const float4*>(Wi + (mirror ? q - r : r) * M + s0 + wc * V);
 #pragma unroll
       for (int i = 0; i < V; i += 2) {
         const float4 a = src[i / 2];
-        v[k][i] = make_float2(a.x, a.y);
-        v[k][i + 1] = make_float2(a.z, a.w);
+        v[k][i] = make_float2(a.x, mirror ? -a.y : a.y);
+        v[k][i + 1] = make_float2(a.z, mirror ? -a.w : a.w);
       }
     }
   }
@@ -213,10 +236,34 @@ __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_c(const floa
   __syncthreads();
   q_dft<-1, SE>(buf, G, pq, tq);
   const float sc = 1.0f / (float)G.N;
-  const int Kp = (G.K + 1) >> 1;
-  const int pout = (Kp + M - 1) / M;  // <= q since K <= 2L - 1 < 2N
   float* hi = h + blockIdx.z * G.out_stride;
   const bool vec = aligned16(hi);
+  if constexpr (CS) {
+    const int pout = (G.K + M - 1) / M;  // <= q since K <= N
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      const int id = threadIdx.x + k * kThreads;
+      const int wc = fdiv(id, dq), t = id - wc * q;
+      if (id < nt && t < pout) {
+        const int j0 = t * M + s0 + wc * V;
+        float* dst = hi + j0;
+        if (vec && j0 + V <= G.K) {
+#pragma unroll
+          for (int i = 0; i < V; i += 4)
+            reinterpret_cast<float4*>(dst)[i / 4] =
+                make_float4(buf[(wc * V + i) * ldb + t].x * sc, buf[(wc * V + i + 1) * ldb + t].x * sc,
+                            buf[(wc * V + i + 2) * ldb + t].x * sc, buf[(wc * V + i + 3) * ldb + t].x * sc);
+        } else {
+#pragma unroll
+          for (int i = 0; i < V; ++i)
+            if (j0 + i < G.K) dst[i] = buf[(wc * V + i) * ldb + t].x * sc;
+        }
+      }
+    }
+    return;
+  }
+  const int Kp = (G.K + 1) >> 1;
+  const int pout = (Kp + M - 1) / M;  // <= q since K <= 2L - 1 < 2N
 #pragma unroll
   for (int k = 0; k < KT; ++k) {
     const int id = threadIdx.x + k * kThreads;
@@ -266,7 +313,7 @@ __device__ __forceinline__ float2 split_tw(const float2* tx, int s) {
 // NA arrays of residues (c, rb, c, rb, ...) from Y into consecutive slots of
 // the engine's layout, times zeta_N^{rs}: all loads are issued before the
 // first store (SYNC: a barrier between them, for the twiddle tables).
-template <int R3, int NA, bool SYNC>
+template <int R3, int NA, bool SYNC, bool PAIRS = true>
 __device__ __forceinline__ void load_twiddled(float2* dst, const float2* const (&src)[NA], const float2* tx, int tid) {
   constexpr int M = cl::Shape<R3>::M, T = cl::Shape<R3>::T, NX = StageB<R3>::NX;
   constexpr int U = M / 2 / T;  // 4
@@ -281,7 +328,7 @@ __device__ __forceinline__ void load_twiddled(float2* dst, const float2* const (
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const int s = 2 * (tid + i * T);
-      const float2* t = tx + (a & 1) * NX;
+      const float2* t = tx + (PAIRS ? (a & 1) * NX : 0);  // PAIRS: slots alternate residues c, rb
       cl::sts4(dst + a * M + cl::phys(s), cmul(make_float2(v[a][i].x, v[a][i].y), split_tw<R3>(t, s)),
                cmul(make_float2(v[a][i].z, v[a][i].w), split_tw<R3>(t, s + 1)));
     }
@@ -461,6 +508,97 @@ static cudaError_t launch_b_any(int R3, dim3 grid, cudaStream_t st, const float2
   return cudaErrorInvalidValue;
 }
 
+// Stage B of hybridCS: grid (q/2 + 1, items); CTA r holds residue r of f and
+// g (the complex residue transform of Sec. 3.1.2, used here for every
+// r <= q/2, as the paper's own code does for the v = 0 case of App. A):
+// pre-twiddle zeta_N^{rs}, length-M DFTs, pointwise product (both spectra in
+// the same digit-reversed order), backward DFT, post-twiddle; writes w'_r.
+template <int R3>
+struct StageBcs {
+  static constexpr int M = cl::Shape<R3>::M;
+  static constexpr size_t SMEM = sizeof(float2) * (2 * (size_t)M + cl::Shape<R3>::TABS + StageB<R3>::NX);
+};
+
+template <int R3>
+__global__ void __launch_bounds__(cl::Shape<R3>::T, cl::Shape<R3>::MINB)
+    k_stage_b_cs(const float2* __restrict__ Y, float2* __restrict__ Wr, Geo G, const float2* __restrict__ tw,
+                 const float2* __restrict__ tab) {
+  using K = cl::Steps<1, R3>;
+  using S = cl::Shape<R3>;
+  constexpr int M = S::M, T = S::T, NX = StageB<R3>::NX;
+  extern __shared__ float4 smem_raw[];
+  float2* arr = reinterpret_cast<float2*>(smem_raw);  // [F, G]
+  float2* tws = arr + 2 * M;
+  float2* tx = tws + S::TABS;  // [lo_r | hi_r]
+  const int tid = threadIdx.x;
+  const int r = blockIdx.x;
+  for (int i = tid; i < S::TABS / 2; i += T) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(tws + 2 * i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(tab + 2 * i) : "memory");
+  }
+  for (int i = tid; i < NX; i += T) tx[i] = __ldg(tw + (i < kLo ? r * i : r * kLo * (i - kLo)));  // < r M < N
+  allow_next_stage();
+  wait_prev_stage();
+  const int64_t astride = (int64_t)G.rows * M;
+  const float2* Y0 = Y + (int64_t)blockIdx.z * G.nin * astride;
+  float2* Wi = Wr + (int64_t)blockIdx.z * astride;
+  {
+    const float2* const src[2] = {Y0 + r * M, Y0 + astride + r * M};
+    load_twiddled<R3, 2, true, false>(arr, src, tx, tid);
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  K::template pass1<1, 2, 2>(arr, tid, tws);
+  __syncthreads();
+  K::template pass2<1, 2, 2>(arr, tid, tws);
+  __syncthreads();
+  K::template pass3<1, 2>(arr, tid);
+  __syncthreads();
+  for (int k = tid; k < M / 2; k += T) {
+    const int p = cl::phys(2 * k);
+    float2 a0, a1, b0, b1;
+    cl::lds4(arr + p, a0, a1);
+    cl::lds4(arr + M + p, b0, b1);
+    cl::sts4(arr + p, cmul(a0, b0), cmul(a1, b1));
+  }
+  __syncthreads();
+  K::template pass3<-1, 1>(arr, tid);
+  __syncthreads();
+  K::template pass2<-1, 1, 1>(arr, tid, tws);
+  __syncthreads();
+  K::template pass1<-1, 1, 1>(arr, tid, tws);
+  __syncthreads();
+  for (int k = tid; k < M / 2; k += T) {
+    const int s = 2 * k;
+    float2 a0, a1;
+    cl::lds4(arr + cl::phys(s), a0, a1);
+    a0 = cmul(a0, cconj(split_tw<R3>(tx, s)));
+    a1 = cmul(a1, cconj(split_tw<R3>(tx, s + 1)));
+    *reinterpret_cast<float4*>(Wi + r * M + s) = make_float4(a0.x, a0.y, a1.x, a1.y);
+  }
+}
+
+template <int R3>
+static cudaError_t launch_b_cs(dim3 grid, cudaStream_t st, const float2* Y, float2* Wr, const Geo& G,
+                               const float2* tw, const float2* tab) {
+  auto k = k_stage_b_cs<R3>;
+  cudaError_t e = smem_optin((const void*)k, StageBcs<R3>::SMEM);
+  if (e != cudaSuccess) return e;
+  return launch_after(k, grid, cl::Shape<R3>::T, StageBcs<R3>::SMEM, st, Y, Wr, G, tw, tab);
+}
+
+static cudaError_t launch_b_cs_any(int R3, dim3 grid, cudaStream_t st, const float2* Y, float2* Wr, const Geo& G,
+                                   const float2* tw, const float2* tab) {
+  switch (R3) {
+    case 2: return launch_b_cs<2>(grid, st, Y, Wr, G, tw, tab);
+    case 4: return launch_b_cs<4>(grid, st, Y, Wr, G, tw, tab);
+    case 8: return launch_b_cs<8>(grid, st, Y, Wr, G, tw, tab);
+    case 16: return launch_b_cs<16>(grid, st, Y, Wr, G, tw, tab);
+    case 18: return launch_b_cs<18>(grid, st, Y, Wr, G, tw, tab);
+  }
+  return cudaErrorInvalidValue;
+}
+
 static bool stage_b_length(int M) {
   for (int r : kR3)
     if (256 * r == M) return true;
@@ -499,13 +637,16 @@ namespace staged {
 
 // The three stages for `batch` items (n arrays each, item b of array i at
 // in.x[i] + b L_i, output item b at h + b K); S = sum L_i - n + 1 <= 2 q M.
+// cs: hybridCS (real residues, q M >= S) instead of hybridRCM (packed, 2 q M >= S).
 static hd_status run(hd_ctx* c, Inputs in, int nin, float* h, int64_t K, int M, int q, int64_t batch,
-                     cudaStream_t st) {
+                     cudaStream_t st, bool cs = false) {
   int64_t S = 1;
   for (int i = 0; i < nin; ++i) S += in.L[i] - 1;
   if (!stage_b_length(M)) return fail(HD_EINVAL, "staged path: M must be 512, 1024, 2048, 4096 or 4608");
   if (q < 2 || q % 2 || q > kMaxQ) return fail(HD_EINVAL, "staged path: q must be even, 2 <= q <= 1024");
-  if (2 * (int64_t)q * M < S) return fail(HD_EINVAL, "staged path needs 2 q M >= sum L_i - n + 1 (q M >= L for two arrays of length L)");
+  if (cs && (int64_t)q * M < S) return fail(HD_EINVAL, "staged hybridCS needs q M >= 2L - 1");
+  if (!cs && 2 * (int64_t)q * M < S)
+    return fail(HD_EINVAL, "staged path needs 2 q M >= sum L_i - n + 1 (q M >= L for two arrays of length L)");
   Geo G;
   G.M = M;
   G.q = q;
@@ -516,8 +657,10 @@ static hd_status run(hd_ctx* c, Inputs in, int nin, float* h, int64_t K, int M, 
   G.ldb = q;  // the structured engine keeps its swizzle inside whole 16-element blocks of each array
   G.K = (int)K;
   G.nin = nin;
+  G.rows = cs ? q / 2 + 1 : q;
   G.out_stride = K;
-  for (int i = 0; i < nin; ++i) in.p[i] = (int)(((int64_t)(in.L[i] + 1) / 2 + M - 1) / M);
+  for (int i = 0; i < nin; ++i)
+    in.p[i] = (int)(((cs ? (int64_t)in.L[i] : (int64_t)(in.L[i] + 1) / 2) + M - 1) / M);
   hd_status terr = HD_OK;
   const float2* tw = c->tables.get(G.N, st, &terr);
   if (!tw) return fail(terr, "twiddle table allocation failed");
@@ -527,26 +670,33 @@ static hd_status run(hd_ctx* c, Inputs in, int nin, float* h, int64_t K, int M, 
   if (!tq) return fail(terr, "twiddle table allocation failed");
   FftPlan pq;
   if (!factor_radices(q, &pq)) return fail(HD_EINVAL, "bad residue count");
-  const size_t per_item = sizeof(float2) * (size_t)(nin + 1) * (size_t)G.N;
+  const size_t per_item = sizeof(float2) * (size_t)(nin + 1) * (size_t)G.rows * M;
   const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(batch, 65535),
                                                                  ((int64_t)1 << 30) / (int64_t)per_item));
   if (ensure_ws(c, per_item * (size_t)chunk, st) != HD_OK) return fail(HD_ENOMEM, "workspace allocation failed");
   float2* Y = reinterpret_cast<float2*>(c->ws);  // [item][array][N]
   const size_t smem_ac = sizeof(float2) * (size_t)G.W * G.ldb;
-  auto ka = se ? (v8 ? k_stage_a<true, 8> : k_stage_a<true, 4>) : (v8 ? k_stage_a<false, 8> : k_stage_a<false, 4>);
-  auto kc = se ? (v8 ? k_stage_c<true, 8> : k_stage_c<true, 4>) : (v8 ? k_stage_c<false, 8> : k_stage_c<false, 4>);
+  auto ka = cs ? (se ? (v8 ? k_stage_a<true, 8, true> : k_stage_a<true, 4, true>)
+                     : (v8 ? k_stage_a<false, 8, true> : k_stage_a<false, 4, true>))
+               : (se ? (v8 ? k_stage_a<true, 8, false> : k_stage_a<true, 4, false>)
+                     : (v8 ? k_stage_a<false, 8, false> : k_stage_a<false, 4, false>));
+  auto kc = cs ? (se ? (v8 ? k_stage_c<true, 8, true> : k_stage_c<true, 4, true>)
+                     : (v8 ? k_stage_c<false, 8, true> : k_stage_c<false, 4, true>))
+               : (se ? (v8 ? k_stage_c<true, 8, false> : k_stage_c<true, 4, false>)
+                     : (v8 ? k_stage_c<false, 8, false> : k_stage_c<false, 4, false>));
   cudaError_t e = smem_optin((const void*)ka, smem_ac);
   if (e == cudaSuccess) e = smem_optin((const void*)kc, smem_ac);
   if (e != cudaSuccess) return cuda_fail(e, "shared memory opt-in");
   for (int64_t b0 = 0; b0 < batch; b0 += chunk) {
     const unsigned nb = (unsigned)std::min(chunk, batch - b0);
-    float2* Wr = Y + (int64_t)nin * nb * G.N;  // [item][N]
+    float2* Wr = Y + (int64_t)nin * nb * G.rows * M;  // [item][rows][M]
     Inputs ic = in;
     for (int i = 0; i < nin; ++i) ic.x[i] = in.x[i] + b0 * in.L[i];
     float* hi = h + b0 * K;
     ka<<<dim3(M / G.W, nin, nb), kThreads, smem_ac, st>>>(ic, Y, G, tq, pq);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "staged path: stage A launch");
-    e = launch_b_any(M / 256, dim3(q / 2, 1, nb), st, Y, Wr, G, tw, tab);
+    e = cs ? launch_b_cs_any(M / 256, dim3(q / 2 + 1, 1, nb), st, Y, Wr, G, tw, tab)
+           : launch_b_any(M / 256, dim3(q / 2, 1, nb), st, Y, Wr, G, tw, tab);
     if (e != cudaSuccess) return cuda_fail(e, "staged path: stage B launch");
     e = launch_after(kc, dim3(M / G.W, 1, nb), kThreads, smem_ac, st, (const float2*)Wr, hi, G, tq, pq);
     if (e != cudaSuccess) return cuda_fail(e, "staged path: stage C launch");
@@ -557,12 +707,12 @@ static hd_status run(hd_ctx* c, Inputs in, int nin, float* h, int64_t K, int M, 
 }  // namespace staged
 
 hd_status conv1d_staged(hd_ctx* c, const float* f, const float* g, float* h, int64_t L, int64_t K, int M, int q,
-                        int64_t batch, cudaStream_t st) {
+                        int64_t batch, cudaStream_t st, bool cs) {
   staged::Inputs in = {};
   in.x[0] = f;
   in.x[1] = g;
   in.L[0] = in.L[1] = (int)L;
-  return staged::run(c, in, 2, h, K > 0 ? K : L, M, q, batch, st);
+  return staged::run(c, in, 2, h, K > 0 ? K : L, M, q, batch, st, cs);
 }
 
 hd_status conv1d_multi(hd_ctx* c, int n, const float* const* x, const int64_t* L, int64_t K, int M, int q,

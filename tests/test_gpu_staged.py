@@ -126,3 +126,49 @@ def test_staged_argument_errors(hd):
     with pytest.raises(hd.HDError) as e:
         hd.conv_staged(buf[:L], g, M=512, q=10, out=buf[L // 2:L // 2 + 2 * L - 1], out_extent="full")
     assert e.value.status == hd.HD_EINVAL
+
+
+# --- hybridCS on the three kernels (App. A's inner loop for real data) -------------
+CS_CASES = [(1, 512, 2), (777, 512, 4), (4097, 512, 18), (5000, 512, 20), (9000, 1024, 18), (20001, 2048, 20),
+            (40000, 4608, 18), (100000, 1024, 256), (3000, 512, 1024)]
+
+
+@pytest.mark.parametrize("L,M,q", CS_CASES)
+@pytest.mark.parametrize("kind", ["L", "full"])
+def test_staged_cs_parity(hd, L, M, q, kind):
+    K = L if kind == "L" else 2 * L - 1
+    f, g = inputs.normal_pair(L, seed=3700 + L + q)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64), (K,))
+    h = host(hd.conv_staged(dev(f), dev(g), M=M, q=q, out_extent=K, algo="hybridCS"))
+    assert rel_l2(h, ref) <= TOL, (L, M, q, K)
+
+
+@pytest.mark.parametrize("L", [9000, 1 << 18, 1000000])
+def test_staged_cs_full_size(hd, L):
+    """hybridCS beyond one CTA (L > 8192) through the public call."""
+    M, q = hd.hd_plan(hd.context(), hd.HD_HYBRID_CS, L)
+    assert M * q >= 2 * L - 1 and M in (512, 1024, 2048, 4096, 4608)
+    f, g = inputs.uniform_pair(L, seed=3800 + L % 1000)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    h = host(hd.conv(dev(f), dev(g), algo="hybridCS"))
+    err = rel_l2(h, ref)
+    if L >= 1 << 18:
+        record_rel(f"1D L={L} hybridCS three-kernel path (M={M}, q={q})", err, TOL, L)
+    assert err <= TOL
+
+
+def test_staged_cs_batch_and_errors(hd):
+    L, B = 30000, 3
+    fs, gs = zip(*(inputs.uniform_pair(L, seed=3900 + b) for b in range(B)))
+    f, g = np.stack(fs), np.stack(gs)
+    h = host(hd.conv_batch(dev(f), dev(g), 1, algo="hybridCS"))
+    for b in range(B):
+        ref = oracle.fft_conv(f[b].astype(np.float64), g[b].astype(np.float64))
+        assert rel_l2(h[b], ref) <= TOL
+    x = dev(np.ones(5000))
+    with pytest.raises(hd.HDError) as e:
+        hd.conv_staged(x, x, M=512, q=18, algo="hybridCS")  # 9216 < 2L - 1
+    assert e.value.status == hd.HD_EINVAL
+    with pytest.raises(hd.HDError) as e:
+        hd.conv_staged(x, x, M=512, q=20, algo="explicit")
+    assert e.value.status == hd.HD_EINVAL
