@@ -44,7 +44,8 @@ WORKLOAD = "1D batched: 4096 real convolutions, L ~ U{500..70000} (seed 2), N(0,
 # Sources compiled into the batched kernel's translation unit (the DRAM-traffic
 # record is valid only for these exact files).
 CLUSTER_SOURCES = ("hd_cl_kernel.cuh", "hd_cl_launch.cuh", "hd_cl_c1.cu", "hd_cl_c1b.cu", "hd_cl_c2.cu",
-                   "hd_cl_c4.cu", "hd_cl_c8.cu", "hd_cluster.cuh", "hd_bfly.cuh", "hd_conv1d.cuh", "hd_internal.h")
+                   "hd_cl_c4.cu", "hd_cl_c4b.cu", "hd_cl_c8.cu", "hd_cl_c8b.cu", "hd_cl_c16.cu", "hd_cluster.cuh",
+                   "hd_bfly.cuh", "hd_conv1d.cuh", "hd_internal.h")
 
 
 def _code_only(text):
@@ -491,6 +492,8 @@ def compare_suite(peak_hbm, reps=20):
         h = torch.empty_like(tf)
         row = {"l2": "warm" if 12 * f.size < 126e6 else "cold (> L2)"}
         variants = [("hybridRCM", "fp32"), ("hybridCS", "fp32"), ("explicitRCM", "fp32"), ("explicit", "fp32")]
+        if len(shape) == 1:
+            variants.append(("hybridCSRCM", "fp32"))
         if len(shape) == 3:
             variants.append(("hybridRCM", "split_bf16"))
         for algo, prec in variants:
@@ -510,6 +513,41 @@ def compare_suite(peak_hbm, reps=20):
         out[name] = row
         del tf, tg, h
         torch.cuda.empty_cache()
+    # long 1D lengths (the three-kernel path of App. A) and unequal lengths (Sec. 7)
+    L = 1000000
+    f, g = inputs.uniform_pair(L, 1)
+    tf, tg = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    h = torch.empty_like(tf)
+    row = {"l2": "warm"}
+
+    def entry(ms):
+        return {"ms": round(ms, 5), "conv_per_s": round(1e3 / ms, 1),
+                "hbm_frac": round(12 * L / (ms * 1e-3) / 1e9 / peak_hbm, 4)}
+
+    for algo in ("hybridRCM", "hybridCS"):
+        row[algo] = entry(time_graph(lambda: hd.conv(tf, tg, algo=algo, out=h)))
+    # the one-CTA kernel with the same kind of parameters (m = 4000, q = 250):
+    # the path lengths beyond the cluster kernel took before the three kernels
+    row["hybridRCM one-CTA (m=4000, q=250)"] = entry(
+        time_graph(lambda: hd.conv(tf, tg, algo="hybridRCM", out=h, params=[(4000, 250)]), n=2))
+    row["three_kernel_speedup"] = round(row["hybridRCM one-CTA (m=4000, q=250)"]["ms"] / row["hybridRCM"]["ms"], 1)
+
+    def cufft():  # library context: explicit padding to 2L with torch.fft (cuFFT)
+        F = torch.fft.rfft(tf, n=2 * L)
+        G = torch.fft.rfft(tg, n=2 * L)
+        h.copy_(torch.fft.irfft(F * G, n=2 * L)[:L])
+
+    row["explicit via torch.fft (cuFFT, library; context)"] = entry(time_graph(cufft))
+    out["1D L=1000000 (three kernels)"] = row
+    k = torch.from_numpy(inputs.uniform_pair(4096, 7)[0]).cuda()
+    kp = torch.zeros_like(tf)
+    kp[:4096] = k
+    row = {"l2": "warm",
+           "hybridRCM multi (p_g = 1 block of the kernel)": entry(time_graph(lambda: hd.conv_multi([tf, k], out=h))),
+           "hybridRCM, kernel zero-padded to L": entry(time_graph(lambda: hd.conv(tf, kp, out=h)))}
+    out["1D unequal: L=1000000 signal * 4096 kernel, first L outputs"] = row
+    del tf, tg, h, k, kp
+    torch.cuda.empty_cache()
     f, g = inputs.uniform_pair((16, 1024, 1024), 6)
     tf = torch.from_numpy(f).cuda().requires_grad_(True)
     tg = torch.from_numpy(g).cuda().requires_grad_(True)
