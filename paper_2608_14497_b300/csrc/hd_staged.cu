@@ -614,20 +614,21 @@ static int s_per_cta(int q) {
 
 }  // namespace staged
 
-// Planner of the staged path: the smallest stage-B length M = 256 R3 whose
-// residue count q (the smallest length {1, 3, 5, 9} x 2^a >= max(16, L / M),
-// which the structured engine transforms) is at most 512, else at most 1024;
-// false if L is beyond 1024 * 4608.
-bool staged_params(int64_t L, int* M, int* q) {
-  for (int cap : {512, staged::kMaxQ}) {
-    for (int r : staged::kR3) {
-      const int64_t mm = 256 * r;
-      const int64_t qq = ladder_ceil(std::max<int64_t>(16, (L + mm - 1) / mm));
-      if (qq <= cap) {
-        *M = (int)mm;
-        *q = (int)qq;
-        return true;
-      }
+// Planner of the three-kernel path for a needed padded length n (hybridRCM:
+// q M >= L packed; hybridCS: q M >= 2L - 1 real): M = 512 below 2^17, 2048
+// below 2^19, else 4096 (4608 when q would exceed 1024), and q the smallest
+// length {1, 3, 5, 9} x 2^a >= max(16, n / M), which the structured engine
+// transforms.  Measured on B300 over L = 10^5 .. 4 10^6 for both algorithms,
+// this rule is within ~10% of the best (M, q) of every length tried; false if
+// n > 1024 x 4608.
+bool staged_params(int64_t n, int* M, int* q) {
+  const int first = n < (1 << 17) ? 512 : n < (1 << 19) ? 2048 : 4096;
+  for (int mm : {first, 4608}) {
+    const int64_t qq = ladder_ceil(std::max<int64_t>(16, (n + mm - 1) / mm));
+    if (qq <= staged::kMaxQ) {
+      *M = mm;
+      *q = (int)qq;
+      return true;
     }
   }
   return false;
