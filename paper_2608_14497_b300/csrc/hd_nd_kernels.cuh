@@ -62,6 +62,41 @@ __device__ __forceinline__ int64_t packed_offset_rev(const ColGeom& cg, int64_t 
   return base + Lreal - 1 - c2;
 }
 
+// Column strips: the W columns b0..b0+W-1 (W a power of two <= 8) of n rows,
+// moved between global memory and shared arrays s[w * ld + j].  Element
+// id = tid + k T is row j = id / W, column w = id mod W, so a warp reads whole
+// 32-byte sectors of consecutive columns; the loads of KT elements per thread
+// are all issued before the first shared store (one round of memory latency
+// per KT T elements, not one per element).
+template <int KT, typename LoadFn>
+__device__ __forceinline__ void strip_load(float2* s, int ld, int n, int W, LoadFn f) {
+  const int T = blockDim.x, total = n * W;
+  const int wl = __ffs(W) - 1;
+  for (int base = 0; base < total; base += KT * T) {
+    float2 v[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      const int id = base + threadIdx.x + k * T;
+      v[k] = id < total ? f(id >> wl, id & (W - 1)) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      const int id = base + threadIdx.x + k * T;
+      if (id < total) s[(id & (W - 1)) * ld + (id >> wl)] = v[k];
+    }
+  }
+}
+
+template <typename StoreFn>
+__device__ __forceinline__ void strip_store(const float2* s, int ld, int n, int W, StoreFn g) {
+  const int T = blockDim.x, total = n * W;
+  const int wl = __ffs(W) - 1;
+  for (int id = threadIdx.x; id < total; id += T) {
+    const int j = id >> wl, w = id & (W - 1);
+    g(j, w, s[w * ld + j]);
+  }
+}
+
 // Input element loaders for the column passes.
 enum : int { IN_COMPLEX = 0, IN_PACKED_REAL = 1, IN_PACKED_REAL_REV = 2 };
 enum : int { OUT_COMPLEX = 0, OUT_UNPACK_REAL = 1, OUT_UNPACK_REAL_REV = 2 };
@@ -90,27 +125,26 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_col_fwd(const void*
   // load columns (zero beyond the input)
   float2* dst = keep ? x : buf;
   const int ldst = keep ? Lin : m;
-  for (int idx = tid; idx < W * ldst; idx += T) {
-    const int j = idx / W, w = idx - j * W;
+  strip_load<SE ? 16 : 4>(dst, ldst, ldst, W, [&](int j, int w) -> float2 {
     const int64_t b = b0 + w;
     float2 v = make_float2(0.f, 0.f);
     if (j < Lin && b < cg.B) {
       const int64_t e = (a * Lin + j) * cg.B + b;
       if (in_mode == IN_COMPLEX) {
-        v = reinterpret_cast<const float2*>(Xv)[e];
+        v = __ldg(reinterpret_cast<const float2*>(Xv) + e);
       } else if (in_mode == IN_PACKED_REAL) {
         int64_t c;
         const float* fr = reinterpret_cast<const float*>(Xv) + packed_offset(cg, a, Lin, j, b, Lreal, &c);
-        v = make_float2(fr[c], (c + 1 < Lreal) ? fr[c + 1] : 0.f);
+        v = make_float2(__ldg(fr + c), (c + 1 < Lreal) ? __ldg(fr + c + 1) : 0.f);
       } else {
         int64_t second;
         const float* xr = reinterpret_cast<const float*>(Xv);
         const int64_t first = packed_offset_rev(cg, a, Lin, j, b, Lreal, &second);
-        v = make_float2(xr[first], second >= 0 ? xr[second] : 0.f);
+        v = make_float2(__ldg(xr + first), second >= 0 ? __ldg(xr + second) : 0.f);
       }
     }
-    dst[w * ldst + j] = v;
-  }
+    return v;
+  });
   __syncthreads();
   auto residue_pass = [&](int r) __attribute__((always_inline)) {
     if (keep) {
@@ -131,11 +165,10 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_col_fwd(const void*
       __syncthreads();
     }
     fft_sel<1, PTS, TC, SE>(buf, m, W, pl, tw, q);
-    for (int idx = tid; idx < W * m; idx += T) {
-      const int l = idx / W, w = idx - l * W;
+    strip_store(buf, m, m, W, [&](int l, int w, float2 v) {
       const int64_t b = b0 + w;
-      if (b < cg.B) Y[(a * (int64_t)N + (int64_t)r * m + l) * cg.B + b] = buf[w * m + l];
-    }
+      if (b < cg.B) Y[(a * (int64_t)N + (int64_t)r * m + l) * cg.B + b] = v;
+    });
     __syncthreads();
   };
   // SE: q <= 2, one inlined transform per residue (no loop around inlined FFTs)
@@ -171,11 +204,10 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_col_bwd(const float
   if (sep)
     for (int idx = tid; idx < W * Lout; idx += T) acc[idx] = make_float2(0.f, 0.f);
   auto residue_pass = [&](int r) __attribute__((always_inline)) {
-    for (int idx = tid; idx < W * m; idx += T) {
-      const int l = idx / W, w = idx - l * W;
+    strip_load<SE ? 16 : 4>(buf, m, m, W, [&](int l, int w) -> float2 {
       const int64_t b = b0 + w;
-      buf[w * m + l] = (b < cg.B) ? Y[(a * (int64_t)N + (int64_t)r * m + l) * cg.B + b] : make_float2(0.f, 0.f);
-    }
+      return (b < cg.B) ? __ldg(Y + (a * (int64_t)N + (int64_t)r * m + l) * cg.B + b) : make_float2(0.f, 0.f);
+    });
     __syncthreads();
     fft_sel<-1, PTS, TC, SE>(buf, m, W, pl, tw, q);
     if (sep) {
@@ -194,11 +226,10 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_col_bwd(const float
   }
   const float2* res = sep ? acc : buf;
   const int lres = sep ? Lout : m;
-  for (int idx = tid; idx < W * Lout; idx += T) {
-    const int j = idx / W, w = idx - j * W;
+  strip_store(res, lres, Lout, W, [&](int j, int w, float2 u) {
     const int64_t b = b0 + w;
-    if (b >= cg.B) continue;
-    const float2 v = cscale(res[w * lres + j], scale);
+    if (b >= cg.B) return;
+    const float2 v = cscale(u, scale);
     if (out_mode == OUT_COMPLEX) {
       reinterpret_cast<float2*>(Zv)[(a * Lout + j) * cg.B + b] = v;
     } else if (out_mode == OUT_UNPACK_REAL) {
@@ -213,7 +244,7 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_col_bwd(const float
       zr[first] = v.x;
       if (second >= 0) zr[second] = v.y;
     }
-  }
+  });
 }
 
 // ---------------------------------------------------------------------------

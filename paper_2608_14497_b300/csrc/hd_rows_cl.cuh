@@ -61,6 +61,37 @@ struct RowSteps {
     }
   }
 
+  // load_row for NR rows at once, into the array pairs a0 + 2 M r: every
+  // global load of the NR rows (and the twiddles) is issued before the first
+  // shared store, so the CTA waits for one round of memory latency, not 2 NR.
+  template <int NR>
+  static __device__ __forceinline__ void load_rows(const float2* const (&x)[NR], int Lp, float2* a0,
+                                                   const float2* __restrict__ tw, int tid) {
+    constexpr int U = M / 2 / T;  // 4 for every R3
+    float2 v[NR][U][2];
+    float4 w[U];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const int s = 2 * (tid + i * T);
+      w[i] = cl::ldg4(tw + s);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        v[r][i][0] = s < Lp ? x[r][s] : make_float2(0.f, 0.f);
+        v[r][i][1] = s + 1 < Lp ? x[r][s + 1] : make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int s = 2 * (tid + i * T);
+        float2* a = a0 + 2 * M * r;
+        cl::sts4(a + phys(s), v[r][i][0], v[r][i][1]);
+        cl::sts4(a + M + phys(s), cmul(v[r][i][0], make_float2(w[i].x, w[i].y)),
+                 cmul(v[r][i][1], make_float2(w[i].z, w[i].w)));
+      }
+  }
+
   // C_1 across a row pair: residue 0 with the (M - l) mod M pairing (one
   // position per task), residue 1 with M - 1 - p (pairs of positions).
   static __device__ __forceinline__ void product_pair(float2* arr, const float2* __restrict__ zt, float2 z1, int tid) {
@@ -141,8 +172,10 @@ __global__ void __launch_bounds__(RowShape<R3>::T, RowShape<R3>::MINB)
   const float2* zt = tab + cl::Shape<R3>::TABZ;
   if (prow == row) {
     // the row is its own partner: the one-CTA convolution of the cluster kernel
-    S::load_row(F + (int64_t)row * Lp, Lp, arr, tw, tid);
-    S::load_row(G + (int64_t)row * Lp, Lp, arr + 2 * M, tw, tid);
+    {
+      const float2* const src[2] = {F + (int64_t)row * Lp, G + (int64_t)row * Lp};
+      S::template load_rows<2>(src, Lp, arr, tw, tid);
+    }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     K::template pass1<1, 4, 2>(arr, tid, tws);
@@ -167,10 +200,11 @@ __global__ void __launch_bounds__(RowShape<R3>::T, RowShape<R3>::MINB)
     S::store_row(O + (int64_t)row * Kp, Kp, arr, tw, scale, tid);
     return;
   }
-  S::load_row(F + (int64_t)row * Lp, Lp, arr, tw, tid);
-  S::load_row(F + (int64_t)prow * Lp, Lp, arr + 2 * M, tw, tid);
-  S::load_row(G + (int64_t)row * Lp, Lp, arr + 4 * M, tw, tid);
-  S::load_row(G + (int64_t)prow * Lp, Lp, arr + 6 * M, tw, tid);
+  {
+    const float2* const src[4] = {F + (int64_t)row * Lp, F + (int64_t)prow * Lp, G + (int64_t)row * Lp,
+                                  G + (int64_t)prow * Lp};
+    S::template load_rows<4>(src, Lp, arr, tw, tid);
+  }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   K::template pass1<1, 8, 2>(arr, tid, tws);
@@ -285,9 +319,10 @@ __global__ void __launch_bounds__(RowShape<R3>::T, RowAdjShape<R3>::MINB)
   const float2* zt = tab + cl::Shape<R3>::TABZ;
   const float2 z1 = cl::ldg2(tw + 1);
   if (prow == row) {  // [U, F, G] x {r0, r1}
-    S::load_row(U + (int64_t)row * Lp, Lp, arr, tw, tid);
-    S::load_row(F + (int64_t)row * Lp, Lp, arr + 2 * M, tw, tid);
-    S::load_row(G + (int64_t)row * Lp, Lp, arr + 4 * M, tw, tid);
+    {
+      const float2* const src[3] = {U + (int64_t)row * Lp, F + (int64_t)row * Lp, G + (int64_t)row * Lp};
+      S::template load_rows<3>(src, Lp, arr, tw, tid);
+    }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     K::template pass1<1, 6, 2>(arr, tid, tws);
@@ -310,12 +345,11 @@ __global__ void __launch_bounds__(RowShape<R3>::T, RowAdjShape<R3>::MINB)
     return;
   }
   // [U row, U partner, F row, F partner, G row, G partner] x {r0, r1}
-  S::load_row(U + (int64_t)row * Lp, Lp, arr, tw, tid);
-  S::load_row(U + (int64_t)prow * Lp, Lp, arr + 2 * M, tw, tid);
-  S::load_row(F + (int64_t)row * Lp, Lp, arr + 4 * M, tw, tid);
-  S::load_row(F + (int64_t)prow * Lp, Lp, arr + 6 * M, tw, tid);
-  S::load_row(G + (int64_t)row * Lp, Lp, arr + 8 * M, tw, tid);
-  S::load_row(G + (int64_t)prow * Lp, Lp, arr + 10 * M, tw, tid);
+  {
+    const float2* const src[6] = {U + (int64_t)row * Lp, U + (int64_t)prow * Lp, F + (int64_t)row * Lp,
+                                  F + (int64_t)prow * Lp, G + (int64_t)row * Lp, G + (int64_t)prow * Lp};
+    S::template load_rows<6>(src, Lp, arr, tw, tid);
+  }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   K::template pass1<1, 12, 2>(arr, tid, tws);
