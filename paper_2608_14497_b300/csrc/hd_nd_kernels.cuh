@@ -62,6 +62,28 @@ __device__ __forceinline__ int64_t packed_offset_rev(const ColGeom& cg, int64_t 
   return base + Lreal - 1 - c2;
 }
 
+// Element loop in batches: for idx < total, v = f(idx) (global loads) then
+// g(idx, v) (shared stores); the f of KT elements per thread are all issued
+// before the first g, so a CTA waits for one round of memory latency per KT T
+// elements instead of one per element.
+template <int KT, typename V, typename LoadFn, typename StoreFn>
+__device__ __forceinline__ void batched(int total, LoadFn f, StoreFn g) {
+  const int T = blockDim.x;
+  for (int base = 0; base < total; base += KT * T) {
+    V v[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      const int idx = base + threadIdx.x + k * T;
+      if (idx < total) v[k] = f(idx);
+    }
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      const int idx = base + threadIdx.x + k * T;
+      if (idx < total) g(idx, v[k]);
+    }
+  }
+}
+
 // Column strips: the W columns b0..b0+W-1 (W a power of two <= 8) of n rows,
 // moved between global memory and shared arrays s[w * ld + j].  Element
 // id = tid + k T is row j = id / W, column w = id mod W, so a warp reads whole
@@ -271,11 +293,17 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_col_fwd_cs(const float* __r
   const int T = blockDim.x, tid = threadIdx.x;
   float* x = reinterpret_cast<float*>(sm);          // W x Lin real
   float2* buf = sm + acc_slots((W * Lin + 1) / 2);  // W x m complex
-  for (int idx = tid; idx < W * Lin; idx += T) {
-    const int j = idx / W, w = idx - j * W;
-    const int64_t b = b0 + w;
-    x[w * Lin + j] = (b < B) ? X[(int64_t)j * B + b] : 0.f;
-  }
+  batched<SE ? 16 : 4, float>(
+      W * Lin,
+      [&](int idx) {
+        const int j = idx / W, w = idx - j * W;
+        const int64_t b = b0 + w;
+        return (b < B) ? __ldg(X + (int64_t)j * B + b) : 0.f;
+      },
+      [&](int idx, float v) {
+        const int j = idx / W, w = idx - j * W;
+        x[w * Lin + j] = v;
+      });
   __syncthreads();
   auto store = [&](int row, int w, float2 v) {
     const int64_t b = b0 + w;
@@ -380,18 +408,24 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_col_bwd_cs(const float2* __
   {
     const int npair = W / 2;
     const int nh = m / 2 + 1;
-    for (int idx = tid; idx < npair * m; idx += T) {
-      const int l = idx / npair, pw = idx - l * npair;
-      float2 a0, a1;
-      if (l < nh) {
-        a0 = load(l, 2 * pw);
-        a1 = load(l, 2 * pw + 1);
-      } else {
-        a0 = cconj(load(m - l, 2 * pw));
-        a1 = cconj(load(m - l, 2 * pw + 1));
-      }
-      buf[pw * m + l] = cadd(a0, cmul_i<1>(a1));
-    }
+    batched<SE ? 8 : 2, float2>(
+        npair * m,
+        [&](int idx) {
+          const int l = idx / npair, pw = idx - l * npair;
+          float2 a0, a1;
+          if (l < nh) {
+            a0 = load(l, 2 * pw);
+            a1 = load(l, 2 * pw + 1);
+          } else {
+            a0 = cconj(load(m - l, 2 * pw));
+            a1 = cconj(load(m - l, 2 * pw + 1));
+          }
+          return cadd(a0, cmul_i<1>(a1));
+        },
+        [&](int idx, float2 v) {
+          const int l = idx / npair, pw = idx - l * npair;
+          buf[pw * m + l] = v;
+        });
     __syncthreads();
     fft_sel<-1, PTS, false, SE>(buf, m, npair, pl_m, tw, q);
     for (int idx = tid; idx < W * Lout; idx += T) {
@@ -403,10 +437,9 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_col_bwd_cs(const float2* __
   }
   int row0 = m / 2 + 1;
   for (int r = 1; r < (SE ? 1 : (q + 1) / 2); ++r) {
-    for (int idx = tid; idx < W * m; idx += T) {
-      const int l = idx / W, w = idx - l * W;
-      buf[w * m + l] = load(row0 + l, w);
-    }
+    batched<SE ? 8 : 2, float2>(
+        W * m, [&](int idx) { return load(row0 + idx / W, idx % W); },
+        [&](int idx, float2 v) { buf[(idx % W) * m + idx / W] = v; });
     __syncthreads();
     fft_sel<-1, PTS, false, SE>(buf, m, W, pl_m, tw, q);
     for (int idx = tid; idx < W * Lout; idx += T) {
@@ -418,10 +451,9 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_col_bwd_cs(const float2* __
   }
   if (q % 2 == 0) {
     const int e = m / 2, qh = q / 2;
-    for (int idx = tid; idx < W * e; idx += T) {
-      const int c = idx / W, w = idx - c * W;
-      buf[w * e + c] = load(row0 + c, w);
-    }
+    batched<SE ? 8 : 2, float2>(
+        W * e, [&](int idx) { return load(row0 + idx / W, idx % W); },
+        [&](int idx, float2 v) { buf[(idx % W) * e + idx / W] = v; });
     __syncthreads();
     fft_sel<-1, PTS, false, SE>(buf, e, W, pl_h, tw, 2 * q);
     for (int idx = tid; idx < W * Lout; idx += T) {
@@ -724,20 +756,23 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_rows_cconv(float2* F, const
   for (int j = tid; j < Lr; j += T) acc[j] = make_float2(0.f, 0.f);
   __syncthreads();
   auto residue_pass = [&](int r) __attribute__((always_inline)) {
-    for (int idx = tid; idx < 2 * m; idx += T) {
-      const int arr = idx / m, s = idx - arr * m;
-      const float2* x = src[arr];
-      float2 sum = make_float2(0.f, 0.f);
-      int e = r * s;
-      for (int t = 0; t < p; ++t) {
-        const int j = t * m + s;
-        if (j >= Lr) break;
-        sum = cadd(sum, cmul(x[j], tw_get<1>(tw, e)));
-        e += r * m;
-        if (e >= N) e -= N;
-      }
-      buf[idx] = sum;
-    }
+    batched<SE ? 8 : 2, float2>(
+        2 * m,
+        [&](int idx) {
+          const int arr = idx / m, s = idx - arr * m;
+          const float2* x = src[arr];
+          float2 sum = make_float2(0.f, 0.f);
+          int e = r * s;
+          for (int t = 0; t < p; ++t) {
+            const int j = t * m + s;
+            if (j >= Lr) break;
+            sum = cadd(sum, cmul(x[j], tw_get<1>(tw, e)));
+            e += r * m;
+            if (e >= N) e -= N;
+          }
+          return sum;
+        },
+        [&](int idx, float2 v) { buf[idx] = v; });
     __syncthreads();
     fft_sel<1, PTS, false, SE>(buf, m, 2, pl, tw, q);
     for (int l = tid; l < m; l += T) buf[l] = cmul(buf[l], buf[m + l]);
@@ -787,20 +822,24 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_rows_fft(RowsIO io, int mod
     orow = a * io.keep_rows_outer[1] + b;
   }
   // load
+  auto put = [&](int j, float2 v) { buf[j] = v; };
   if (mode == 0) {
     const float* s = reinterpret_cast<const float*>(io.src) + row * io.src_stride;
-    for (int j = tid; j < n; j += T) buf[j] = make_float2(s[2 * j], s[2 * j + 1]);
+    batched<SE ? 16 : 4, float2>(n, [&](int j) { return make_float2(s[2 * j], s[2 * j + 1]); }, put);
   } else if (mode == 1) {
     const float2* s = reinterpret_cast<const float2*>(io.src) + row * io.src_stride;
     // Eq. fourierPack: Z_k = 1/2 (H_k + conj H_{n-k}) + i/2 (H_k - conj H_{n-k}) zeta_{2n}^{-k}
-    for (int k = tid; k < n; k += T) {
-      const float2 hk = s[k], hc = cconj(s[n - k]);
-      const float2 w = tw_get<-1>(tw, k * twmul / 2);
-      buf[k] = cscale(cadd(cadd(hk, hc), cmul_i<1>(cmul(csub(hk, hc), w))), 0.5f);
-    }
+    batched<SE ? 8 : 2, float2>(
+        n,
+        [&](int k) {
+          const float2 hk = s[k], hc = cconj(s[n - k]);
+          const float2 w = tw_get<-1>(tw, k * twmul / 2);
+          return cscale(cadd(cadd(hk, hc), cmul_i<1>(cmul(csub(hk, hc), w))), 0.5f);
+        },
+        put);
   } else {
     const float2* s = reinterpret_cast<const float2*>(io.src) + row * io.src_stride;
-    for (int j = tid; j < n; j += T) buf[j] = s[j];
+    batched<SE ? 16 : 4, float2>(n, [&](int j) { return s[j]; }, put);
   }
   __syncthreads();
   if (mode == 0 || mode == 2)
