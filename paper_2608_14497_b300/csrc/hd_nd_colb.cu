@@ -6,7 +6,9 @@ namespace hd {
 cudaError_t launch_col_bwd(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, const float2* Y, void* Z,
                            ColGeom cg, int Lout, int m, int q, int out_mode, int Lreal, float scale, const float2* tw,
                            FftPlan pl) {
-  auto k = e == Eng::SE    ? k_col_bwd<kPtsSE, false, true>
+  // the structured engine at <= 16 points per thread (T <= 256): the 4-CTA-per-SM instance
+  auto k = (e == Eng::SE && T <= 256) ? k_col_bwd<16, false, true>
+           : e == Eng::SE    ? k_col_bwd<kPtsSE, false, true>
            : e == Eng::TC  ? k_col_bwd<kPts, true, false>
            : e == Eng::TCS ? k_col_bwd<kPts, true, true>
                            : k_col_bwd<kPts, false, false>;

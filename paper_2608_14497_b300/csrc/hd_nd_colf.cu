@@ -6,7 +6,9 @@ namespace hd {
 cudaError_t launch_col_fwd(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, const void* X, float2* Y,
                            ColGeom cg, int Lin, int m, int q, int p, int in_mode, int Lreal, const float2* tw,
                            FftPlan pl) {
-  auto k = e == Eng::SE    ? k_col_fwd<kPtsSE, false, true>
+  // the structured engine at <= 16 points per thread (T <= 256): the 4-CTA-per-SM instance
+  auto k = (e == Eng::SE && T <= 256) ? k_col_fwd<16, false, true>
+           : e == Eng::SE    ? k_col_fwd<kPtsSE, false, true>
            : e == Eng::TC  ? k_col_fwd<kPts, true, false>
            : e == Eng::TCS ? k_col_fwd<kPts, true, true>
                            : k_col_fwd<kPts, false, false>;

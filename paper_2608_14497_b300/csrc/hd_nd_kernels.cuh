@@ -129,8 +129,21 @@ enum : int { OUT_COMPLEX = 0, OUT_UNPACK_REAL = 1, OUT_UNPACK_REAL_REV = 2 };
 //      (f[j][2b], f[j][2b+1]) with real row length Lreal), Y: [A][q m][B],
 //   residue-major rows.  Eq. forwardr per column.
 // ---------------------------------------------------------------------------
+// Launch bounds of the column passes: the structured engine with 16 points
+// per thread runs at most 256 threads and asks for 4 resident CTAs per SM (64
+// registers), the other engines as before.
+#ifndef HD_COL_MINB
+#define HD_COL_MINB 4
+#endif
 template <int PTS, bool TC, bool SE>
-__global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_col_fwd(const void* Xv, float2* Y, ColGeom cg,
+struct ColBounds {
+  static constexpr int T = (SE && !TC && PTS <= 16) ? 256 : (TC || SE) ? 512 : 1024;
+  static constexpr int MINB = (SE && !TC && PTS <= 16) ? HD_COL_MINB : 1;
+  static constexpr int KT = (SE && !TC) ? (PTS <= 16 ? 8 : 16) : 4;  // strip_load batch
+};
+
+template <int PTS, bool TC, bool SE>
+__global__ void __launch_bounds__(ColBounds<PTS, TC, SE>::T, ColBounds<PTS, TC, SE>::MINB) k_col_fwd(const void* Xv, float2* Y, ColGeom cg,
                                                   int Lin, int m, int q, int p, int in_mode, int Lreal,
                                                   const float2* __restrict__ tw, FftPlan pl) {
   extern __shared__ float4 smem_raw[];
@@ -147,7 +160,7 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_col_fwd(const void*
   // load columns (zero beyond the input)
   float2* dst = keep ? x : buf;
   const int ldst = keep ? Lin : m;
-  strip_load<SE ? 16 : 4>(dst, ldst, ldst, W, [&](int j, int w) -> float2 {
+  strip_load<ColBounds<PTS, TC, SE>::KT>(dst, ldst, ldst, W, [&](int j, int w) -> float2 {
     const int64_t b = b0 + w;
     float2 v = make_float2(0.f, 0.f);
     if (j < Lin && b < cg.B) {
@@ -209,7 +222,7 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_col_fwd(const void*
 //   Eqs. accumulator and accumulation per column, scaled by `scale`.
 // ---------------------------------------------------------------------------
 template <int PTS, bool TC, bool SE>
-__global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_col_bwd(const float2* Y, void* Zv, ColGeom cg, int Lout, int m,
+__global__ void __launch_bounds__(ColBounds<PTS, TC, SE>::T, ColBounds<PTS, TC, SE>::MINB) k_col_bwd(const float2* Y, void* Zv, ColGeom cg, int Lout, int m,
                                                   int q, int out_mode, int Lreal, float scale,
                                                   const float2* __restrict__ tw, FftPlan pl) {
   extern __shared__ float4 smem_raw[];
@@ -226,7 +239,7 @@ __global__ void __launch_bounds__((TC || SE) ? 512 : 1024) k_col_bwd(const float
   if (sep)
     for (int idx = tid; idx < W * Lout; idx += T) acc[idx] = make_float2(0.f, 0.f);
   auto residue_pass = [&](int r) __attribute__((always_inline)) {
-    strip_load<SE ? 16 : 4>(buf, m, m, W, [&](int l, int w) -> float2 {
+    strip_load<ColBounds<PTS, TC, SE>::KT>(buf, m, m, W, [&](int l, int w) -> float2 {
       const int64_t b = b0 + w;
       return (b < cg.B) ? __ldg(Y + (a * (int64_t)N + (int64_t)r * m + l) * cg.B + b) : make_float2(0.f, 0.f);
     });
@@ -282,7 +295,7 @@ __host__ __device__ __forceinline__ int cs_rows(int m, int q) {
 }
 
 template <int PTS, bool SE>
-__global__ void __launch_bounds__(SE ? 512 : 1024) k_col_fwd_cs(const float* __restrict__ X, float2* __restrict__ Y, int64_t B,
+__global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, false, SE>::MINB) k_col_fwd_cs(const float* __restrict__ X, float2* __restrict__ Y, int64_t B,
                                                      int W, int Lin, int m, int q, int p,
                                                      const float2* __restrict__ tw, FftPlan pl_m, FftPlan pl_h) {
   extern __shared__ float4 smem_raw[];
@@ -293,7 +306,7 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_col_fwd_cs(const float* __r
   const int T = blockDim.x, tid = threadIdx.x;
   float* x = reinterpret_cast<float*>(sm);          // W x Lin real
   float2* buf = sm + acc_slots((W * Lin + 1) / 2);  // W x m complex
-  batched<SE ? 16 : 4, float>(
+  batched<ColBounds<PTS, false, SE>::KT, float>(
       W * Lin,
       [&](int idx) {
         const int j = idx / W, w = idx - j * W;
@@ -389,7 +402,7 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_col_fwd_cs(const float* __r
 // k_col_bwd_cs: inverse of k_col_fwd_cs with Eq. real-accumulation; writes the
 // first Lout rows of the real array Z [Lout][B], scaled.
 template <int PTS, bool SE>
-__global__ void __launch_bounds__(SE ? 512 : 1024) k_col_bwd_cs(const float2* __restrict__ Y, float* __restrict__ Z, int64_t B,
+__global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, false, SE>::MINB) k_col_bwd_cs(const float2* __restrict__ Y, float* __restrict__ Z, int64_t B,
                                                      int W, int Lout, int m, int q, float scale,
                                                      const float2* __restrict__ tw, FftPlan pl_m, FftPlan pl_h) {
   extern __shared__ float4 smem_raw[];
@@ -408,7 +421,7 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_col_bwd_cs(const float2* __
   {
     const int npair = W / 2;
     const int nh = m / 2 + 1;
-    batched<SE ? 8 : 2, float2>(
+    batched<ColBounds<PTS, false, SE>::KT / 2, float2>(
         npair * m,
         [&](int idx) {
           const int l = idx / npair, pw = idx - l * npair;
@@ -437,7 +450,7 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_col_bwd_cs(const float2* __
   }
   int row0 = m / 2 + 1;
   for (int r = 1; r < (SE ? 1 : (q + 1) / 2); ++r) {
-    batched<SE ? 8 : 2, float2>(
+    batched<ColBounds<PTS, false, SE>::KT / 2, float2>(
         W * m, [&](int idx) { return load(row0 + idx / W, idx % W); },
         [&](int idx, float2 v) { buf[(idx % W) * m + idx / W] = v; });
     __syncthreads();
@@ -451,7 +464,7 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_col_bwd_cs(const float2* __
   }
   if (q % 2 == 0) {
     const int e = m / 2, qh = q / 2;
-    batched<SE ? 8 : 2, float2>(
+    batched<ColBounds<PTS, false, SE>::KT / 2, float2>(
         W * e, [&](int idx) { return load(row0 + idx / W, idx % W); },
         [&](int idx, float2 v) { buf[(idx % W) * e + idx / W] = v; });
     __syncthreads();
@@ -743,7 +756,7 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_rows_adj(float2* F, float2*
 // same row of G along the last dimension, pointwise product, in place over F.
 // ---------------------------------------------------------------------------
 template <int PTS, bool SE>
-__global__ void __launch_bounds__(SE ? 512 : 1024) k_rows_cconv(float2* F, const float2* __restrict__ G, int Lr, int m, int q,
+__global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, false, SE>::MINB) k_rows_cconv(float2* F, const float2* __restrict__ G, int Lr, int m, int q,
                                                      int p, float scale, const float2* __restrict__ tw, FftPlan pl) {
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
@@ -756,7 +769,7 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_rows_cconv(float2* F, const
   for (int j = tid; j < Lr; j += T) acc[j] = make_float2(0.f, 0.f);
   __syncthreads();
   auto residue_pass = [&](int r) __attribute__((always_inline)) {
-    batched<SE ? 8 : 2, float2>(
+    batched<ColBounds<PTS, false, SE>::KT / 2, float2>(
         2 * m,
         [&](int idx) {
           const int arr = idx / m, s = idx - arr * m;
@@ -807,7 +820,7 @@ struct RowsIO {
 };
 
 template <int PTS, bool SE>
-__global__ void __launch_bounds__(SE ? 512 : 1024) k_rows_fft(RowsIO io, int mode, int n, const float2* __restrict__ tw,
+__global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, false, SE>::MINB) k_rows_fft(RowsIO io, int mode, int n, const float2* __restrict__ tw,
                                                    int twmul, FftPlan pl) {
   extern __shared__ float4 smem_raw[];
   float2* buf = reinterpret_cast<float2*>(smem_raw);
@@ -825,11 +838,11 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_rows_fft(RowsIO io, int mod
   auto put = [&](int j, float2 v) { buf[j] = v; };
   if (mode == 0) {
     const float* s = reinterpret_cast<const float*>(io.src) + row * io.src_stride;
-    batched<SE ? 16 : 4, float2>(n, [&](int j) { return make_float2(s[2 * j], s[2 * j + 1]); }, put);
+    batched<ColBounds<PTS, false, SE>::KT, float2>(n, [&](int j) { return make_float2(s[2 * j], s[2 * j + 1]); }, put);
   } else if (mode == 1) {
     const float2* s = reinterpret_cast<const float2*>(io.src) + row * io.src_stride;
     // Eq. fourierPack: Z_k = 1/2 (H_k + conj H_{n-k}) + i/2 (H_k - conj H_{n-k}) zeta_{2n}^{-k}
-    batched<SE ? 8 : 2, float2>(
+    batched<ColBounds<PTS, false, SE>::KT / 2, float2>(
         n,
         [&](int k) {
           const float2 hk = s[k], hc = cconj(s[n - k]);
@@ -839,7 +852,7 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_rows_fft(RowsIO io, int mod
         put);
   } else {
     const float2* s = reinterpret_cast<const float2*>(io.src) + row * io.src_stride;
-    batched<SE ? 16 : 4, float2>(n, [&](int j) { return s[j]; }, put);
+    batched<ColBounds<PTS, false, SE>::KT, float2>(n, [&](int j) { return s[j]; }, put);
   }
   __syncthreads();
   if (mode == 0 || mode == 2)
