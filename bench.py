@@ -492,8 +492,7 @@ def compare_suite(peak_hbm, reps=20):
         h = torch.empty_like(tf)
         row = {"l2": "warm" if 12 * f.size < 126e6 else "cold (> L2)"}
         variants = [("hybridRCM", "fp32"), ("hybridCS", "fp32"), ("explicitRCM", "fp32"), ("explicit", "fp32")]
-        if len(shape) == 1:
-            variants.append(("hybridCSRCM", "fp32"))
+        variants.append(("hybridCSRCM", "fp32"))
         if len(shape) == 3:
             variants.append(("hybridRCM", "split_bf16"))
         for algo, prec in variants:

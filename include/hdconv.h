@@ -30,9 +30,13 @@
  *                    Eq. RCM, with no unpack/pack step) and residue q/2 by
  *                    the implicitly packed half-length transform of Eqs.
  *                    forwardq2/accumulateq2, so every residue is computed on
- *                    its own (no r, q-r pairing).  1D only (single calls,
- *                    hd_conv_ext and batched plans); parameters and planner
- *                    as HD_HYBRID_CS.
+ *                    its own (no r, q-r pairing).  1D (single calls,
+ *                    hd_conv_ext, batched plans) and 2D/3D along the first
+ *                    dimension (first L outputs): there residues 0 and q/2
+ *                    run through the packed recursion of Sec. 5 and the
+ *                    other residues through hybridCS's complex rows.
+ *                    Parameters as HD_HYBRID_CS (q m >= 2L-1; m need not be
+ *                    even in 2D/3D).
  *
  * Memory: every array argument of a compute call is a DEVICE pointer owned
  * by the caller (row-major, last dimension contiguous, FP32).  h may equal f
@@ -81,7 +85,7 @@ typedef enum {
   HD_EXPLICIT_RCM = 1,
   HD_HYBRID_CS = 2,
   HD_HYBRID_RCM = 3,
-  HD_HYBRID_CSRCM = 4 /* combined CS+RCM (1D): see the algorithm list above */
+  HD_HYBRID_CSRCM = 4 /* combined CS+RCM: see the algorithm list above */
 } hd_algo;
 
 /* Arithmetic of the DFT stages.  HD_FP32 everywhere; HD_SPLIT_BF16 runs the

@@ -364,29 +364,34 @@ hd_status adjoint_rcm_nd(hd_ctx* c, int d, const int64_t* L, int64_t batch, cons
   return s;
 }
 
+// mid: the combined CS+RCM form (hybrid_csrcm_nd) — only the residues strictly
+// between 0 and q0/2 of the first dimension, plus the period-2m0 convolution of
+// residues 0 and q0/2 added in the last pass; (m0, q0) then come from the caller.
 static hd_status hybrid_cs_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_params* prm, const float* f,
-                              const float* g, float* h, cudaStream_t st) {
+                              const float* g, float* h, cudaStream_t st, const CsMid* only_mid = nullptr) {
   // first dimension: real residues (CS); middle (3D): complex hybrid; rows: complex conv
   const int64_t B0 = d == 2 ? L[1] : L[1] * L[2];  // real columns of the first pass
   int64_t m0, q0;
   if (prm && prm[0].m > 0) {
     m0 = prm[0].m;
     q0 = prm[0].q > 0 ? prm[0].q : (2 * L[0] - 1 + m0 - 1) / m0;
-    if (q0 * m0 < 2 * L[0] - 1 || (q0 % 2 == 0 && m0 % 2 == 1)) return HD_EINVAL;
+    if (q0 * m0 < 2 * L[0] - 1 || (!only_mid && q0 % 2 == 0 && m0 % 2 == 1)) return HD_EINVAL;
   } else {
     m0 = ladder_ceil(L[0]);
     while (m0 % 2) m0 = ladder_ceil(m0 + 1);
     q0 = 2;
   }
-  if (m0 % 2) return HD_EUNSUPPORTED;  // residue 0 pairs columns through an even-length real DFT
+  const CsMid md = only_mid ? *only_mid : CsMid{0, nullptr, 1, 0, 0.f};
+  // residue 0 pairs columns through an even-length real DFT (not run in the mid form)
+  if (m0 % 2 && !md.only) return HD_EUNSUPPORTED;
   const int p0 = (int)((L[0] + m0 - 1) / m0);
   FftPlan pm0, ph0;
   factor_radices((int)m0, &pm0);
-  factor_radices((int)(m0 / 2), &ph0);
+  factor_radices((int)std::max<int64_t>(1, m0 / 2), &ph0);
   hd_status terr = HD_OK;
   const float2* tw0 = c->tables.get(q0 * m0, st, &terr);
   if (!tw0) return terr;
-  const int R0 = cs_rows((int)m0, (int)q0);
+  const int R0 = md.only ? (int)(((q0 + 1) / 2 - 1) * m0) : cs_rows((int)m0, (int)q0);
   ColPass mid, row;
   hd_status s = HD_OK;
   if (d == 3) {
@@ -418,9 +423,9 @@ static hd_status hybrid_cs_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_p
     float2* outF = d == 3 ? TF : SF;
     float2* outG = d == 3 ? TG : SG;
     HD_TRY(launch_col_fwd_cs(eng0, grid0, T0, smem0, st, f, outF, B0, W0, (int)L[0], (int)m0, (int)q0, p0, tw0, pm0,
-               ph0));
+               ph0, md));
     HD_TRY(launch_col_fwd_cs(eng0, grid0, T0, smem0, st, g, outG, B0, W0, (int)L[0], (int)m0, (int)q0, p0, tw0, pm0,
-               ph0));
+               ph0, md));
   }
   if (d == 3) {
     s = col_fwd(c, TF, IN_COMPLEX, 0, SF, R0, (int)L[1], Lr, mid, st);
@@ -443,9 +448,85 @@ static hd_status hybrid_cs_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_p
   {
     const float2* src = d == 3 ? TF : SF;
     HD_TRY(launch_col_bwd_cs(eng0, grid0, T0, smem0, st, src, h, B0, W0, (int)L[0], (int)m0, (int)q0,
-               1.0f / (float)(q0 * m0), tw0, pm0, ph0));
+               1.0f / (float)(q0 * m0), tw0, pm0, ph0, md));
   }
   return HD_OK;
+}
+
+// Fold modulo P along the first dimension: out[s][b] = sum_t in[t P + s][b], s < P.
+__global__ void k_fold_first(const float* __restrict__ in, float* __restrict__ out, int64_t L0, int64_t P, int64_t B) {
+  const int64_t total = P * B;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / B, b = i - s * B;
+    float acc = 0.f;
+    for (int64_t j = s; j < L0; j += P) acc += in[j * B + b];
+    out[i] = acc;
+  }
+}
+
+// The combined CS+RCM algorithm in 2D/3D (Sec. 6.3): hybridCS along the first
+// dimension with (m0, q0), q0 m0 >= 2 L0 - 1.  For even q0, residues 0 and
+// q0/2 of that dimension together are the convolution of period P = 2 m0 (in
+// the first dimension; linear, truncated, in the others) of the arrays folded
+// modulo 2 m0: even frequencies of the length-2m0 transform are residue 0, odd
+// ones residue q0/2 (Eq. resq2 with the blocks t split by parity); for odd q0,
+// residue 0 alone is the period-m0 convolution of the arrays folded modulo m0
+// (Sec. 3.1.1).  That part is computed by implicit packing, the hybridRCM
+// recursion (packed rows, C_1 within each residue), as the linear convolution
+// of the folded arrays (first-dimension extent 2P - 1) folded back;
+// residues 1..ceil(q0/2)-1 run through hybridCS's complex path, and the last
+// pass adds (2 / q0, or 1 / q0 for odd q0) times the period-P result.  With
+// q0 = 2 there is no other residue and the arrays need no folding: the call is
+// the hybridRCM recursion with (m0, 2) along the first dimension.
+static hd_status hybrid_csrcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_params* prm, const float* f,
+                                 const float* g, float* h, cudaStream_t st) {
+  int64_t m0, q0;
+  if (prm && prm[0].m > 0) {
+    m0 = prm[0].m;
+    q0 = prm[0].q > 0 ? prm[0].q : (2 * L[0] - 1 + m0 - 1) / m0;
+    if (q0 * m0 < 2 * L[0] - 1) return fail(HD_EINVAL, "hybridCSRCM needs q m >= 2L-1 in the first dimension");
+  } else {
+    m0 = ladder_ceil(L[0]);
+    q0 = 2;
+  }
+  hd_dim_params pr[3] = {};
+  for (int i = 1; i < d; ++i) pr[i] = prm ? prm[i] : hd_dim_params{0, 0};
+  if (q0 <= 2) {
+    pr[0] = hd_dim_params{(int32_t)m0, 2};
+    const bool user = prm != nullptr;
+    return hybrid_rcm_nd(c, d, L, user ? pr : nullptr, f, g, h, st, false, 1, L);
+  }
+  // q0 even: residues 0 and q0/2 (period 2 m0); q0 odd: residue 0 alone (period m0)
+  const bool even = q0 % 2 == 0;
+  const int64_t P = even ? 2 * m0 : m0;
+  const int64_t B = d == 2 ? L[1] : L[1] * L[2];
+  const int64_t Lf[3] = {P, L[1], d == 3 ? L[2] : 1};
+  const int64_t Kf[3] = {2 * P - 1, L[1], d == 3 ? L[2] : 1};
+  // scratch: the two folded arrays and the linear convolution of period extent
+  const size_t nfold = (size_t)(P * B), nlin = (size_t)((2 * P - 1) * B);
+  float* tmp = nullptr;
+  if (cudaMallocAsync(&tmp, sizeof(float) * (2 * nfold + nlin), st) != cudaSuccess)
+    return fail(HD_ENOMEM, "hybridCSRCM scratch");
+  float* ff = tmp;
+  float* fg = tmp + nfold;
+  float* lin = tmp + 2 * nfold;
+  const int blocks = (int)std::min<int64_t>((int64_t)(nfold + 255) / 256, 148 * 32);
+  k_fold_first<<<blocks, 256, 0, st>>>(f, ff, L[0], P, B);
+  k_fold_first<<<blocks, 256, 0, st>>>(g, fg, L[0], P, B);
+  hd_status s = HD_OK;
+  if (cudaGetLastError() != cudaSuccess) s = fail(HD_ECUDA, "hybridCSRCM fold launch");
+  if (s == HD_OK) {
+    hd_dim_params pf[3] = {hd_dim_params{(int32_t)m0, even ? 4 : 2}, pr[1], pr[2]};  // q m >= 2 P - 1
+    s = hybrid_rcm_nd(c, d, Lf, prm ? pf : nullptr, ff, fg, lin, st, false, 1, Kf);
+  }
+  if (s == HD_OK) {
+    const CsMid mid{1, lin, (int)P, (int)(2 * P - 1), (even ? 2.0f : 1.0f) / (float)q0};
+    hd_dim_params pc[3] = {hd_dim_params{(int32_t)m0, (int32_t)q0}, pr[1], pr[2]};
+    s = hybrid_cs_nd(c, d, L, pc, f, g, h, st, &mid);
+    if (s != HD_OK) fail(s, "hybridCSRCM: the middle residues");
+  }
+  cudaFreeAsync(tmp, st);
+  return s;
 }
 
 hd_status explicit_nd(hd_ctx* c, hd_algo algo, int d, const int64_t* Lin, const float* f, const float* g, float* h,
@@ -590,7 +671,10 @@ hd_status conv_nd_ext(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, con
       return hybrid_cs_nd(c, d, L, prm, f, g, h, st);
     case HD_EXPLICIT:
     case HD_EXPLICIT_RCM: return explicit_nd(c, algo, d, L, f, g, h, st, K);
-    case HD_HYBRID_CSRCM: return fail(HD_EUNSUPPORTED, "hybridCSRCM is built for 1D");
+    case HD_HYBRID_CSRCM:
+      if (full) return fail(HD_EUNSUPPORTED, "hybridCSRCM in 2D/3D returns the first L outputs only");
+      if (prec != HD_FP32) return fail(HD_EUNSUPPORTED, "hybridCSRCM: FP32 only");
+      return hybrid_csrcm_nd(c, d, L, prm, f, g, h, st);
   }
   return fail(HD_EINVAL, "unknown algorithm");
 }

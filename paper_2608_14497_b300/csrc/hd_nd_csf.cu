@@ -5,9 +5,9 @@ namespace hd {
 
 cudaError_t launch_col_fwd_cs(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, const float* X, float2* Y,
                               int64_t B, int W, int Lin, int m, int q, int p, const float2* tw, FftPlan pl_m,
-                              FftPlan pl_h) {
+                              FftPlan pl_h, CsMid mid) {
   auto k = (e == Eng::SE && T <= 256) ? k_col_fwd_cs<16, true> : e == Eng::SE ? k_col_fwd_cs<kPtsSE, true> : k_col_fwd_cs<kPts, false>;
-  return launch_kernel(k, grid, T, smem, st, X, Y, B, W, Lin, m, q, p, tw, pl_m, pl_h);
+  return launch_kernel(k, grid, T, smem, st, X, Y, B, W, Lin, m, q, p, tw, pl_m, pl_h, mid);
 }
 
 }  // namespace hd

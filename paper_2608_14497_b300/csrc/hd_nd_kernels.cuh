@@ -290,6 +290,19 @@ __global__ void __launch_bounds__(ColBounds<PTS, TC, SE>::T, ColBounds<PTS, TC, 
 //   residues 1..ceil(q/2)-1: m rows each (Eq. forwardr)
 //   residue q/2 (q even):    m/2 rows (Eq. forwardq2)
 // ---------------------------------------------------------------------------
+// The combined CS+RCM form (Sec. 6.3) runs hybridCS's residues strictly
+// between 0 and q/2 only (rows (r - 1) m + l); residues 0 and q/2 come from
+// an implicitly packed convolution whose real result `add` ([addlen][B], the
+// linear convolution along the first dimension of the arrays folded modulo
+// `period` = 2m) is folded modulo `period` and added, times add_scale, in the
+// last pass.
+struct CsMid {
+  int only;
+  const float* add;
+  int period, addlen;
+  float add_scale;
+};
+
 __host__ __device__ __forceinline__ int cs_rows(int m, int q) {
   return (m / 2 + 1) + ((q + 1) / 2 - 1) * m + ((q % 2 == 0) ? m / 2 : 0);
 }
@@ -297,7 +310,8 @@ __host__ __device__ __forceinline__ int cs_rows(int m, int q) {
 template <int PTS, bool SE>
 __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, false, SE>::MINB) k_col_fwd_cs(const float* __restrict__ X, float2* __restrict__ Y, int64_t B,
                                                      int W, int Lin, int m, int q, int p,
-                                                     const float2* __restrict__ tw, FftPlan pl_m, FftPlan pl_h) {
+                                                     const float2* __restrict__ tw, FftPlan pl_m, FftPlan pl_h,
+                                                     CsMid mid) {
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   const int64_t b0 = (int64_t)blockIdx.x * W;
@@ -323,7 +337,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
     if (b < B) Y[(int64_t)row * B + b] = v;
   };
   // residue 0: pairs of real columns as one complex column
-  {
+  if (!mid.only) {
     const int npair = W / 2;
     for (int idx = tid; idx < npair * m; idx += T) {
       const int pw = idx / m, s = idx - pw * m;
@@ -348,7 +362,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
     }
     __syncthreads();
   }
-  int row0 = m / 2 + 1;
+  int row0 = mid.only ? 0 : m / 2 + 1;
   // SE: q = 2, so no residue lies strictly between 0 and q/2
   for (int r = 1; r < (SE ? 1 : (q + 1) / 2); ++r) {
     for (int idx = tid; idx < W * m; idx += T) {
@@ -376,7 +390,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
     __syncthreads();
     row0 += m;
   }
-  if (q % 2 == 0) {
+  if (q % 2 == 0 && !mid.only) {
     const int e = m / 2, qh = q / 2;
     for (int idx = tid; idx < W * e; idx += T) {
       const int w = idx / e, bb = idx - w * e;
@@ -404,7 +418,8 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
 template <int PTS, bool SE>
 __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, false, SE>::MINB) k_col_bwd_cs(const float2* __restrict__ Y, float* __restrict__ Z, int64_t B,
                                                      int W, int Lout, int m, int q, float scale,
-                                                     const float2* __restrict__ tw, FftPlan pl_m, FftPlan pl_h) {
+                                                     const float2* __restrict__ tw, FftPlan pl_m, FftPlan pl_h,
+                                                     CsMid mid) {
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   const int64_t b0 = (int64_t)blockIdx.x * W;
@@ -418,7 +433,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
   };
   for (int idx = tid; idx < W * Lout; idx += T) acc[idx] = 0.f;
   // residue 0: complex-to-real, two columns per complex DFT: Z_l = H_w[l] + i H_{w+1}[l]
-  {
+  if (!mid.only) {
     const int npair = W / 2;
     const int nh = m / 2 + 1;
     batched<ColBounds<PTS, false, SE>::KT / 2, float2>(
@@ -448,7 +463,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
     }
     __syncthreads();
   }
-  int row0 = m / 2 + 1;
+  int row0 = mid.only ? 0 : m / 2 + 1;
   for (int r = 1; r < (SE ? 1 : (q + 1) / 2); ++r) {
     batched<ColBounds<PTS, false, SE>::KT / 2, float2>(
         W * m, [&](int idx) { return load(row0 + idx / W, idx % W); },
@@ -462,7 +477,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
     __syncthreads();
     row0 += m;
   }
-  if (q % 2 == 0) {
+  if (q % 2 == 0 && !mid.only) {
     const int e = m / 2, qh = q / 2;
     batched<ColBounds<PTS, false, SE>::KT / 2, float2>(
         W * e, [&](int idx) { return load(row0 + idx / W, idx % W); },
@@ -482,7 +497,15 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
   for (int idx = tid; idx < W * Lout; idx += T) {
     const int j = idx / W, w = idx - j * W;
     const int64_t b = b0 + w;
-    if (b < B) Z[(int64_t)j * B + b] = acc[w * Lout + j] * scale;
+    if (b >= B) continue;
+    float v = acc[w * Lout + j] * scale;
+    if (mid.add) {  // residues 0 and q/2: the period-2m convolution (the linear one folded)
+      const int s = j % mid.period;
+      float a = mid.add[(int64_t)s * B + b];
+      if (s + mid.period < mid.addlen) a += mid.add[(int64_t)(s + mid.period) * B + b];
+      v += mid.add_scale * a;
+    }
+    Z[(int64_t)j * B + b] = v;
   }
 }
 
@@ -925,10 +948,10 @@ cudaError_t launch_col_bwd(Eng e, unsigned grid, int T, size_t smem, cudaStream_
                            FftPlan pl);
 cudaError_t launch_col_fwd_cs(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, const float* X, float2* Y,
                               int64_t B, int W, int Lin, int m, int q, int p, const float2* tw, FftPlan pl_m,
-                              FftPlan pl_h);
+                              FftPlan pl_h, CsMid mid = CsMid{0, nullptr, 1, 0, 0.f});
 cudaError_t launch_col_bwd_cs(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, const float2* Y, float* Z,
                               int64_t B, int W, int Lout, int m, int q, float scale, const float2* tw, FftPlan pl_m,
-                              FftPlan pl_h);
+                              FftPlan pl_h, CsMid mid = CsMid{0, nullptr, 1, 0, 0.f});
 // O: output rows (rg.Kout per row); O = F (in place) when Kout = Lrow.
 cudaError_t launch_rows_rcm(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, float2* F, const float2* G,
                             float2* O, RowGeom rg, float scale, const float2* tw, FftPlan pl);

@@ -93,8 +93,42 @@ def test_batched_plan(hd):
         assert rel_l2(h[o:o + L], ref[o:o + L]) <= TOL, L
 
 
-def test_nd_unsupported(hd):
+def test_nd_full_output_unsupported(hd):
     f = dev(np.ones((8, 8)))
     with pytest.raises(hd.HDError) as e:
-        hd.conv(f, f, algo="hybridCSRCM")
+        hd.conv(f, f, algo="hybridCSRCM", out_extent="full")
     assert e.value.status == hd.HD_EUNSUPPORTED
+
+
+# --- 2D / 3D: the combined form along the first dimension ------------------------
+def nd_case(shape, seed):
+    return inputs.normal_pair(shape, seed=seed)
+
+
+@pytest.mark.parametrize("shape", [(37, 50), (64, 33), (12, 9, 14)])
+@pytest.mark.parametrize("q0", [2, 3, 4, 5, 6])
+def test_nd_first_dimension_residues(hd, shape, q0):
+    """(m0, q0) along the first dimension: q0 = 2 is the packed recursion alone;
+    q0 >= 3 adds hybridCS's complex residues 1..ceil(q0/2)-1 to the
+    period-2m0 convolution of residues 0 and q0/2."""
+    L0 = shape[0]
+    m0 = -(-(2 * L0 - 1) // q0)
+    f, g = nd_case(shape, 5600 + q0 + sum(shape))
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    prm = [(m0, q0)] + [(0, 0)] * (len(shape) - 1)
+    h = run(hd, f, g, params=prm)
+    assert rel_l2(h, ref) <= TOL, (shape, m0, q0)
+    if q0 > 2:  # an odd m0 is allowed: residue q0/2 is not hybridCS's half-length transform here
+        prm = [(m0 + (1 - m0 % 2), q0)] + [(0, 0)] * (len(shape) - 1)
+        assert rel_l2(run(hd, f, g, params=prm), ref) <= TOL
+
+
+@pytest.mark.parametrize("shape", [(1024, 1024), (64, 64, 64), (1000, 700)])
+def test_nd_planner_and_large(hd, shape):
+    f, g = inputs.uniform_pair(shape, seed=5700 + shape[0])
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    assert rel_l2(run(hd, f, g), ref) <= TOL
+    if len(shape) == 2:  # p0 = 4 blocks, q0 = 8 residues along the first dimension
+        m0 = -(-shape[0] // 4)
+        prm = [(m0, -(-(2 * shape[0] - 1) // m0)), (0, 0)]
+        assert rel_l2(run(hd, f, g, params=prm), ref) <= TOL
