@@ -89,9 +89,13 @@ typedef enum {
 } hd_algo;
 
 /* Arithmetic of the DFT stages.  HD_FP32 everywhere; HD_SPLIT_BF16 runs the
- * radix-16 stages of the 3D path on tensor cores with hi/lo bfloat16 operands
- * and FP32 accumulation (returns HD_EUNSUPPORTED where not available). */
-typedef enum { HD_FP32 = 0, HD_SPLIT_BF16 = 1 } hd_prec;
+ * radix-16 stages of the 2D/3D hybridRCM path on tensor cores with hi/lo
+ * bfloat16 operands and FP32 accumulation (returns HD_EUNSUPPORTED where not
+ * available).  HD_SPLIT_FP16 (hi/lo half precision) is declared for the same
+ * stage and always returns HD_EUNSUPPORTED: the spectra of the 2D/3D
+ * configurations exceed half precision's range (max 65504) before the
+ * normalisation, and the bfloat16 split already meets the 5e-5 bar. */
+typedef enum { HD_FP32 = 0, HD_SPLIT_BF16 = 1, HD_SPLIT_FP16 = 2 } hd_prec;
 
 /* Hybrid parameters of one dimension (Sec. 2: p = ceil(L/m), q = ceil(M/m)).
  * m = 0 lets the planner choose (m, q).  For HD_HYBRID_CS the data are real

@@ -17,11 +17,11 @@ LIB_PATH = os.path.join(HERE, "libhdconv.so")
 
 HD_OK, HD_EINVAL, HD_ENOMEM, HD_ECUDA, HD_ETIMEOUT, HD_EUNSUPPORTED = range(6)
 HD_EXPLICIT, HD_EXPLICIT_RCM, HD_HYBRID_CS, HD_HYBRID_RCM, HD_HYBRID_CSRCM = range(5)
-HD_FP32, HD_SPLIT_BF16 = range(2)
+HD_FP32, HD_SPLIT_BF16, HD_SPLIT_FP16 = range(3)
 
 ALGOS = {"explicit": HD_EXPLICIT, "explicitRCM": HD_EXPLICIT_RCM, "hybridCS": HD_HYBRID_CS,
          "hybridRCM": HD_HYBRID_RCM, "hybridCSRCM": HD_HYBRID_CSRCM}
-PRECS = {"fp32": HD_FP32, "split_bf16": HD_SPLIT_BF16}
+PRECS = {"fp32": HD_FP32, "split_bf16": HD_SPLIT_BF16, "split_fp16": HD_SPLIT_FP16}
 
 # Every symbol include/hdconv.h declares.
 EXPORTS = ("hd_create", "hd_destroy", "hd_conv1d", "hd_conv2d", "hd_conv3d", "hd_batch_plan_create",

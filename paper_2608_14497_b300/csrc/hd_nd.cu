@@ -663,6 +663,7 @@ hd_status conv_nd_ext(hd_ctx* c, hd_algo algo, hd_prec prec, const float* f, con
   for (int i = 0; i < d; ++i) full = full || K[i] != L[i];
   // split precision: the radix-16 passes of hybridRCM's 2D/3D kernels on tensor cores
   if (prec == HD_SPLIT_BF16 && algo != HD_HYBRID_RCM) return fail(HD_EUNSUPPORTED, "split precision: hybridRCM only");
+  if (prec == HD_SPLIT_FP16) return fail(HD_EUNSUPPORTED, "split precision: bfloat16 only (half precision range)");
   if (prec != HD_FP32 && prec != HD_SPLIT_BF16) return fail(HD_EINVAL, "unknown precision");
   switch (algo) {
     case HD_HYBRID_RCM: return hybrid_rcm_nd(c, d, L, prm, f, g, h, st, prec == HD_SPLIT_BF16, 1, K);

@@ -77,3 +77,10 @@ def test_split_precision_other_algorithms_rejected(hd):
     with pytest.raises(hd.HDError) as e:
         hd.conv(f, f, algo="explicit", prec="split_bf16")
     assert e.value.status == hd.HD_EUNSUPPORTED
+
+
+def test_split_fp16_declared_unsupported(hd):
+    f = torch.zeros((8, 8), device="cuda")
+    with pytest.raises(hd.HDError) as e:
+        hd.conv(f, f, algo="hybridRCM", prec="split_fp16")
+    assert e.value.status == hd.HD_EUNSUPPORTED
