@@ -490,3 +490,85 @@ def conv_hybrid_cs_nd(f, g, params, K=None):
     if K is not None:
         out = out[tuple(slice(0, k) for k in K)]
     return out
+
+
+# ---------------------------------------------------------------------------
+# App. A: the inner loop for many blocks -- the sums over the blocks t of
+# Eq. forwardr, and the sum over the residues of Eq. accumulation, as q-point
+# DFTs (the blocks t >= p are zero).  Used with the n-array product of Sec.
+# 4.1 and the per-array block counts of Sec. 7.
+# ---------------------------------------------------------------------------
+def inner_loop_forward(x, m, q):
+    """F[q l + r] = sum_s zeta_m^{ls} zeta_{qm}^{rs} sum_t zeta_q^{rt} x_{tm+s}:
+    the sum over t as one q-point DFT of the q blocks (zero for t >= p)."""
+    x = np.asarray(x, dtype=np.complex128)
+    if len(x) > q * m:
+        raise ValueError("more than q blocks")
+    blocks = np.zeros((q, m), dtype=np.complex128)
+    blocks.reshape(-1)[: len(x)] = x
+    Y = dft(blocks, +1, axis=0)                      # Y[r][s] = sum_t zeta_q^{rt} x_t[s]
+    r = np.arange(q)[:, None]
+    s = np.arange(m)[None, :]
+    Y = Y * zeta(q * m, r * s)                       # pre-twiddle zeta_{qm}^{rs}
+    Fr = dft(Y, +1, axis=1)                          # Fr[r][l]
+    F = np.empty(q * m, dtype=np.complex128)
+    for rr in range(q):
+        F[rr::q] = Fr[rr]                            # k = q l + r
+    return F
+
+
+def inner_loop_backward(H, m, q, K):
+    """h_{tm+s} = sum_r zeta_q^{-rt} zeta_{qm}^{-rs} sum_l zeta_m^{-ls} H[q l + r]
+    (Eqs. accumulator and accumulation, unscaled): the sum over r as one
+    backward q-point DFT; the first K entries."""
+    Hr = np.stack([H[rr::q] for rr in range(q)])   # Hr[r][l]
+    w = dft(Hr, -1, axis=1)                          # w[r][s]
+    r = np.arange(q)[:, None]
+    s = np.arange(m)[None, :]
+    v = w * zeta(q * m, -r * s)
+    h = dft(v, -1, axis=0)                           # h[t][s]
+    return h.reshape(-1)[:K]
+
+
+def conv_rcm_inner_loop(xs, m, q, K=None):
+    """x^1 * ... * x^n (real 1D arrays of any lengths) by implicit packing with
+    the inner loop: pack each array, transform, R^1 = F^1 and R^j = R^{j-1} RCM F^j
+    by the residue-pair formulas (Eqs. Akn, Rnk, RnMk: Eqs. Hr/Hr-conj with
+    R^{j-1} in F's place), transform back, scale 1/(qm), unpack the first K
+    (default max L_i).  Needs 2 q m >= sum L_i - n + 1."""
+    Ls = [len(x) for x in xs]
+    S = sum(Ls) - len(xs) + 1
+    if 2 * q * m < S:
+        raise ValueError("does not dealias")
+    K = max(Ls) if K is None else K
+    R = inner_loop_forward(pack(xs[0]), m, q)
+    for x in xs[1:]:
+        R = rcm_residue_pairs(R, inner_loop_forward(pack(x), m, q), m, q)
+    ht = inner_loop_backward(R, m, q, (K + 1) // 2) / (q * m)
+    return unpack_real(ht, K)
+
+
+def conv_cs_inner_loop(f, g, m, q, K=None):
+    """hybridCS with the inner loop for real f, g: the q-point DFT over the
+    blocks of real data is Hermitian in r, so residues r <= q/2 are formed,
+    multiplied pointwise and transformed back; the sum over r takes
+    v_{q-r} = conj v_r (Eq. hrHerm), and the real part is the result (Eq.
+    real-accumulation), scaled 1/(qm).  Needs q m >= 2L - 1."""
+    L = len(f)
+    if q * m < 2 * L - 1:
+        raise ValueError("does not dealias")
+    K = L if K is None else K
+    F = inner_loop_forward(np.asarray(f, dtype=np.float64), m, q)
+    G = inner_loop_forward(np.asarray(g, dtype=np.float64), m, q)
+    H = np.zeros(q * m, dtype=np.complex128)
+    for rr in range(q // 2 + 1):
+        H[rr::q] = F[rr::q] * G[rr::q]
+    Hr = np.stack([H[rr::q] for rr in range(q)])
+    w = dft(Hr, -1, axis=1)
+    r = np.arange(q)[:, None]
+    s = np.arange(m)[None, :]
+    v = w * zeta(q * m, -r * s)
+    for rr in range(q // 2 + 1, q):
+        v[rr] = np.conj(v[q - rr])                   # Eq. hrHerm
+    h = dft(v, -1, axis=0).reshape(-1)[:K]
+    return h.real / (q * m)

@@ -487,3 +487,45 @@ def test_planted_multi_reversed_operand_is_caught(monkeypatch):
     monkeypatch.setattr(oracle, "_multi", lambda name, ys, K: orig(name, [ys[0], ys[1][::-1]] + list(ys[2:]), K))
     S = 40 + 7 + 9 - 2
     assert not _multi_matches(oracle.direct_conv_multi(xs, S), xi, S)
+
+
+# --- App. A inner loop (the three-kernel path's arithmetic), pinned against O1 ---
+@pytest.mark.parametrize("L,m,q", [(1, 1, 2), (7, 2, 4), (37, 4, 10), (100, 8, 14), (64, 16, 8), (250, 10, 26)])
+def test_inner_loop_forward_is_eq_forwardr(L, m, q):
+    rng = np.random.default_rng(40 + L)
+    x = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    if L > q * m:
+        pytest.skip("more blocks than residues")
+    assert np.allclose(steps.inner_loop_forward(x, m, q), steps.hybrid_forward(x, m, q), atol=1e-9)
+
+
+@pytest.mark.parametrize("L,m,q", [(1, 1, 2), (9, 2, 6), (37, 4, 10), (101, 8, 14), (256, 16, 16), (300, 20, 16)])
+def test_inner_loop_rcm_and_cs_match_direct(L, m, q):
+    rng = np.random.default_rng(50 + L)
+    f, g = rng.standard_normal(L), rng.standard_normal(L)
+    for K in (L, 2 * L - 1):
+        ref = oracle.direct_conv(f, g, (K,))
+        if 2 * q * m >= 2 * L - 1:
+            assert rel_l2(steps.conv_rcm_inner_loop([f, g], m, q, K), ref) < 1e-12
+        if q * m >= 2 * L - 1:
+            assert rel_l2(steps.conv_cs_inner_loop(f, g, m, q, K), ref) < 1e-12
+
+
+@pytest.mark.parametrize("lengths,m,q", [((50, 7), 8, 8), ((30, 20, 12), 8, 8), ((13, 1, 5, 9), 4, 8), ((64,) * 5, 16, 20)])
+def test_inner_loop_n_arrays_unequal_match_direct(lengths, m, q):
+    """Sec. 4.1 (R^j = R^{j-1} RCM F^j) and Sec. 7 (separate block counts), the
+    reading of Eq. RnMk with conj(A_k)."""
+    rng = np.random.default_rng(60 + sum(lengths))
+    xs = [rng.standard_normal(L) for L in lengths]
+    S = sum(lengths) - len(lengths) + 1
+    ref = oracle.direct_conv_multi(xs, S)
+    assert rel_l2(steps.conv_rcm_inner_loop(xs, m, q, S), ref) < 1e-12
+
+
+def test_planted_inner_loop_sign_is_caught(monkeypatch):
+    """A q-point DFT over the blocks with the wrong sign fails the pin."""
+    rng = np.random.default_rng(70)
+    f, g = rng.standard_normal(101), rng.standard_normal(101)
+    orig = steps.dft
+    monkeypatch.setattr(steps, "dft", lambda x, sign=+1, axis=-1: orig(x, -sign if axis == 0 else sign, axis))
+    assert rel_l2(steps.conv_rcm_inner_loop([f, g], 8, 14), oracle.direct_conv(f, g)) > 1e-3
