@@ -268,11 +268,13 @@ struct CtaState {
 // materialised zero-padded copies (real length 2L), every block t < q of them
 // is read (no block is known to be zero) and the q-point sum over t is the
 // full DFT, x_t and x_{t+C} combined before the two length-C DFTs.
-template <int C, int R3, bool EXP = false>
+// TT: threads that run the steps (the cluster kernel: Shape<R3>::T; the
+// row-pair kernel of the nD path may give a short row more threads).
+template <int C, int R3, bool EXP = false, int TT = Shape<R3>::T>
 struct Steps {
   using S = Shape<R3>;
   static constexpr int M = S::M;
-  static constexpr int T = S::T;
+  static constexpr int T = TT;
   static constexpr int Q = 2 * C;
   static constexpr int SL = M / C;                  // slice of s per CTA
   static constexpr int SW1 = (C >= 16) ? 1 : 2;     // s per phase-1 task

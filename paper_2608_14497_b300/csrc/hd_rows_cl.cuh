@@ -30,15 +30,17 @@ using cl::phys;
 template <int R3>
 struct RowShape {
   static constexpr int M = 256 * R3;
-  static constexpr int T = 32 * R3;
+  // threads per row pair: two warps for M = 256 (one warp would run 64 points
+  // per thread per pass with only the 12 CTAs per SM that shared memory allows)
+  static constexpr int T = R3 == 1 ? 64 : 32 * R3;
   static constexpr size_t SMEM = sizeof(float2) * (8 * (size_t)M + cl::Shape<R3>::TABS);
   // CTAs per SM the launch bounds ask registers for (what shared memory allows)
-  static constexpr int MINB = R3 == 1 ? 12 : R3 == 2 ? 6 : R3 <= 4 ? 3 : 2;
+  static constexpr int MINB = R3 == 1 ? 10 : R3 == 2 ? 6 : R3 <= 4 ? 3 : 2;
 };
 
 template <int R3>
 struct RowSteps {
-  using K = cl::Steps<1, R3>;
+  using K = cl::Steps<1, R3, false, RowShape<R3>::T>;
   static constexpr int M = K::M;
   static constexpr int T = K::T;
 
