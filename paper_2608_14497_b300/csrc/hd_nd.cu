@@ -170,7 +170,7 @@ static hd_status outer_params(hd_ctx* c, int64_t L, const hd_dim_params* prm, Co
 // Parameters of the last (row) dimension for the RCM rows (packed, needs
 // q m >= L) or CS rows (complex, needs q m >= 2L-1).
 static hd_status row_params(hd_ctx* c, int64_t L, bool packed, const hd_dim_params* prm, ColPass* cp,
-                            cudaStream_t st, bool cl_rows = false) {
+                            cudaStream_t st, bool cl_rows = false, bool q1 = false) {
   const int64_t Lr = packed ? (L + 1) / 2 : L;
   const int64_t need = packed ? L : 2 * L - 1;
   int64_t m, q;
@@ -189,6 +189,16 @@ static hd_status row_params(hd_ctx* c, int64_t L, bool packed, const hd_dim_para
           q = 2;
           break;
         }
+      // one residue (q = 1) when some 256 R3 >= L gives a shorter padded row
+      if (q1)
+        for (int R3 : {1, 2, 3, 4, 5, 6, 8})
+          if (256 * R3 >= L) {
+            if (256 * R3 < q * m) {
+              m = 256 * R3;
+              q = 1;
+            }
+            break;
+          }
     }
   }
   cp->m = (int)m;
@@ -206,13 +216,13 @@ struct RcmNdPlan {
   int64_t Lp, M0, M1;
 };
 static hd_status rcm_nd_plan(hd_ctx* c, int d, const int64_t* L, const hd_dim_params* prm, RcmNdPlan* P,
-                             cudaStream_t st, bool cl_rows = false) {
+                             cudaStream_t st, bool cl_rows = false, bool q1 = false) {
   P->Lp = (L[d - 1] + 1) / 2;
   for (int i = 0; i < d - 1; ++i) {
     hd_status s = outer_params(c, L[i], prm ? &prm[i] : nullptr, &P->outer[i], st);
     if (s != HD_OK) return s;
   }
-  hd_status s = row_params(c, L[d - 1], true, prm ? &prm[d - 1] : nullptr, &P->row, st, cl_rows);
+  hd_status s = row_params(c, L[d - 1], true, prm ? &prm[d - 1] : nullptr, &P->row, st, cl_rows, q1);
   if (s != HD_OK) return s;
   P->M0 = (int64_t)P->outer[0].q * P->outer[0].m;
   P->M1 = d == 3 ? (int64_t)P->outer[1].q * P->outer[1].m : 1;
@@ -276,7 +286,7 @@ static hd_status hybrid_rcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_
                                const int64_t* K = nullptr) {
   if (!K) K = L;
   RcmNdPlan P;
-  hd_status s = rcm_nd_plan(c, d, L, prm, &P, st, !tc);
+  hd_status s = rcm_nd_plan(c, d, L, prm, &P, st, !tc, !tc);
   if (s != HD_OK) return s;
   const int64_t Kp = (K[d - 1] + 1) / 2;
   const bool ext = Kp != P.Lp;  // longer rows: the row pass writes a separate buffer
@@ -297,12 +307,15 @@ static hd_status hybrid_rcm_nd(hd_ctx* c, int d, const int64_t* L, const hd_dim_
   // rows: C_1 on each row pair; arrays per residue step: {A, C, B, D} x (1 or
   // 2 residues); with q <= 2 every residue is its own partner, so 4
   const RowGeom rg = rcm_row_geom(d, batch, P, Kp);
-  if (!tc && P.row.q == 2 && rows_cl_length(P.row.m)) {
+  if (!tc && P.row.q <= 2 && rows_cl_length(P.row.m) && (P.row.q == 2 || 2 * Kp <= 2 * P.row.m)) {
     hd_status terr = HD_OK;
     const float2* tab = c->tables.get_pass_table(P.row.m, st, &terr);
     if (!tab) return terr;
-    HD_TRY(launch_rows_cl(P.row.m, (unsigned)rg.nrows, st, SF, SG, SO, rg, 1.0f / (float)(P.row.q * P.row.m),
-                          P.row.tw, tab));
+    if (P.row.q == 1)
+      HD_TRY(launch_rows_cl1(P.row.m, (unsigned)rg.nrows, st, SF, SG, SO, rg, 1.0f / (float)P.row.m, tab));
+    else
+      HD_TRY(launch_rows_cl(P.row.m, (unsigned)rg.nrows, st, SF, SG, SO, rg, 1.0f / (float)(P.row.q * P.row.m),
+                            P.row.tw, tab));
     return rcm_nd_backward(c, d, K, batch, P, SO, TF, h, OUT_UNPACK_REAL, st, tc);
   }
   const int narr = P.row.q <= 2 ? 4 : 8;

@@ -960,6 +960,9 @@ cudaError_t launch_rows_rcm(Eng e, unsigned grid, int T, size_t smem, cudaStream
 bool rows_cl_length(int m);
 cudaError_t launch_rows_cl(int m, unsigned grid, cudaStream_t st, float2* F, const float2* G, float2* O, RowGeom rg,
                            float scale, const float2* tw, const float2* tab);
+// The one-residue row pass (q = 1, M >= the real row length).
+cudaError_t launch_rows_cl1(int m, unsigned grid, cudaStream_t st, float2* F, const float2* G, float2* O, RowGeom rg,
+                            float scale, const float2* tab);
 cudaError_t launch_rows_adj_cl(int m, unsigned grid, cudaStream_t st, float2* F, float2* G, const float2* U,
                                RowGeom rg, float scale, int outs, const float2* tw, const float2* tab);
 cudaError_t launch_rows_adj(Eng e, unsigned grid, int T, size_t smem, cudaStream_t st, float2* F, float2* G,

@@ -25,6 +25,20 @@ cudaError_t launch_rows_cl(int m, unsigned grid, cudaStream_t st, float2* F, con
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_rows_cl1(int m, unsigned grid, cudaStream_t st, float2* F, const float2* G, float2* O, RowGeom rg,
+                            float scale, const float2* tab) {
+  switch (m / 256) {
+    case 1: return rows::launch_rows1<1>(grid, st, F, G, O, rg, scale, tab);
+    case 2: return rows::launch_rows1<2>(grid, st, F, G, O, rg, scale, tab);
+    case 3: return rows::launch_rows1<3>(grid, st, F, G, O, rg, scale, tab);
+    case 4: return rows::launch_rows1<4>(grid, st, F, G, O, rg, scale, tab);
+    case 5: return rows::launch_rows1<5>(grid, st, F, G, O, rg, scale, tab);
+    case 6: return rows::launch_rows1<6>(grid, st, F, G, O, rg, scale, tab);
+    case 8: return rows::launch_rows1<8>(grid, st, F, G, O, rg, scale, tab);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_rows_adj_cl(int m, unsigned grid, cudaStream_t st, float2* F, float2* G, const float2* U,
                                RowGeom rg, float scale, int outs, const float2* tw, const float2* tab) {
   switch (m / 256) {

@@ -228,6 +228,146 @@ __global__ void __launch_bounds__(RowShape<R3>::T, RowShape<R3>::MINB)
 }
 
 // ---------------------------------------------------------------------------
+// Rows with one residue (q = 1): when M >= the real row length, the packed
+// row's residue-0 transform alone dealiases (q m >= L), half the work of
+// q = 2 (rows of L <= 256 with M = 256, e.g. 3D L = 256).  Arrays [F row,
+// F partner, G row, G partner]; C_1 pairs frequency l of the row with
+// (M - l) mod M of the partner (the residue-0 rule of Eq. Hr); a row that is
+// its own partner pairs l with (M - l) mod M of itself.
+// ---------------------------------------------------------------------------
+template <int R3>
+struct Row1Shape {
+  static constexpr int M = 256 * R3;
+  static constexpr size_t SMEM = sizeof(float2) * (4 * (size_t)M + cl::Shape<R3>::TABS);
+  static constexpr int MINB = R3 == 1 ? 12 : R3 == 2 ? 8 : R3 <= 4 ? 4 : 2;
+};
+
+template <int R3>
+__global__ void __launch_bounds__(RowShape<R3>::T, Row1Shape<R3>::MINB)
+    k_rows_cl1(float2* F, const float2* __restrict__ G, float2* O, RowGeom rg, float scale,
+               const float2* __restrict__ tab) {
+  using S = RowSteps<R3>;
+  using K = typename S::K;
+  constexpr int M = S::M, T = S::T;
+  constexpr int U = M / 2 / T;
+  const int row = blockIdx.x;
+  const int prow = row_partner(row, rg);
+  if (prow < row) return;
+  extern __shared__ float4 smem_raw[];
+  float2* arr = reinterpret_cast<float2*>(smem_raw);
+  float2* tws = arr + 4 * M;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < cl::Shape<R3>::TABS / 2; i += T) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(tws + 2 * i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(tab + 2 * i) : "memory");
+  }
+  const int Lp = rg.Lrow, Kp = rg.Kout;
+  const float2* zt = tab + cl::Shape<R3>::TABZ;
+  const bool self = (prow == row);
+  const int nr = self ? 2 : 4;
+  {
+    // all loads in flight first: rows [F row, F partner, G row, G partner] (self: [F, G])
+    const float2* src[4] = {F + (int64_t)row * Lp, F + (int64_t)prow * Lp, G + (int64_t)row * Lp,
+                            G + (int64_t)prow * Lp};
+    if (self) src[1] = src[2];
+    float2 v[4][U][2];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int s = 2 * (tid + i * T);
+        const bool on = r < nr;
+        v[r][i][0] = on && s < Lp ? src[r][s] : make_float2(0.f, 0.f);
+        v[r][i][1] = on && s + 1 < Lp ? src[r][s + 1] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (r < nr)
+#pragma unroll
+        for (int i = 0; i < U; ++i) cl::sts4(arr + r * M + phys(2 * (tid + i * T)), v[r][i][0], v[r][i][1]);
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  if (self) {
+    K::template pass1<1, 2, 2>(arr, tid, tws);
+    __syncthreads();
+    K::template pass2<1, 2, 2>(arr, tid, tws);
+    __syncthreads();
+    K::template pass3<1, 2>(arr, tid);
+    __syncthreads();
+    float2* Fa = arr;
+    const float2* Ga = arr + M;
+    for (int p = tid; p < M; p += T) {
+      const int l = cl::digit_freq(p, R3);
+      const int ls = (l == 0) ? 0 : M - l;
+      if (l > ls) continue;
+      const int ps = cl::digit_pos(ls, R3);
+      float2 A = Fa[phys(p)], Ac = Fa[phys(ps)];
+      const bool own = (ls == l);
+      K::rcm_pair(A, Ga[phys(p)], Ac, Ga[phys(ps)], K::rcm_factor(cl::ldg2(zt + p), make_float2(1.f, 0.f)), own);
+      Fa[phys(p)] = A;
+      if (!own) Fa[phys(ps)] = Ac;
+    }
+    __syncthreads();
+    K::template pass3<-1, 1>(arr, tid);
+    __syncthreads();
+    K::template pass2<-1, 1, 1>(arr, tid, tws);
+    __syncthreads();
+    K::template pass1<-1, 1, 1>(arr, tid, tws);
+    __syncthreads();
+  } else {
+    K::template pass1<1, 4, 2>(arr, tid, tws);
+    __syncthreads();
+    K::template pass2<1, 4, 2>(arr, tid, tws);
+    __syncthreads();
+    K::template pass3<1, 4>(arr, tid);
+    __syncthreads();
+    float2* Fr = arr;
+    float2* Fp = arr + M;
+    const float2* Gr = arr + 2 * M;
+    const float2* Gp = arr + 3 * M;
+    for (int p = tid; p < M; p += T) {
+      const int l = cl::digit_freq(p, R3);
+      const int ps = cl::digit_pos(l == 0 ? 0 : M - l, R3);
+      float2 A = Fr[phys(p)], Cs = Fp[phys(ps)];
+      K::rcm_pair(A, Gr[phys(p)], Cs, Gp[phys(ps)], K::rcm_factor(cl::ldg2(zt + p), make_float2(1.f, 0.f)), false);
+      Fr[phys(p)] = A;
+      Fp[phys(ps)] = Cs;
+    }
+    __syncthreads();
+    K::template pass3<-1, 2>(arr, tid);
+    __syncthreads();
+    K::template pass2<-1, 2, 1>(arr, tid, tws);
+    __syncthreads();
+    K::template pass1<-1, 2, 1>(arr, tid, tws);
+    __syncthreads();
+  }
+  // h~_s = w_0[s] * scale, s < Kp <= M
+  for (int r = 0; r < (self ? 1 : 2); ++r) {
+    float2* x = O + (int64_t)(r ? prow : row) * Kp;
+    const float2* a = arr + r * M;
+    for (int k = tid; k < M / 2; k += T) {
+      const int s = 2 * k;
+      if (s >= Kp) continue;
+      float2 w0, w1;
+      cl::lds4(a + phys(s), w0, w1);
+      x[s] = cscale(w0, scale);
+      if (s + 1 < Kp) x[s + 1] = cscale(w1, scale);
+    }
+  }
+}
+
+template <int R3>
+cudaError_t launch_rows1(unsigned grid, cudaStream_t st, float2* F, const float2* G, float2* O, RowGeom rg,
+                         float scale, const float2* tab) {
+  auto k = k_rows_cl1<R3>;
+  cudaError_t e = smem_optin((const void*)k, Row1Shape<R3>::SMEM);
+  if (e != cudaSuccess) return e;
+  k<<<grid, RowShape<R3>::T, Row1Shape<R3>::SMEM, st>>>(F, G, O, rg, scale, tab);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // The adjoint's row pass: C_1 applied to (U, G) and (U, F) for the row pair,
 // with U = rev(grad_h)'s outer spectra transformed once and only read; the
 // products replace G's and F's rows (outs bit 0: G, bit 1: F).  Arrays: for
