@@ -150,3 +150,19 @@ def test_2d_composite_last_pass(hd, algo, shape):
     f, g = inputs.uniform_pair(shape, seed=sum(shape))
     ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
     assert rel_l2(run(hd, f, g, algo), ref) <= TOL
+
+
+# Rows whose real length fits 256 R3 take the one-residue row pass (q = 1):
+# packed row lengths 65..128 with L <= 256, 129..256 with L <= 512, ragged and
+# odd, first L outputs and the full 2L-1 (output rows up to M).
+@pytest.mark.parametrize("shape", [(40, 200), (17, 256), (9, 129), (6, 7, 250), (5, 3, 511), (33, 500)])
+@pytest.mark.parametrize("full", [False, True])
+def test_one_residue_rows(hd, shape, full):
+    f, g = inputs.normal_pair(shape, seed=900 + sum(shape))
+    K = tuple(2 * n - 1 for n in shape) if full else tuple(shape)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64), K)
+    tf = torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).cuda()
+    tg = torch.from_numpy(np.ascontiguousarray(g, dtype=np.float32)).cuda()
+    h = hd.conv(tf, tg, algo="hybridRCM", out_extent=K if full else None)
+    torch.cuda.synchronize()
+    assert rel_l2(h.cpu().numpy().astype(np.float64), ref) <= TOL
