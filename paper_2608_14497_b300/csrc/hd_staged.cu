@@ -90,9 +90,17 @@ __device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p 
 // be scheduled once all of its CTAs are running (launch_dependents), and the
 // next stage does its set-up (tables) before it waits for the previous grid to
 // complete and flush its writes (wait).  The wait returns when the previous
-// grid ends; it is not a spin on memory.
+// grid ends; it is not a spin on memory.  It takes the pointer to the previous
+// grid's output through the asm and hands it back: the loads through that
+// pointer then depend on the wait, whereas a const __restrict__ pointer that
+// only sits behind a "memory" clobber lets the compiler hoist unconditional
+// loads above the wait and read the output before it is written.
 __device__ __forceinline__ void allow_next_stage() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void wait_prev_stage() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <typename T>
+__device__ __forceinline__ T* after_prev_stage(T* p) {
+  asm volatile("griddepcontrol.wait;" : "+l"(p) : : "memory");
+  return p;
+}
 
 // Stages A and C move the W x q tile of a CTA between global memory (W
 // consecutive s of each row t or r: contiguous) and shared memory (one array
@@ -206,8 +214,7 @@ __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_c(const floa
   const int s0 = blockIdx.x * G.W;
   const int q = G.q, M = G.M, ldb = G.ldb, nt = G.q * (G.W / V);
   const DivF dq = make_div(q);
-  const float2* Wi = Wr + (int64_t)blockIdx.z * G.rows * M;
-  wait_prev_stage();
+  const float2* Wi = after_prev_stage(Wr) + (int64_t)blockIdx.z * G.rows * M;
   float2 v[KT][V];
 #pragma unroll
   for (int k = 0; k < KT; ++k) {
@@ -282,6 +289,216 @@ __global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_c(const floa
         for (int i = 0; i < V; ++i) {
           const int e = 2 * (j0 + i);
           const float2 a = buf[(wc * V + i) * ldb + t];
+          if (e < G.K) dst[2 * i] = a.x * sc;
+          if (e + 1 < G.K) dst[2 * i + 1] = a.y * sc;
+        }
+      }
+    }
+  }
+}
+
+// Stages A and C for q = 256 R3 (R3 in {1, 2, 4}) on the compile-time engine
+// of the cluster kernel (hd_cl_kernel.cuh): W = 16 / R3 arrays of q per CTA
+// (4096 points), 256 threads, the in-place DIF passes (stage A, output in
+// digit-reversed order: position p holds r = digit_freq(p)) and DIT passes
+// (stage C, input placed at digit_pos(r), output in natural order), pass
+// twiddles in shared memory.  Every trip count and stride is a compile-time
+// constant, which the plan-driven and structured engines above are not.
+template <int R3>
+struct QEng {
+  static constexpr int Q = 256 * R3;
+  static constexpr int W = 16 / R3;    // s per CTA
+  static constexpr int T = kThreads;
+  using K = cl::Steps<1, R3, false, T>;
+  static constexpr int TABS = cl::Shape<R3>::TABS;
+  static constexpr size_t SMEM = sizeof(float2) * ((size_t)W * Q + TABS);
+  static constexpr int V = W >= 8 ? 8 : 4;  // s per task
+  static constexpr int KT = W * Q / V / T;  // tasks per thread (exact)
+};
+
+template <int R3>
+__device__ __forceinline__ void qeng_tables(float2* tws, const float2* __restrict__ tab, int tid) {
+  for (int i = tid; i < QEng<R3>::TABS / 2; i += QEng<R3>::T) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(tws + 2 * i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(tab + 2 * i) : "memory");
+  }
+}
+
+template <int R3, bool CS>
+__global__ void __launch_bounds__(kThreads, 4) k_stage_a_q(const Inputs in, float2* __restrict__ Y, Geo G,
+                                                            const float2* __restrict__ tab) {
+  using E = QEng<R3>;
+  using K = typename E::K;
+  constexpr int Q = E::Q, W = E::W, V = E::V, KT = E::KT;
+  extern __shared__ float4 smem_raw[];
+  float2* arr = reinterpret_cast<float2*>(smem_raw);  // W arrays of Q (row t at cl::phys(t))
+  float2* tws = arr + W * Q;
+  const int tid = threadIdx.x;
+  allow_next_stage();
+  qeng_tables<R3>(tws, tab, tid);
+  const int which = blockIdx.y;
+  const int Li = in.L[which], pi = in.p[which];
+  const float* __restrict__ x = in.x[which] + (int64_t)blockIdx.z * Li;
+  const int s0 = blockIdx.x * W, M = G.M;
+  const bool vec = aligned16(x);
+  float2 v[KT][V];
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int id = tid + k * E::T;
+    const int wc = id / Q, t = id % Q;  // consecutive lanes: consecutive blocks t
+#pragma unroll
+    for (int i = 0; i < V; ++i) v[k][i] = make_float2(0.f, 0.f);
+    if (t < pi) {
+      const int j0 = t * M + s0 + wc * V;
+      if constexpr (CS) {
+        const float* src = x + j0;
+        if (vec && j0 + V <= Li) {
+#pragma unroll
+          for (int i = 0; i < V; i += 4) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(src) + i / 4);
+            v[k][i].x = a.x;
+            v[k][i + 1].x = a.y;
+            v[k][i + 2].x = a.z;
+            v[k][i + 3].x = a.w;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < V; ++i)
+            if (j0 + i < Li) v[k][i].x = __ldg(src + i);
+        }
+      } else {
+        const float* src = x + 2 * j0;
+        if (vec && 2 * (j0 + V) <= Li) {
+#pragma unroll
+          for (int i = 0; i < V; i += 2) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(src) + i / 2);
+            v[k][i] = make_float2(a.x, a.y);
+            v[k][i + 1] = make_float2(a.z, a.w);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < V; ++i) {
+            const int e = 2 * (j0 + i);
+            if (e < Li) v[k][i].x = __ldg(src + 2 * i);
+            if (e + 1 < Li) v[k][i].y = __ldg(src + 2 * i + 1);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int id = tid + k * E::T;
+    const int wc = id / Q, t = id % Q;
+#pragma unroll
+    for (int i = 0; i < V; ++i) arr[(wc * V + i) * Q + cl::phys(t)] = v[k][i];
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  K::template pass1<1, W, 2>(arr, tid, tws);
+  __syncthreads();
+  K::template pass2<1, W, 2>(arr, tid, tws);
+  __syncthreads();
+  K::template pass3<1, W>(arr, tid);
+  __syncthreads();
+  float2* Yw = Y + ((int64_t)blockIdx.z * G.nin + which) * G.rows * M;
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int id = tid + k * E::T;
+    const int wc = id / Q, r = id % Q;
+    if (r < G.rows) {
+      const int pr = cl::phys(cl::digit_pos(r, R3));
+      float4* dst = reinterpret_cast<float4*>(Yw + r * M + s0 + wc * V);
+#pragma unroll
+      for (int i = 0; i < V; i += 2) {
+        const float2 a = arr[(wc * V + i) * Q + pr], b = arr[(wc * V + i + 1) * Q + pr];
+        dst[i / 2] = make_float4(a.x, a.y, b.x, b.y);
+      }
+    }
+  }
+}
+
+template <int R3, bool CS>
+__global__ void __launch_bounds__(kThreads, 4) k_stage_c_q(const float2* __restrict__ Wr, float* __restrict__ h,
+                                                            Geo G, const float2* __restrict__ tab) {
+  using E = QEng<R3>;
+  using K = typename E::K;
+  constexpr int Q = E::Q, W = E::W, V = E::V, KT = E::KT;
+  extern __shared__ float4 smem_raw[];
+  float2* arr = reinterpret_cast<float2*>(smem_raw);
+  float2* tws = arr + W * Q;
+  const int tid = threadIdx.x;
+  qeng_tables<R3>(tws, tab, tid);
+  const int s0 = blockIdx.x * W, M = G.M;
+  const float2* Wi = after_prev_stage(Wr) + (int64_t)blockIdx.z * G.rows * M;
+  float2 v[KT][V];
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int id = tid + k * E::T;
+    const int wc = id / Q, r = id % Q;
+    const bool mirror = CS && r >= G.rows;  // r > q/2: conj of row q - r
+    const float4* src = reinterpret_cast<const float4*>(Wi + (mirror ? Q - r : r) * M + s0 + wc * V);
+#pragma unroll
+    for (int i = 0; i < V; i += 2) {
+      const float4 a = src[i / 2];
+      v[k][i] = make_float2(a.x, mirror ? -a.y : a.y);
+      v[k][i + 1] = make_float2(a.z, mirror ? -a.w : a.w);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int id = tid + k * E::T;
+    const int wc = id / Q, r = id % Q;
+    const int pr = cl::phys(cl::digit_pos(r, R3));
+#pragma unroll
+    for (int i = 0; i < V; ++i) arr[(wc * V + i) * Q + pr] = v[k][i];
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  K::template pass3<-1, W>(arr, tid);
+  __syncthreads();
+  K::template pass2<-1, W, 1>(arr, tid, tws);
+  __syncthreads();
+  K::template pass1<-1, W, 1>(arr, tid, tws);
+  __syncthreads();
+  const float sc = 1.0f / (float)G.N;
+  float* hi = h + blockIdx.z * G.out_stride;
+  const bool vec = aligned16(hi);
+  const int Kp = CS ? G.K : (G.K + 1) >> 1;  // output positions j = t M + s (packed pairs for RCM)
+  const int pout = (Kp + M - 1) / M;
+#pragma unroll
+  for (int k = 0; k < KT; ++k) {
+    const int id = tid + k * E::T;
+    const int wc = id / Q, t = id % Q;
+    if (t >= pout) continue;
+    const int j0 = t * M + s0 + wc * V;
+    const int pt = cl::phys(t);
+    if constexpr (CS) {
+      float* dst = hi + j0;
+      if (vec && j0 + V <= G.K) {
+#pragma unroll
+        for (int i = 0; i < V; i += 4)
+          reinterpret_cast<float4*>(dst)[i / 4] =
+              make_float4(arr[(wc * V + i) * Q + pt].x * sc, arr[(wc * V + i + 1) * Q + pt].x * sc,
+                          arr[(wc * V + i + 2) * Q + pt].x * sc, arr[(wc * V + i + 3) * Q + pt].x * sc);
+      } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i)
+          if (j0 + i < G.K) dst[i] = arr[(wc * V + i) * Q + pt].x * sc;
+      }
+    } else {
+      float* dst = hi + 2 * j0;
+      if (vec && 2 * (j0 + V) <= G.K) {
+#pragma unroll
+        for (int i = 0; i < V; i += 2) {
+          const float2 a = arr[(wc * V + i) * Q + pt], b = arr[(wc * V + i + 1) * Q + pt];
+          reinterpret_cast<float4*>(dst)[i / 2] = make_float4(a.x * sc, a.y * sc, b.x * sc, b.y * sc);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+          const int e = 2 * (j0 + i);
+          const float2 a = arr[(wc * V + i) * Q + pt];
           if (e < G.K) dst[2 * i] = a.x * sc;
           if (e + 1 < G.K) dst[2 * i + 1] = a.y * sc;
         }
@@ -417,8 +634,7 @@ __global__ void __launch_bounds__(cl::Shape<R3>::T, cl::Shape<R3>::MINB)
     tx[i] = __ldg(tw + (u < kLo ? rr * u : rr * kLo * (u - kLo)));  // < r M <= N
   }
   allow_next_stage();
-  wait_prev_stage();
-  const float2* Y0 = Y + (int64_t)blockIdx.z * G.nin * G.N;
+  const float2* Y0 = after_prev_stage(Y) + (int64_t)blockIdx.z * G.nin * G.N;
   float2* Wi = Wr + (int64_t)blockIdx.z * G.N;
   {
     const float2* const src[4] = {Y0 + c * M, Y0 + rb * M, Y0 + G.N + c * M, Y0 + G.N + rb * M};
@@ -538,9 +754,8 @@ __global__ void __launch_bounds__(cl::Shape<R3>::T, cl::Shape<R3>::MINB)
   }
   for (int i = tid; i < NX; i += T) tx[i] = __ldg(tw + (i < kLo ? r * i : r * kLo * (i - kLo)));  // < r M < N
   allow_next_stage();
-  wait_prev_stage();
   const int64_t astride = (int64_t)G.rows * M;
-  const float2* Y0 = Y + (int64_t)blockIdx.z * G.nin * astride;
+  const float2* Y0 = after_prev_stage(Y) + (int64_t)blockIdx.z * G.nin * astride;
   float2* Wi = Wr + (int64_t)blockIdx.z * astride;
   {
     const float2* const src[2] = {Y0 + r * M, Y0 + astride + r * M};
@@ -615,29 +830,78 @@ static int s_per_cta(int q) {
 }  // namespace staged
 
 // Planner of the three-kernel path for a needed padded length n (hybridRCM:
-// q M >= L packed; hybridCS: q M >= 2L - 1 real): M = 512 below 2^17, 2048
-// below 2^19, else 4096 (4608 when q would exceed 1024), and q the smallest
-// length {1, 3, 5, 9} x 2^a >= max(16, n / M), which the structured engine
-// transforms.  Measured on B300 over L = 10^5 .. 4 10^6 for both algorithms,
-// this rule is within ~10% of the best (M, q) of every length tried; false if
-// n > 1024 x 4608.
+// q M >= L packed; hybridCS: q M >= 2L - 1 real).  From n = 2^17 on, q is one
+// of 256, 512, 1024 (stages A and C on the compile-time engine) and M = 256 R3
+// (R3 in {2, 4, 8, 16, 18}) with the smallest N = q M >= n, the largest M
+// among equal N (fewer, longer stage-B transforms measured faster).  Below,
+// M = 512 and q the smallest length {1, 3, 5, 9} x 2^a >= max(16, n / 512).
+// False if n > 1024 x 4608.
 bool staged_params(int64_t n, int* M, int* q) {
-  const int first = n < (1 << 17) ? 512 : n < (1 << 19) ? 2048 : 4096;
-  for (int mm : {first, 4608}) {
-    const int64_t qq = ladder_ceil(std::max<int64_t>(16, (n + mm - 1) / mm));
-    if (qq <= staged::kMaxQ) {
-      *M = mm;
-      *q = (int)qq;
-      return true;
-    }
+  if (n < (1 << 17)) {
+    *M = 512;
+    *q = (int)ladder_ceil(std::max<int64_t>(16, (n + 511) / 512));
+    return true;
   }
-  return false;
+  int64_t bestN = 0;
+  for (int qq : {256, 512, 1024})
+    for (int r : staged::kR3) {
+      const int64_t mm = 256 * r, N = qq * mm;
+      if (N < n) continue;
+      if (bestN == 0 || N < bestN || (N == bestN && mm > *M)) {
+        bestN = N;
+        *M = (int)mm;
+        *q = qq;
+      }
+    }
+  return bestN > 0;
 }
 
 namespace staged {
 
 // The three stages for `batch` items (n arrays each, item b of array i at
 // in.x[i] + b L_i, output item b at h + b K); S = sum L_i - n + 1 <= 2 q M.
+// Stages A and C on the compile-time engine when q = 256 R3, R3 in {1, 2, 4}.
+static bool qeng_length(int q) { return q == 256 || q == 512 || q == 1024; }
+
+template <int R3>
+static cudaError_t launch_a_q(bool cs, unsigned gx, unsigned gy, unsigned gz, cudaStream_t st, const Inputs& in,
+                              float2* Y, const Geo& G, const float2* tabq) {
+  auto k = cs ? k_stage_a_q<R3, true> : k_stage_a_q<R3, false>;
+  cudaError_t e = smem_optin((const void*)k, QEng<R3>::SMEM);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(gx, gy, gz), kThreads, QEng<R3>::SMEM, st>>>(in, Y, G, tabq);
+  return cudaGetLastError();
+}
+
+template <int R3>
+static cudaError_t launch_c_q(bool cs, unsigned gx, unsigned gz, cudaStream_t st, const float2* Wr, float* h,
+                              const Geo& G, const float2* tabq) {
+  auto k = cs ? k_stage_c_q<R3, true> : k_stage_c_q<R3, false>;
+  cudaError_t e = smem_optin((const void*)k, QEng<R3>::SMEM);
+  if (e != cudaSuccess) return e;
+  return launch_after(k, dim3(gx, 1, gz), kThreads, QEng<R3>::SMEM, st, Wr, h, G, tabq);
+}
+
+static cudaError_t launch_a_q_any(int q, bool cs, unsigned gy, unsigned gz, cudaStream_t st, const Inputs& in,
+                                  float2* Y, const Geo& G, const float2* tabq) {
+  switch (q) {
+    case 256: return launch_a_q<1>(cs, G.M / QEng<1>::W, gy, gz, st, in, Y, G, tabq);
+    case 512: return launch_a_q<2>(cs, G.M / QEng<2>::W, gy, gz, st, in, Y, G, tabq);
+    case 1024: return launch_a_q<4>(cs, G.M / QEng<4>::W, gy, gz, st, in, Y, G, tabq);
+  }
+  return cudaErrorInvalidValue;
+}
+
+static cudaError_t launch_c_q_any(int q, bool cs, unsigned gz, cudaStream_t st, const float2* Wr, float* h,
+                                  const Geo& G, const float2* tabq) {
+  switch (q) {
+    case 256: return launch_c_q<1>(cs, G.M / QEng<1>::W, gz, st, Wr, h, G, tabq);
+    case 512: return launch_c_q<2>(cs, G.M / QEng<2>::W, gz, st, Wr, h, G, tabq);
+    case 1024: return launch_c_q<4>(cs, G.M / QEng<4>::W, gz, st, Wr, h, G, tabq);
+  }
+  return cudaErrorInvalidValue;
+}
+
 // cs: hybridCS (real residues, q M >= S) instead of hybridRCM (packed, 2 q M >= S).
 static hd_status run(hd_ctx* c, Inputs in, int nin, float* h, int64_t K, int M, int q, int64_t batch,
                      cudaStream_t st, bool cs = false) {
@@ -669,6 +933,9 @@ static hd_status run(hd_ctx* c, Inputs in, int nin, float* h, int64_t K, int M, 
   if (!tab) return fail(terr, "pass table allocation failed");
   const float2* tq = c->tables.get(q, st, &terr);
   if (!tq) return fail(terr, "twiddle table allocation failed");
+  const bool qe = qeng_length(q);
+  const float2* tabq = qe ? c->tables.get_pass_table(q, st, &terr) : nullptr;
+  if (qe && !tabq) return fail(terr, "pass table allocation failed");
   FftPlan pq;
   if (!factor_radices(q, &pq)) return fail(HD_EINVAL, "bad residue count");
   const size_t per_item = sizeof(float2) * (size_t)(nin + 1) * (size_t)G.rows * M;
@@ -694,12 +961,18 @@ static hd_status run(hd_ctx* c, Inputs in, int nin, float* h, int64_t K, int M, 
     Inputs ic = in;
     for (int i = 0; i < nin; ++i) ic.x[i] = in.x[i] + b0 * in.L[i];
     float* hi = h + b0 * K;
-    ka<<<dim3(M / G.W, nin, nb), kThreads, smem_ac, st>>>(ic, Y, G, tq, pq);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "staged path: stage A launch");
+    if (qe) {
+      e = launch_a_q_any(q, cs, (unsigned)nin, nb, st, ic, Y, G, tabq);
+    } else {
+      ka<<<dim3(M / G.W, nin, nb), kThreads, smem_ac, st>>>(ic, Y, G, tq, pq);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "staged path: stage A launch");
     e = cs ? launch_b_cs_any(M / 256, dim3(q / 2 + 1, 1, nb), st, Y, Wr, G, tw, tab)
            : launch_b_any(M / 256, dim3(q / 2, 1, nb), st, Y, Wr, G, tw, tab);
     if (e != cudaSuccess) return cuda_fail(e, "staged path: stage B launch");
-    e = launch_after(kc, dim3(M / G.W, 1, nb), kThreads, smem_ac, st, (const float2*)Wr, hi, G, tq, pq);
+    e = qe ? launch_c_q_any(q, cs, nb, st, Wr, hi, G, tabq)
+           : launch_after(kc, dim3(M / G.W, 1, nb), kThreads, smem_ac, st, (const float2*)Wr, hi, G, tq, pq);
     if (e != cudaSuccess) return cuda_fail(e, "staged path: stage C launch");
   }
   return HD_OK;
