@@ -116,7 +116,7 @@ __device__ __forceinline__ T* after_prev_stage(T* p) {
 // CS: real unpacked input (hybridCS, Sec. 3 with App. A), x_t[s] = f_{tM+s};
 // the DFT over t of real data is Hermitian in r, so rows r <= q/2 are kept.
 template <bool SE, int V, bool CS>
-__global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_a(const Inputs in, float2* __restrict__ Y, Geo G,
+__global__ void __launch_bounds__(kThreads, SE ? kMinB : 1) k_stage_a(const __grid_constant__ Inputs in, float2* __restrict__ Y, Geo G,
                                                        const float2* __restrict__ tq, FftPlan pq) {
   constexpr int KT = kPts / V;  // tasks per thread (W q <= kPts kThreads)
   extern __shared__ float4 smem_raw[];
@@ -324,8 +324,11 @@ __device__ __forceinline__ void qeng_tables(float2* tws, const float2* __restric
   }
 }
 
+#ifndef HD_STAGE_AQ_MINB
+#define HD_STAGE_AQ_MINB 2  // 117 registers, no spills (4: 64 registers, 340 B of spills, 7% slower)
+#endif
 template <int R3, bool CS>
-__global__ void __launch_bounds__(kThreads, 4) k_stage_a_q(const Inputs in, float2* __restrict__ Y, Geo G,
+__global__ void __launch_bounds__(kThreads, HD_STAGE_AQ_MINB) k_stage_a_q(const __grid_constant__ Inputs in, float2* __restrict__ Y, Geo G,
                                                             const float2* __restrict__ tab) {
   using E = QEng<R3>;
   using K = typename E::K;
