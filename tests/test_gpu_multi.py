@@ -99,13 +99,26 @@ def test_three_geometric_alternating(hd):
     assert err <= 18 * np.log2(8192) * np.finfo(np.float32).eps * kap
 
 
-@pytest.mark.parametrize("M,q", [(512, 2), (512, 10), (1024, 16), (2048, 64), (4608, 18)])
+@pytest.mark.parametrize("M,q", [(512, 2), (512, 10), (1024, 16), (2048, 64), (4608, 18), (512, 256), (1024, 512),
+                                 (512, 1024), (4096, 256)])
 def test_explicit_parameters(hd, M, q):
     lengths = (6000, 300, 77)
     S = sum(lengths) - 2
     if 2 * M * q < S:
         pytest.skip("does not dealias")
     xs = arrays(lengths, seed=4200 + M + q)
+    ref = oracle.fft_conv_multi([x.astype(np.float64) for x in xs], S)
+    h = host(hd.conv_multi([dev(x) for x in xs], out_extent="full", M=M, q=q))
+    assert rel_l2(h, ref) <= TOL
+
+
+@pytest.mark.parametrize("M,q", [(2048, 256), (1024, 512), (512, 1024)])
+def test_long_arrays_compile_time_engine(hd, M, q):
+    """Three long arrays (many blocks of each) through stages A and C on the
+    compile-time engine, with the n-ary product in stage B."""
+    lengths = (300000, 100000, 5)
+    S = sum(lengths) - 2
+    xs = arrays(lengths, seed=4300 + q)
     ref = oracle.fft_conv_multi([x.astype(np.float64) for x in xs], S)
     h = host(hd.conv_multi([dev(x) for x in xs], out_extent="full", M=M, q=q))
     assert rel_l2(h, ref) <= TOL

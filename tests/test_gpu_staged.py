@@ -30,16 +30,22 @@ def host(t):
 
 
 # (L, M, q): q = 2 (one CTA pair), q with radices 2/4/5 and 3, a prime radix
-# (q = 14, 2 x 7), p < q/2 (many empty blocks), q = 1024 (four s per CTA in
-# stages A and C), every stage-B length, ragged tails in both s and t; the
-# q-point DFTs run on the plan-driven engine for q = 2, 4, 10, 12, 14, 30, 100,
-# 150 and on the structured one for the rest.
+# (q = 14, 2 x 7), p < q/2 (many empty blocks), q = 1024, every stage-B
+# length, ragged tails in both s and t; the q-point DFTs run on the
+# plan-driven engine for q = 2, 4, 10, 12, 14, 30, 100, 150, on the compile-time
+# one for q = 256, 512, 1024 and on the structured one for the rest.
 CASES = [
     (1, 512, 2), (2, 512, 2), (777, 512, 2), (1000, 512, 4), (4097, 512, 10), (5000, 512, 14),
     (9000, 1024, 12), (9000, 1024, 30), (20001, 2048, 10), (40000, 4096, 10), (40000, 4608, 10),
     (70001, 512, 150), (3000, 512, 1024), (100000, 1024, 100), (123457, 2048, 64),
     # lengths of the structured engine ({1, 3, 5, 9} x 2^a >= 16)
     (9000, 512, 48), (60000, 512, 144), (100000, 1024, 160), (200000, 512, 768), (7000, 4608, 16),
+    # the compile-time engine of stages A and C (q = 256, 512, 1024) with every
+    # stage-B length behind it and few or many blocks (p from 30 to q/2): the
+    # stage-B runtimes differ, so a load of w' that ran ahead of the wait for
+    # stage B would show here
+    (60000, 1024, 256), (200000, 1024, 256), (262144, 2048, 256), (300000, 4096, 256), (200000, 512, 512),
+    (500000, 1024, 512), (500000, 512, 1024), (150000, 4608, 256),
 ]
 
 
@@ -130,7 +136,8 @@ def test_staged_argument_errors(hd):
 
 # --- hybridCS on the three kernels (App. A's inner loop for real data) -------------
 CS_CASES = [(1, 512, 2), (777, 512, 4), (4097, 512, 18), (5000, 512, 20), (9000, 1024, 18), (20001, 2048, 20),
-            (40000, 4608, 18), (100000, 1024, 256), (3000, 512, 1024)]
+            (40000, 4608, 18), (100000, 1024, 256), (3000, 512, 1024),
+            (60000, 1024, 256), (262144, 2048, 256), (300000, 4096, 256), (100000, 512, 512), (200000, 512, 1024)]
 
 
 @pytest.mark.parametrize("L,M,q", CS_CASES)
