@@ -386,9 +386,16 @@ __host__ __device__ inline bool struct_length(int n) {
   return a2 >= 4 && (odd == 1 || odd == 3 || odd == 5 || odd == 9);
 }
 
-template <int R, int SIGN, int PTS, bool IN_SWZ, bool OUT_SWZ, bool PASS_TW>
+// NN > 0: the transform length NN and the stride NSS of this pass are
+// compile-time constants (n and Ns ignored), so the index divisions below
+// become multiplies and shifts.
+template <int R, int SIGN, int PTS, bool IN_SWZ, bool OUT_SWZ, bool PASS_TW, int NN = 0, int NSS = 1>
 __device__ __forceinline__ void gstage(float2* base, int stride, int nbuf, int n, int Ns,
                                        const float2* __restrict__ tw, int twmul) {
+  if constexpr (NN > 0) {
+    n = NN;
+    Ns = NSS;
+  }
   constexpr int BPT = (PTS + R - 1) / R;
   const int nb = n / R;
   const DivF dnb = make_div(nb), dNs = make_div(Ns);
@@ -400,9 +407,9 @@ __device__ __forceinline__ void gstage(float2* base, int stride, int nbuf, int n
   for (int b = 0; b < BPT; ++b) {
     const int idx = threadIdx.x + b * T;
     if (idx < total) {
-      const int a = fdiv(idx, dnb);
+      const int a = NN > 0 ? idx / nb : fdiv(idx, dnb);
       const int j = idx - a * nb;
-      const int jm = j - fdiv(j, dNs) * Ns;
+      const int jm = NN > 0 ? j % Ns : j - fdiv(j, dNs) * Ns;
       const float2* x = base + a * stride;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[b][r] = x[IN_SWZ ? swz(j + r * nb) : j + r * nb];
@@ -426,9 +433,9 @@ __device__ __forceinline__ void gstage(float2* base, int stride, int nbuf, int n
   for (int b = 0; b < BPT; ++b) {
     const int idx = threadIdx.x + b * T;
     if (idx < total) {
-      const int a = fdiv(idx, dnb);
+      const int a = NN > 0 ? idx / nb : fdiv(idx, dnb);
       const int j = idx - a * nb;
-      const int jm = j - fdiv(j, dNs) * Ns;
+      const int jm = NN > 0 ? j % Ns : j - fdiv(j, dNs) * Ns;
       dft_reg<R, SIGN>(v[b]);
       float2* y = base + a * stride;
       const int o = (j - jm) * R + jm;
@@ -517,6 +524,50 @@ __device__ __forceinline__ void cta_fft_struct(float2* base, int stride, int nbu
     gstage_odd<SIGN, PTS, true, PASS_TW>(base, stride, nbuf, n, Ns, odd, tw, twmul);
   }
 }
+
+// The passes of cta_fft_struct for a compile-time length N (at most three
+// radix-16 passes), same order, same swizzles, every trip count and divisor a
+// constant.
+template <int SIGN, int PTS, int N, int NS, bool IN_SWZ, bool PASS_TW>
+__device__ __forceinline__ void struct_tail_k(float2* base, int stride, int nbuf, const float2* __restrict__ tw,
+                                              int twmul) {
+  constexpr int a2 = __builtin_ctz(N);
+  constexpr int odd = N >> a2, rem = a2 & 3;
+  constexpr int mt = merged_tail(1 << rem, odd);
+  if constexpr (mt) {
+    gstage<mt, SIGN, PTS, IN_SWZ, false, PASS_TW, N, NS>(base, stride, nbuf, N, NS, tw, twmul);
+  } else {
+    if constexpr (rem) gstage<(1 << rem), SIGN, PTS, IN_SWZ, false, PASS_TW, N, NS>(base, stride, nbuf, N, NS, tw, twmul);
+    constexpr int NS2 = NS << rem;
+    constexpr bool SW2 = rem ? false : IN_SWZ;
+    if constexpr (odd > 1) gstage<odd, SIGN, PTS, SW2, false, PASS_TW, N, NS2>(base, stride, nbuf, N, NS2, tw, twmul);
+  }
+}
+
+template <int SIGN, int PTS, int N, bool PASS_TW = false>
+__device__ __forceinline__ void cta_fft_struct_k(float2* base, int stride, int nbuf, const float2* __restrict__ tw,
+                                                 int twmul) {
+  constexpr int a2 = __builtin_ctz(N);
+  constexpr int n16 = a2 >> 2;
+  static_assert(n16 >= 1 && n16 <= 3, "compile-time structured lengths: 16 <= N, at most three radix-16 passes");
+  if constexpr (N == 16) {
+    gstage<16, SIGN, PTS, false, false, PASS_TW, N, 1>(base, stride, nbuf, N, 1, tw, twmul);
+  } else {
+    gstage<16, SIGN, PTS, false, true, PASS_TW, N, 1>(base, stride, nbuf, N, 1, tw, twmul);
+    if constexpr (n16 >= 2) {
+      gstage<16, SIGN, PTS, true, false, PASS_TW, N, 16>(base, stride, nbuf, N, 16, tw, twmul);
+      if constexpr (n16 >= 3) {
+        gstage<16, SIGN, PTS, false, false, PASS_TW, N, 256>(base, stride, nbuf, N, 256, tw, twmul);
+        struct_tail_k<SIGN, PTS, N, 4096, false, PASS_TW>(base, stride, nbuf, tw, twmul);
+      } else {
+        struct_tail_k<SIGN, PTS, N, 256, false, PASS_TW>(base, stride, nbuf, tw, twmul);
+      }
+    } else {
+      struct_tail_k<SIGN, PTS, N, 16, true, PASS_TW>(base, stride, nbuf, tw, twmul);
+    }
+  }
+}
+
 
 // ---------------------------------------------------------------------------
 // Out-of-place form of the structured engine: pass k reads one buffer and
@@ -666,10 +717,12 @@ __device__ __forceinline__ void cta_fft_struct_tc(float2* base, int stride, int 
 // DFT dispatch of the nD kernels: SE (struct_length lengths) inlines the
 // structured engine (TC: with tensor-core radix-16 passes), otherwise the
 // generic plan-driven cta_fft.
-template <int SIGN, int PTS, bool TC, bool SE>
+// NN > 0: the structured engine at the compile-time length NN (= pl.n).
+template <int SIGN, int PTS, bool TC, bool SE, int NN = 0>
 __device__ __forceinline__ void fft_sel(float2* base, int stride, int nbuf, const FftPlan& pl,
                                         const float2* __restrict__ tw, int twmul) {
-  if constexpr (SE && TC) cta_fft_struct_tc<SIGN, PTS>(base, stride, nbuf, pl.n, tw, twmul);
+  if constexpr (SE && !TC && NN > 0) cta_fft_struct_k<SIGN, PTS, NN>(base, stride, nbuf, tw, twmul);
+  else if constexpr (SE && TC) cta_fft_struct_tc<SIGN, PTS>(base, stride, nbuf, pl.n, tw, twmul);
   else if constexpr (SE) cta_fft_struct<SIGN, PTS>(base, stride, nbuf, pl.n, tw, twmul);
   else cta_fft<SIGN, PTS, TC>(base, stride, nbuf, pl, tw, twmul);
 }

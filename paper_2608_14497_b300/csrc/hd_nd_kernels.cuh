@@ -142,10 +142,13 @@ struct ColBounds {
   static constexpr int KT = (SE && !TC) ? (PTS <= 16 ? 8 : 16) : 4;  // strip_load batch
 };
 
-template <int PTS, bool TC, bool SE>
+// NN > 0: an instance for the residue length m = NN (the structured engine's
+// passes and the strip index arithmetic with a compile-time length).
+template <int PTS, bool TC, bool SE, int NN = 0>
 __global__ void __launch_bounds__(ColBounds<PTS, TC, SE>::T, ColBounds<PTS, TC, SE>::MINB) k_col_fwd(const void* Xv, float2* Y, ColGeom cg,
                                                   int Lin, int m, int q, int p, int in_mode, int Lreal,
                                                   const float2* __restrict__ tw, FftPlan pl) {
+  if constexpr (NN > 0) m = NN;
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   const int W = cg.W;
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, TC, SE>::T, ColBounds<PTS, TC, 
       }
       __syncthreads();
     }
-    fft_sel<1, PTS, TC, SE>(buf, m, W, pl, tw, q);
+    fft_sel<1, PTS, TC, SE, NN>(buf, m, W, pl, tw, q);
     strip_store(buf, m, m, W, [&](int l, int w, float2 v) {
       const int64_t b = b0 + w;
       if (b < cg.B) Y[(a * (int64_t)N + (int64_t)r * m + l) * cg.B + b] = v;
@@ -221,10 +224,11 @@ __global__ void __launch_bounds__(ColBounds<PTS, TC, SE>::T, ColBounds<PTS, TC, 
 //   real array (element (j, b) -> h[j][2b], h[j][2b+1], real row length Lreal).
 //   Eqs. accumulator and accumulation per column, scaled by `scale`.
 // ---------------------------------------------------------------------------
-template <int PTS, bool TC, bool SE>
+template <int PTS, bool TC, bool SE, int NN = 0>
 __global__ void __launch_bounds__(ColBounds<PTS, TC, SE>::T, ColBounds<PTS, TC, SE>::MINB) k_col_bwd(const float2* Y, void* Zv, ColGeom cg, int Lout, int m,
                                                   int q, int out_mode, int Lreal, float scale,
                                                   const float2* __restrict__ tw, FftPlan pl) {
+  if constexpr (NN > 0) m = NN;
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   const int W = cg.W;
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, TC, SE>::T, ColBounds<PTS, TC, 
       return (b < cg.B) ? __ldg(Y + (a * (int64_t)N + (int64_t)r * m + l) * cg.B + b) : make_float2(0.f, 0.f);
     });
     __syncthreads();
-    fft_sel<-1, PTS, TC, SE>(buf, m, W, pl, tw, q);
+    fft_sel<-1, PTS, TC, SE, NN>(buf, m, W, pl, tw, q);
     if (sep) {
       for (int idx = tid; idx < W * Lout; idx += T) {
         const int w = idx / Lout, j = idx - w * Lout;
