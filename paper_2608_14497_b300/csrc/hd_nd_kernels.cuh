@@ -311,11 +311,12 @@ __host__ __device__ __forceinline__ int cs_rows(int m, int q) {
   return (m / 2 + 1) + ((q + 1) / 2 - 1) * m + ((q % 2 == 0) ? m / 2 : 0);
 }
 
-template <int PTS, bool SE>
+template <int PTS, bool SE, int NN = 0>
 __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, false, SE>::MINB) k_col_fwd_cs(const float* __restrict__ X, float2* __restrict__ Y, int64_t B,
                                                      int W, int Lin, int m, int q, int p,
                                                      const float2* __restrict__ tw, FftPlan pl_m, FftPlan pl_h,
                                                      CsMid mid) {
+  if constexpr (NN > 0) m = NN;  // instance for the residue length NN (and NN / 2)
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   const int64_t b0 = (int64_t)blockIdx.x * W;
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
       buf[idx] = make_float2(x0, x1);
     }
     __syncthreads();
-    fft_sel<1, PTS, false, SE>(buf, m, npair, pl_m, tw, q);
+    fft_sel<1, PTS, false, SE, NN>(buf, m, npair, pl_m, tw, q);
     const int nh = m / 2 + 1;
     for (int idx = tid; idx < npair * nh; idx += T) {
       const int l = idx / npair, pw = idx - l * npair;
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
       buf[idx] = sum;
     }
     __syncthreads();
-    fft_sel<1, PTS, false, SE>(buf, m, W, pl_m, tw, q);
+    fft_sel<1, PTS, false, SE, NN>(buf, m, W, pl_m, tw, q);
     for (int idx = tid; idx < W * m; idx += T) {
       const int l = idx / W, w = idx - l * W;
       store(row0 + l, w, buf[w * m + l]);
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
       buf[idx] = cmul(make_float2(x0, x1), tw_get<1>(tw, bb * qh));
     }
     __syncthreads();
-    fft_sel<1, PTS, false, SE>(buf, e, W, pl_h, tw, 2 * q);
+    fft_sel<1, PTS, false, SE, NN / 2>(buf, e, W, pl_h, tw, 2 * q);
     for (int idx = tid; idx < W * e; idx += T) {
       const int c = idx / W, w = idx - c * W;
       store(row0 + c, w, buf[w * e + c]);
@@ -419,11 +420,12 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
 
 // k_col_bwd_cs: inverse of k_col_fwd_cs with Eq. real-accumulation; writes the
 // first Lout rows of the real array Z [Lout][B], scaled.
-template <int PTS, bool SE>
+template <int PTS, bool SE, int NN = 0>
 __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, false, SE>::MINB) k_col_bwd_cs(const float2* __restrict__ Y, float* __restrict__ Z, int64_t B,
                                                      int W, int Lout, int m, int q, float scale,
                                                      const float2* __restrict__ tw, FftPlan pl_m, FftPlan pl_h,
                                                      CsMid mid) {
+  if constexpr (NN > 0) m = NN;  // instance for the residue length NN (and NN / 2)
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   const int64_t b0 = (int64_t)blockIdx.x * W;
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
           buf[pw * m + l] = v;
         });
     __syncthreads();
-    fft_sel<-1, PTS, false, SE>(buf, m, npair, pl_m, tw, q);
+    fft_sel<-1, PTS, false, SE, NN>(buf, m, npair, pl_m, tw, q);
     for (int idx = tid; idx < W * Lout; idx += T) {
       const int w = idx / Lout, j = idx - w * Lout;
       const float2 v = buf[(w / 2) * m + (j % m)];
@@ -473,7 +475,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
         W * m, [&](int idx) { return load(row0 + idx / W, idx % W); },
         [&](int idx, float2 v) { buf[(idx % W) * m + idx / W] = v; });
     __syncthreads();
-    fft_sel<-1, PTS, false, SE>(buf, m, W, pl_m, tw, q);
+    fft_sel<-1, PTS, false, SE, NN>(buf, m, W, pl_m, tw, q);
     for (int idx = tid; idx < W * Lout; idx += T) {
       const int w = idx / Lout, j = idx - w * Lout;
       acc[idx] += 2.f * cmul(buf[w * m + (j % m)], tw_get<-1>(tw, modmul(r, j, N))).x;
@@ -487,7 +489,7 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
         W * e, [&](int idx) { return load(row0 + idx / W, idx % W); },
         [&](int idx, float2 v) { buf[(idx % W) * e + idx / W] = v; });
     __syncthreads();
-    fft_sel<-1, PTS, false, SE>(buf, e, W, pl_h, tw, 2 * q);
+    fft_sel<-1, PTS, false, SE, NN / 2>(buf, e, W, pl_h, tw, 2 * q);
     for (int idx = tid; idx < W * Lout; idx += T) {
       const int w = idx / Lout, j = idx - w * Lout;
       const int t = j / m, s = j - t * m;
