@@ -300,14 +300,14 @@ def run_gpu(args):
     traffic = recorded_traffic("k_rcm_cl", args.algo)
 
     # end to end: pinned host buffers, copies inside the timed region.  The
-    # batch is cut into E2E_CHUNKS runs of consecutive items, each with its own
+    # batch is cut into --e2e-chunks runs of consecutive items, each with its own
     # plan (the public BatchPlan API), so the host-to-device copy of one chunk,
     # the convolutions of the previous one and the device-to-host copy of the
     # one before run concurrently (copy engines and SMs); every step still
     # copies all of f and g in and all of h out inside the timed region.
     e2e = None
     if not args.no_e2e:
-        E2E_CHUNKS = 8
+        E2E_CHUNKS = max(1, args.e2e_chunks)
         hf = torch.from_numpy(f_np).pin_memory()
         hg = torch.from_numpy(g_np).pin_memory()
         hh = torch.empty_like(hf).pin_memory()
@@ -620,6 +620,8 @@ def main():
     ap.add_argument("--algo", default="hybridRCM", choices=["hybridRCM", "hybridCS"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-chunks", type=int, default=8,
+                    help="pipeline depth of the end-to-end measurement (runs of consecutive items)")
     ap.add_argument("--no-check", action="store_true", help="accepted for compatibility; no effect")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the same-GPU timings of all algorithms on the 1D/2D/3D configs")
