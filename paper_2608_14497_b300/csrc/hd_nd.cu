@@ -97,14 +97,17 @@ static int elementwise_blocks(int64_t n) {
 
 // Choose W columns per CTA for a column pass over A blocks of B columns:
 // shared memory per column `per_col` bytes and points per column `pts`;
-// W <= 8, W even if `even`; then halved while the grid is under two CTAs per
-// SM (wide column groups on few SMs leave most of the GPU idle).
+// W a power of two <= 8 (the strip loops of the complex passes split the
+// element index with a shift and a mask), W even if `even`; no wider than B
+// (the largest power of two <= B) unless `even`; then halved while the grid is
+// under two CTAs per SM (wide column groups on few SMs leave most of the GPU
+// idle).
 static int choose_W(size_t per_col, int pts, int64_t A, int64_t B, size_t max_smem, bool even, int64_t max_pts,
                     int num_sms) {
   int W = 8;
   while (W > 1 && ((size_t)W * per_col > max_smem || (int64_t)W * pts > max_pts)) W >>= 1;
   if (even && W < 2) W = 2;
-  if ((int64_t)W > B && !even) W = (int)std::max<int64_t>(1, B);
+  while (!even && W > 1 && (int64_t)W > B) W >>= 1;
   const int wmin = even ? 2 : 1;
   while (W > wmin && A * ((B + W - 1) / W) < 2 * (int64_t)std::max(num_sms, 1)) W >>= 1;
   return W;
@@ -122,6 +125,7 @@ static hd_status col_fwd(hd_ctx* c, const void* X, int in_mode, int Lreal, float
   const Eng eng = pick_eng(tc, struct_length(cp.m) && cp.q <= 2);
   const size_t per_col = sizeof(float2) * ((keep ? (size_t)Lin : 0) + (size_t)cp.m) + 16;
   const int W = choose_W(per_col, cp.m, A, B, (size_t)c->max_smem, false, max_points(eng), c->num_sms);
+  if (W < 1 || (W & (W - 1))) return fail(HD_EUNSUPPORTED, "column pass: strip width not a power of two");
   ColGeom cg{A, B, W, Bp > 0 ? Bp : B};
   const size_t smem = sizeof(float2) * ((keep ? (size_t)acc_slots(W * Lin) : 0) + (size_t)W * cp.m);
   if (smem > (size_t)c->max_smem || (int64_t)W * cp.m > max_points(eng)) return HD_EUNSUPPORTED;
@@ -137,6 +141,7 @@ static hd_status col_bwd(hd_ctx* c, const float2* Y, void* Z, int out_mode, int 
   const Eng eng = pick_eng(tc, struct_length(cp.m) && cp.q <= 2);
   const size_t per_col = sizeof(float2) * ((sep ? (size_t)Lout : 0) + (size_t)cp.m) + 16;
   const int W = choose_W(per_col, cp.m, A, B, (size_t)c->max_smem, false, max_points(eng), c->num_sms);
+  if (W < 1 || (W & (W - 1))) return fail(HD_EUNSUPPORTED, "column pass: strip width not a power of two");
   ColGeom cg{A, B, W, Bp > 0 ? Bp : B};
   const size_t smem = sizeof(float2) * ((sep ? (size_t)acc_slots(W * Lout) : 0) + (size_t)W * cp.m);
   if (smem > (size_t)c->max_smem || (int64_t)W * cp.m > max_points(eng)) return HD_EUNSUPPORTED;

@@ -166,3 +166,16 @@ def test_one_residue_rows(hd, shape, full):
     h = hd.conv(tf, tg, algo="hybridRCM", out_extent=K if full else None)
     torch.cuda.synchronize()
     assert rel_l2(h.cpu().numpy().astype(np.float64), ref) <= TOL
+
+
+# the column passes' compile-time residue lengths (m = 256, 384, 1024, 2048,
+# 3072 for L = 256, 384, 1024, 2048, 3000 along an outer dimension) with column
+# counts that leave a partial last strip (B not a multiple of the strip width),
+# along the first and, in 3D, the middle dimension; every output against O2
+@pytest.mark.parametrize("algo", ("hybridRCM", "hybridCS", "hybridCSRCM"))
+@pytest.mark.parametrize("shape", [(384, 379), (256, 61), (1024, 33), (2048, 9), (3000, 17), (384, 7, 13),
+                                   (5, 384, 11), (256, 3, 29)])
+def test_compile_time_column_lengths(hd, algo, shape):
+    f, g = inputs.uniform_pair(shape, seed=7000 + sum(shape))
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    assert rel_l2(run(hd, f, g, algo), ref) <= TOL
