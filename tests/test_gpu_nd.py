@@ -179,3 +179,13 @@ def test_compile_time_column_lengths(hd, algo, shape):
     f, g = inputs.uniform_pair(shape, seed=7000 + sum(shape))
     ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
     assert rel_l2(run(hd, f, g, algo), ref) <= TOL
+
+
+# a middle-dimension column pass with fewer than 8 columns per block (Lp = 3,
+# 5, 6, 7) and hundreds of blocks: the strip width must stay a power of two
+@pytest.mark.parametrize("algo", ALL)
+@pytest.mark.parametrize("shape", [(300, 5, 11), (160, 9, 5), (200, 3, 9), (150, 4, 14)])
+def test_3d_narrow_middle_blocks(hd, algo, shape):
+    f, g = inputs.normal_pair(shape, seed=7100 + sum(shape))
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    assert rel_l2(run(hd, f, g, algo), ref) <= TOL
