@@ -223,9 +223,13 @@ hd_status hd_conv_adjoint(hd_ctx* ctx, hd_algo algo, int ndim, const int64_t* Ls
                           const float* grad_h, const float* f, const float* g, float* grad_f, float* grad_g,
                           void* stream);
 
-/* The planner's (m, q) for one dimension of real length L and `algo`
- * (HD_HYBRID_RCM reports packed lengths; beyond the cluster kernel, the (M, q)
- * of the three-kernel path of hd_conv1d_staged). */
+/* The planner's (m, q) for one dimension of real length L and `algo`, as a
+ * single hd_conv1d call uses it.  HD_HYBRID_RCM reports packed lengths: up to
+ * L = 73728 the cluster instance (m, q = 2C) with the smallest modelled
+ * latency for one convolution per call (a per-call cost for each cluster size
+ * C plus a per-point cost of the m-point transforms, fitted to B300 timings;
+ * batched plans choose by measured throughput instead); beyond, the (M, q) of
+ * the three-kernel path of hd_conv1d_staged. */
 hd_status hd_plan(hd_ctx* ctx, hd_algo algo, int64_t L, hd_dim_params* out);
 
 /* The batched planner's autotuner table (filled by the first hybridRCM batch

@@ -179,7 +179,7 @@ static hd_status conv1d_hybrid(hd_ctx* c, hd_algo algo, const float* f, const fl
                                const hd_dim_params* prm, cudaStream_t st, int64_t K) {
   if (algo == HD_HYBRID_RCM && !(prm && prm->m > 0)) {
     int C, m, p;
-    if (cluster_params(L, &C, &m, &p)) return conv1d_rcm_cluster(c, f, g, h, L, C, m, p, st, 1, K);
+    if (cluster_params_single(L, &C, &m, &p)) return conv1d_rcm_cluster(c, f, g, h, L, C, m, p, st, 1, K);
     int M, q;
     if (staged_params(L, &M, &q)) return conv1d_staged(c, f, g, h, L, K, M, q, 1, st);
   }
@@ -281,7 +281,7 @@ hd_status hd_plan(hd_ctx* c, hd_algo algo, int64_t L, hd_dim_params* out) {
   switch (algo) {
     case HD_HYBRID_RCM: {
       int C, m, p;
-      if (cluster_params(L, &C, &m, &p)) {
+      if (cluster_params_single(L, &C, &m, &p)) {
         out->m = m;
         out->q = 2 * C;
         return HD_OK;

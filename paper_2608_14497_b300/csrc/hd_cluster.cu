@@ -80,6 +80,39 @@ bool cluster_params(int64_t L, int* C_out, int* m_out, int* p_out, const Cluster
   return false;
 }
 
+// One convolution per call: the built instance with the smallest modelled time
+// a_C + b_C m.  A call is one cluster, so its time is latency: a per-call cost
+// a_C (launch, cluster set-up and the exchanges between the C CTAs) and a cost
+// b_C per point of the C CTAs' m-point transforms, fitted to CUDA-graph
+// timings of single calls on a B300 (L = 10^3 ... 65536; e.g. L = 16384:
+// 18.9 us at (C, m) = (2, 4096), the first instance that fits, 11.0 us at
+// (8, 1280)).  Small L stays on one CTA, whose a_1 has no exchange.
+bool cluster_params_single(int64_t L, int* C_out, int* m_out, int* p_out) {
+  if (L < 1) return false;
+  struct Cost {
+    int C;
+    double a_us, b_us;
+  };
+  static const Cost model[] = {{1, 5.5, 1.5e-3}, {2, 5.3, 3.3e-3}, {4, 7.4, 2.1e-3}, {8, 6.8, 3.3e-3},
+                               {16, 8.3, 2.9e-3}};
+  const int64_t Lp = (L + 1) / 2;
+  double best = 1e300;
+  for (const auto& cm : instances()) {
+    if ((int64_t)2 * cm.first * cm.second < L) continue;
+    for (const Cost& k : model) {
+      if (k.C != cm.first) continue;
+      const double t = k.a_us + k.b_us * cm.second;
+      if (t < best) {
+        best = t;
+        *C_out = cm.first;
+        *m_out = cm.second;
+        *p_out = (int)((Lp + cm.second - 1) / cm.second);
+      }
+    }
+  }
+  return best < 1e300;
+}
+
 hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out) {
   const std::vector<std::pair<int, int>> cand = instances();
   const int64_t budget = int64_t{1} << 22;  // real elements per timed batch

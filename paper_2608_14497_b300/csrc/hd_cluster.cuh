@@ -38,6 +38,8 @@ bool cluster_instance(int C, int m);
 // holds an autotuner table, else the smallest cluster whose largest length
 // suffices, with the smallest such length.
 bool cluster_params(int64_t L, int* C, int* m, int* p, const ClusterTuning* tun = nullptr);
+// (C, m, p) for one convolution per call (latency model; see hd_cluster.cu).
+bool cluster_params_single(int64_t L, int* C, int* m, int* p);
 // Time every built instance on synthetic batches (device scratch, ~50 MB).
 hd_status cluster_autotune(hd_ctx* c, ClusterTuning* out);
 // Launch over `nitems` convolutions of the same (C, m) (clusters of C CTAs);

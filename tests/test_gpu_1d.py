@@ -183,3 +183,21 @@ def test_explicit_rcm_long_lengths(hd, L):
     f, g = inputs.normal_pair(L, seed=700 + L)
     ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
     assert rel_l2(run(hd, f, g, "explicitRCM"), ref) <= TOL
+
+
+# single calls pick the cluster size by a latency model: every size it can
+# choose (one CTA up to clusters of 16), first L and full outputs
+@pytest.mark.parametrize("L", [4096, 4097, 8192, 9000, 16384, 20000, 32768, 40000, 65536, 73728])
+@pytest.mark.parametrize("full", [False, True])
+def test_single_call_cluster_choice(hd, L, full):
+    ctx = hd.context()
+    m, q = hd.hd_plan(ctx, hd.HD_HYBRID_RCM, L)
+    assert q in (2, 4, 8, 16, 32) and m % 256 == 0 and m * q >= L
+    f, g = inputs.normal_pair(L, seed=7200 + L)
+    K = 2 * L - 1 if full else L
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64), (K,))
+    tf = torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).cuda()
+    tg = torch.from_numpy(np.ascontiguousarray(g, dtype=np.float32)).cuda()
+    h = hd.conv(tf, tg, algo="hybridRCM", out_extent="full" if full else None)
+    torch.cuda.synchronize()
+    assert rel_l2(h.cpu().numpy().astype(np.float64), ref) <= TOL, (L, m, q)
