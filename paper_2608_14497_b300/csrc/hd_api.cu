@@ -3,6 +3,7 @@
 // Sec. 2 for a length, and dispatch to the kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -332,9 +333,13 @@ hd_status hd_conv_batch(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const i
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == HD_FP32 && algo == HD_HYBRID_RCM) {
     if (ndim >= 2) return conv_nd_batch_rcm(c, ndim, Ls, batch, f, g, h, st);
+    // a batch whose clusters all fit in one wave is latency-bound like a single
+    // call and takes the single-call choice (so each item equals its single-call
+    // result bit for bit); larger batches take the throughput rule
     int C, m, p;
-    if (batch < (1 << 24) && cluster_params(Ls[0], &C, &m, &p))
-      return conv1d_rcm_cluster(c, f, g, h, Ls[0], C, m, p, st, batch);
+    bool cl = cluster_params_single(Ls[0], &C, &m, &p) && (int64_t)batch * C <= (int64_t)std::max(c->num_sms, 1);
+    if (!cl) cl = batch < (1 << 24) && cluster_params(Ls[0], &C, &m, &p);
+    if (cl) return conv1d_rcm_cluster(c, f, g, h, Ls[0], C, m, p, st, batch);
     int M, q;
     if (staged_params(Ls[0], &M, &q)) return conv1d_staged(c, f, g, h, Ls[0], Ls[0], M, q, batch, st);
   }

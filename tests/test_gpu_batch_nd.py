@@ -36,7 +36,8 @@ def test_batch_every_item(hd, algo, shape):
 
 
 def test_batch_matches_single_calls_bitwise_1d(hd):
-    """One cluster launch over the batch gives the single-call result per item."""
+    """A batch whose clusters fit in one wave takes the single-call (C, m), so
+    one cluster launch over the batch gives the single-call result per item."""
     B, L = 7, 20000
     f, g = inputs.uniform_pair((B, L), seed=91)
     tf, tg = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
