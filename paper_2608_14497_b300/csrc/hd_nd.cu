@@ -102,8 +102,8 @@ static int elementwise_blocks(int64_t n) {
 // (the largest power of two <= B) unless `even`; then halved while the grid is
 // under two CTAs per SM (wide column groups on few SMs leave most of the GPU
 // idle).
-static int choose_W(size_t per_col, int pts, int64_t A, int64_t B, size_t max_smem, bool even, int64_t max_pts,
-                    int num_sms) {
+int choose_W(size_t per_col, int pts, int64_t A, int64_t B, size_t max_smem, bool even, int64_t max_pts,
+             int num_sms) {
   int W = 8;
   while (W > 1 && ((size_t)W * per_col > max_smem || (int64_t)W * pts > max_pts)) W >>= 1;
   if (even && W < 2) W = 2;

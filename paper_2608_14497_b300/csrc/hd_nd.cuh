@@ -17,4 +17,8 @@ hd_status conv_nd_batch_rcm(hd_ctx* c, int d, const int64_t* L, int64_t batch, c
 // rev(conv(rev(u), g)), grad_g = rev(conv(rev(u), f)); either may be NULL.
 hd_status adjoint_rcm_nd(hd_ctx* c, int d, const int64_t* L, int64_t batch, const float* u, const float* f,
                          const float* g, float* gf, float* gg, cudaStream_t st);
+// Columns per CTA of a column pass over A blocks of B columns (a power of two
+// <= 8; host logic, tested without a GPU).
+int choose_W(size_t per_col, int pts, int64_t A, int64_t B, size_t max_smem, bool even, int64_t max_pts,
+             int num_sms);
 }  // namespace hd

@@ -22,12 +22,14 @@ def lib():
         "staged": ("_ZN2hd13staged_paramsElPiS0_", [ctypes.c_int64] + [ctypes.POINTER(ctypes.c_int)] * 2),
         "single": ("_ZN2hd21cluster_params_singleElPiS0_S0_", [ctypes.c_int64] + [ctypes.POINTER(ctypes.c_int)] * 3),
         "instance": ("_ZN2hd16cluster_instanceEii", [ctypes.c_int, ctypes.c_int]),
+        "choose_W": ("_ZN2hd8choose_WEmillmbli", [ctypes.c_size_t, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                                  ctypes.c_size_t, ctypes.c_bool, ctypes.c_int64, ctypes.c_int]),
     }
     out = {}
     for key, (sym, args) in fns.items():
         f = getattr(lb, sym)
         f.argtypes = args
-        f.restype = ctypes.c_bool
+        f.restype = ctypes.c_int if key == "choose_W" else ctypes.c_bool
         out[key] = f
     return out
 
@@ -89,3 +91,24 @@ def test_single_call_beyond_the_cluster_kernel(lib):
     C, m, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     assert not lib["single"](73729, ctypes.byref(C), ctypes.byref(m), ctypes.byref(p))
     assert not lib["single"](0, ctypes.byref(C), ctypes.byref(m), ctypes.byref(p))
+
+
+@pytest.mark.parametrize("even", [False, True])
+def test_column_strip_width(lib, even):
+    """Strip widths of the column passes: a power of two <= 8 for every block
+    shape (the strip loops split the element index with a shift and a mask),
+    even for the paired real columns, at most B otherwise unless B < 1, and
+    within the shared-memory and point limits."""
+    smem, pts_max, sms = 232448, 4096, 148
+    for per_col in (8 * 400, 8 * 1200, 8 * 4000, 8 * 20000):
+        for pts in (16, 192, 384, 1024, 3072):
+            for A in (1, 3, 24, 300, 768, 4096):
+                for B in (1, 2, 3, 5, 6, 7, 8, 9, 15, 49, 190, 1500, 73728):
+                    W = lib["choose_W"](per_col, pts, A, B, smem, even, pts_max, sms)
+                    assert W in (1, 2, 4, 8), (per_col, pts, A, B, even, W)
+                    if even:
+                        assert W >= 2
+                    else:
+                        assert W <= B
+                        if W > 1:
+                            assert W * per_col <= smem and W * pts <= pts_max
