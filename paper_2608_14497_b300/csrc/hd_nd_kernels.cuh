@@ -784,9 +784,11 @@ __global__ void __launch_bounds__(SE ? 512 : 1024) k_rows_adj(float2* F, float2*
 // k_rows_cconv: complex hybrid convolution (Sec. 2) of each row of F with the
 // same row of G along the last dimension, pointwise product, in place over F.
 // ---------------------------------------------------------------------------
-template <int PTS, bool SE>
+// NN > 0: an instance for the residue length m = NN (compile-time passes).
+template <int PTS, bool SE, int NN = 0>
 __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, false, SE>::MINB) k_rows_cconv(float2* F, const float2* __restrict__ G, int Lr, int m, int q,
                                                      int p, float scale, const float2* __restrict__ tw, FftPlan pl) {
+  if constexpr (NN > 0) m = NN;
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   const int64_t row = blockIdx.x;
@@ -816,10 +818,10 @@ __global__ void __launch_bounds__(ColBounds<PTS, false, SE>::T, ColBounds<PTS, f
         },
         [&](int idx, float2 v) { buf[idx] = v; });
     __syncthreads();
-    fft_sel<1, PTS, false, SE>(buf, m, 2, pl, tw, q);
+    fft_sel<1, PTS, false, SE, NN>(buf, m, 2, pl, tw, q);
     for (int l = tid; l < m; l += T) buf[l] = cmul(buf[l], buf[m + l]);
     __syncthreads();
-    fft_sel<-1, PTS, false, SE>(buf, m, 1, pl, tw, q);
+    fft_sel<-1, PTS, false, SE, NN>(buf, m, 1, pl, tw, q);
     for (int j = tid; j < Lr; j += T) acc[j] = cadd(acc[j], cmul(buf[j % m], tw_get<-1>(tw, modmul(r, j, N))));
     __syncthreads();
   };
