@@ -154,8 +154,10 @@ hd_status hd_conv_batch(hd_ctx* ctx, hd_algo algo, hd_prec prec, int ndim, const
  * backward DFTs, stage C transforms back over the residues and unpacks
  * (hybridRCM) or takes the real part (hybridCS, Eq. real-accumulation).
  * hd_conv1d, hd_conv_ext and hd_conv_batch take this path when prm is NULL
- * for hybridRCM lengths beyond the cluster kernel (L > 73728) and hybridCS
- * lengths beyond one CTA (L > 8192); this call runs it for any L.
+ * for hybridRCM lengths beyond the cluster kernel (L > 73728) and for hybridCS
+ * from L = 513 in single calls (hd_conv1d, hd_conv_ext: the q/2 + 1 residue
+ * CTAs beat one CTA's latency) and beyond one CTA (L > 8192) in
+ * hd_conv_batch; this call runs it for any L.
  *   algo: HD_HYBRID_RCM (needs q M >= L) or HD_HYBRID_CS (needs q M >= 2L-1).
  *   `batch` items of L floats back to back in f and g, of K floats in h
  *   (K = 0 means K = L; L <= K <= 2L-1).  M in {512, 1024, 2048, 4096,

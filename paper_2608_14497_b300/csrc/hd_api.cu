@@ -34,8 +34,11 @@ namespace hd {
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // hybridCS lengths one CTA transforms with q = 2 (m <= 8192); longer ones run
-// the three-kernel path (App. A), unless the caller gives (m, q).
+// the three-kernel path (App. A), unless the caller gives (m, q).  A single
+// call (one convolution) takes the three-kernel path from kCsSingleStaged on:
+// its q residues run on q/2 + 1 SMs instead of one (L = 4096: 39 -> 10 us).
 constexpr int64_t kCsOneCta = 8192;
+constexpr int64_t kCsSingleStaged = 512;
 
 static int64_t next_smooth_even(int64_t n) {
   int64_t m = next_smooth(n < 2 ? 2 : n);
@@ -184,7 +187,7 @@ static hd_status conv1d_hybrid(hd_ctx* c, hd_algo algo, const float* f, const fl
     int M, q;
     if (staged_params(L, &M, &q)) return conv1d_staged(c, f, g, h, L, K, M, q, 1, st);
   }
-  if (algo == HD_HYBRID_CS && !(prm && prm->m > 0) && L > kCsOneCta) {
+  if (algo == HD_HYBRID_CS && !(prm && prm->m > 0) && L > kCsSingleStaged) {
     int M, q;
     if (staged_params(2 * L - 1, &M, &q)) return conv1d_staged(c, f, g, h, L, K, M, q, 1, st, true);
   }
@@ -297,7 +300,7 @@ hd_status hd_plan(hd_ctx* c, hd_algo algo, int64_t L, hd_dim_params* out) {
       break;
     }
     case HD_HYBRID_CS:
-      if (L > kCsOneCta) {
+      if (L > kCsSingleStaged) {
         int M, q;
         if (staged_params(2 * L - 1, &M, &q)) {
           out->m = M;

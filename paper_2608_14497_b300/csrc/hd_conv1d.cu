@@ -28,6 +28,8 @@
 // (then it is private to the CTA; no atomics are needed).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "hd_conv1d.cuh"
 
 namespace hd {
@@ -128,8 +130,20 @@ __global__ void __launch_bounds__(1024) k_rcm1d(Launch1D la, const float* f, con
   }
 }
 
-template <int PTS, bool RCM0>
-__global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, const float* g, float* h) {
+// A length-n DFT of k_cs1d on nbuf arrays at stride n: the plan-driven engine,
+// or with NN > 0 the structured engine at the compile-time length NN (the
+// half-length DFTs of residues 0 and q/2 in an instance for one m; the
+// length-m DFTs of the other residues stay on the plan-driven engine, which
+// such an instance, launched for q = 2 only, never runs).
+template <int SIGN, int PTS, int NN>
+__device__ __forceinline__ void cs1d_fft(float2* buf, int n, int nbuf, const FftPlan& pl, const float2* tw,
+                                         int twmul) {
+  if constexpr (NN > 0) cta_fft_struct_k<SIGN, PTS, NN>(buf, NN, nbuf, tw, twmul);
+  else cta_fft<SIGN, PTS>(buf, n, nbuf, pl, tw, twmul);
+}
+
+template <int PTS, bool RCM0, int NM = 0>
+__global__ void __launch_bounds__(NM > 0 ? 512 : 1024) k_cs1d(Launch1D la, const float* f, const float* g, float* h) {
   extern __shared__ float4 smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   __shared__ FftPlan s_pm, s_ph;
@@ -139,7 +153,7 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
     if (it.plan_half >= 0) s_ph = la.plans ? la.plans[it.plan_half] : la.plan_half;
   }
   const int T = blockDim.x, tid = threadIdx.x;
-  const int L = it.L, m = it.m, q = it.q, p = it.p;
+  const int L = it.L, m = NM > 0 ? NM : it.m, q = it.q, p = it.p;
   const int N = q * m;
   const int K = it.K > 0 ? it.K : L;  // real output length
   const float* fi = f + it.off;
@@ -171,7 +185,7 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
         buf[idx] = make_float2(x0, x1);
       }
       __syncthreads();
-      cta_fft<1, PTS>(buf, n2, 2, s_ph, tw, 2 * q);
+      cs1d_fft<1, PTS, NM / 2>(buf, n2, 2, s_ph, tw, 2 * q);
       float2* Z = buf;
       float2* Y = buf + n2;
       if constexpr (RCM0) {
@@ -208,7 +222,7 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
       }
       }
       __syncthreads();
-      cta_fft<-1, PTS>(buf, n2, 1, s_ph, tw, 2 * q);
+      cs1d_fft<-1, PTS, NM / 2>(buf, n2, 1, s_ph, tw, 2 * q);
       // h_0 = 2 unpack(z''), repeated for every block t (Sec. 3.1.1).
       for (int j = tid; j < K; j += T) {
         const int s = j % m;
@@ -229,10 +243,10 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
         buf[idx] = make_float2(x0, 0.f);
       }
       __syncthreads();
-      cta_fft<1, PTS>(buf, m, 2, s_pm, tw, q);
+      cs1d_fft<1, PTS, 0>(buf, m, 2, s_pm, tw, q);
       for (int l = tid; l < m; l += T) buf[l] = cmul(buf[l], buf[m + l]);
       __syncthreads();
-      cta_fft<-1, PTS>(buf, m, 1, s_pm, tw, q);
+      cs1d_fft<-1, PTS, 0>(buf, m, 1, s_pm, tw, q);
       for (int j = tid; j < K; j += T) acc[j] += buf[j % m].x;
       __syncthreads();
     } else if (2 * r == q) {
@@ -253,10 +267,10 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
         buf[idx] = cmul(make_float2(x0, x1), tw_get<1>(tw, b * qh));
       }
       __syncthreads();
-      cta_fft<1, PTS>(buf, e, 2, s_ph, tw, 2 * q);
+      cs1d_fft<1, PTS, NM / 2>(buf, e, 2, s_ph, tw, 2 * q);
       for (int c = tid; c < e; c += T) buf[c] = cmul(buf[c], buf[e + c]);
       __syncthreads();
-      cta_fft<-1, PTS>(buf, e, 1, s_ph, tw, 2 * q);
+      cs1d_fft<-1, PTS, NM / 2>(buf, e, 1, s_ph, tw, 2 * q);
       // Eqs. wb / accumulateq2: w_b = zeta_2m^{-b} (...); (-1)^t 2Re w_b, (-1)^t 2Im w_b.
       for (int j = tid; j < K; j += T) {
         const int t = j / m, s = j - t * m;
@@ -286,10 +300,10 @@ __global__ void __launch_bounds__(1024) k_cs1d(Launch1D la, const float* f, cons
         buf[idx] = sum;
       }
       __syncthreads();
-      cta_fft<1, PTS>(buf, m, 2, s_pm, tw, q);
+      cs1d_fft<1, PTS, 0>(buf, m, 2, s_pm, tw, q);
       for (int l = tid; l < m; l += T) buf[l] = cmul(buf[l], buf[m + l]);
       __syncthreads();
-      cta_fft<-1, PTS>(buf, m, 1, s_pm, tw, q);
+      cs1d_fft<-1, PTS, 0>(buf, m, 1, s_pm, tw, q);
       for (int j = tid; j < K; j += T) {
         const float2 v = cmul(buf[j % m], tw_get<-1>(tw, mulmod(r, j, N)));
         acc[j] += 2.f * v.x;
@@ -336,6 +350,22 @@ cudaError_t launch_rcm1d(const Launch1D& la, int nitems, int threads, size_t sme
 cudaError_t launch_cs1d(const Launch1D& la, int nitems, int threads, size_t smem, const float* f, const float* g,
                         float* h, cudaStream_t st, bool rcm0) {
   auto k = rcm0 ? k_cs1d<kPts, true> : k_cs1d<kPts, false>;
+  // single calls with q = 2 at the residue lengths of the usual sizes: the
+  // compile-time instance (its DFTs of m / 2 on the structured engine, on two
+  // arrays, so m points at kPts per thread: 256 to 512 threads, launch bound
+  // 512 for the registers of the unrolled passes)
+  if (!la.items && nitems == 1 && la.one.q == 2 && la.one.m <= 512 * kPts) {
+    const int tq = std::max(256, la.one.m / kPts);
+    switch (la.one.m) {
+      case 1024: k = rcm0 ? k_cs1d<kPts, true, 1024> : k_cs1d<kPts, false, 1024>; break;
+      case 2048: k = rcm0 ? k_cs1d<kPts, true, 2048> : k_cs1d<kPts, false, 2048>; break;
+      case 3072: k = rcm0 ? k_cs1d<kPts, true, 3072> : k_cs1d<kPts, false, 3072>; break;
+      case 4096: k = rcm0 ? k_cs1d<kPts, true, 4096> : k_cs1d<kPts, false, 4096>; break;
+      case 8192: k = rcm0 ? k_cs1d<kPts, true, 8192> : k_cs1d<kPts, false, 8192>; break;
+      default: break;
+    }
+    if (k != (rcm0 ? k_cs1d<kPts, true> : k_cs1d<kPts, false>)) threads = tq;
+  }
   cudaError_t e = allow_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<nitems, threads, smem, st>>>(la, f, g, h);

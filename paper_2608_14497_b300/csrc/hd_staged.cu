@@ -836,10 +836,18 @@ static int s_per_cta(int q) {
 // q M >= L packed; hybridCS: q M >= 2L - 1 real).  From n = 2^17 on, q is one
 // of 256, 512, 1024 (stages A and C on the compile-time engine) and M = 256 R3
 // (R3 in {2, 4, 8, 16, 18}) with the smallest N = q M >= n, the largest M
-// among equal N (fewer, longer stage-B transforms measured faster).  Below,
-// M = 512 and q the smallest length {1, 3, 5, 9} x 2^a >= max(16, n / 512).
-// False if n > 1024 x 4608.
+// among equal N (fewer, longer stage-B transforms measured faster).  Up to
+// n = 16384 (single hybridCS calls of L <= 8192), q = 4 and the smallest
+// M >= n / 4: a few long residues, measured 1.7-2x faster than M = 512 with
+// q up to 32.  In between, M = 512 and q the smallest length
+// {1, 3, 5, 9} x 2^a >= max(16, n / 512).  False if n > 1024 x 4608.
 bool staged_params(int64_t n, int* M, int* q) {
+  if (n <= 4 * 4096) {
+    *q = 4;
+    *M = 512;
+    while (4 * (int64_t)*M < n) *M *= 2;
+    return true;
+  }
   if (n < (1 << 17)) {
     *M = 512;
     *q = (int)ladder_ceil(std::max<int64_t>(16, (n + 511) / 512));

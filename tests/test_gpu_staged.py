@@ -179,3 +179,29 @@ def test_staged_cs_batch_and_errors(hd):
     with pytest.raises(hd.HDError) as e:
         hd.conv_staged(x, x, M=512, q=20, algo="explicit")
     assert e.value.status == hd.HD_EINVAL
+
+
+@pytest.mark.parametrize("L", [512, 513, 1000, 2048, 2049, 4096, 6000, 8192, 8193])
+@pytest.mark.parametrize("kind", ["L", "full"])
+def test_single_cs_call_short_lengths(hd, L, kind):
+    """Single hybridCS calls from L = 513 on take the three kernels (q = 4 and
+    the smallest M >= (2L - 1) / 4 up to L = 8192); L = 512 stays on one CTA."""
+    M, q = hd.hd_plan(hd.context(), hd.HD_HYBRID_CS, L)
+    if L > 512:
+        assert M * q >= 2 * L - 1 and M in (512, 1024, 2048, 4096, 4608)
+        if L <= 8192:
+            assert q == 4
+    K = L if kind == "L" else 2 * L - 1
+    f, g = inputs.normal_pair(L, seed=7300 + L)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64), (K,))
+    h = host(hd.conv(dev(f), dev(g), algo="hybridCS", out_extent=K))
+    assert rel_l2(h, ref) <= TOL, (L, K)
+
+
+def test_single_cs_call_in_place(hd):
+    L = 4096
+    f, g = inputs.uniform_pair(L, seed=7400)
+    ref = oracle.fft_conv(f.astype(np.float64), g.astype(np.float64))
+    tf, tg = dev(f), dev(g)
+    hd.conv(tf, tg, algo="hybridCS", out=tf)
+    assert rel_l2(host(tf), ref) <= TOL

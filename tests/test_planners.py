@@ -50,7 +50,7 @@ def staged(lib, n):
     return ok, M.value, q.value
 
 
-LENGTHS = [1, 2, 100, 5000, 73729, 100000, (1 << 17) - 1, 1 << 17, (1 << 17) + 1, 200000, 262144, 262145, 500000,
+LENGTHS = [1, 2, 100, 2047, 2048, 2049, 5000, 8191, 16383, 16384, 16385, 73729, 100000, (1 << 17) - 1, 1 << 17, (1 << 17) + 1, 200000, 262144, 262145, 500000,
            524288, 1000000, 1048576, 2000000, 3000000, 4000000, 4194304, 4718592]
 
 
@@ -59,7 +59,9 @@ def test_staged_params_rule(lib, n):
     ok, M, q = staged(lib, n)
     assert ok
     assert M in STAGE_B_M and q % 2 == 0 and 2 <= q <= 1024 and M * q >= n
-    if n < (1 << 17):
+    if n <= 16384:
+        assert q == 4 and M == min(mm for mm in (512, 1024, 2048, 4096) if 4 * mm >= n)
+    elif n < (1 << 17):
         assert M == 512 and q == ladder_ceil(max(16, -(-n // 512)))
     else:
         # the compile-time q lengths, the smallest N, the larger M on ties
