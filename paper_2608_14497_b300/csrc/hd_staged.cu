@@ -833,14 +833,16 @@ static int s_per_cta(int q) {
 }  // namespace staged
 
 // Planner of the three-kernel path for a needed padded length n (hybridRCM:
-// q M >= L packed; hybridCS: q M >= 2L - 1 real).  From n = 2^17 on, q is one
-// of 256, 512, 1024 (stages A and C on the compile-time engine) and M = 256 R3
-// (R3 in {2, 4, 8, 16, 18}) with the smallest N = q M >= n, the largest M
-// among equal N (fewer, longer stage-B transforms measured faster).  Up to
-// n = 16384 (single hybridCS calls of L <= 8192), q = 4 and the smallest
-// M >= n / 4: a few long residues, measured 1.7-2x faster than M = 512 with
-// q up to 32.  In between, M = 512 and q the smallest length
-// {1, 3, 5, 9} x 2^a >= max(16, n / 512).  False if n > 1024 x 4608.
+// q M >= L packed; hybridCS: q M >= 2L - 1 real), from CUDA-graph timings of
+// single calls.  Up to n = 16384 (single hybridCS calls of L <= 8192), q = 4
+// and the smallest M >= n / 4: a few long residues, 1.7-2x faster than
+// M = 512 with q up to 32; up to n = 32768, (M, q) = (4096, 8) (L = 9000:
+// 19.3 -> 14.5 us).  Beyond, q is one of 256, 512, 1024 (stages A and C on
+// the compile-time engine) and M = 256 R3 (R3 in {2, 4, 8, 16, 18}) with the
+// smallest N = q M >= n, the largest M among equal N (fewer, longer stage-B
+// transforms measured faster); below n = 2^17 that is (512, 256), 13-14 us
+// flat, where the q lengths {1, 3, 5, 9} x 2^a took 13-21 us (hybridRCM
+// L = 80000: 16.2 -> 13.5 us).  False if n > 1024 x 4608.
 bool staged_params(int64_t n, int* M, int* q) {
   if (n <= 4 * 4096) {
     *q = 4;
@@ -848,9 +850,9 @@ bool staged_params(int64_t n, int* M, int* q) {
     while (4 * (int64_t)*M < n) *M *= 2;
     return true;
   }
-  if (n < (1 << 17)) {
-    *M = 512;
-    *q = (int)ladder_ceil(std::max<int64_t>(16, (n + 511) / 512));
+  if (n <= 8 * 4096) {
+    *q = 8;
+    *M = 4096;
     return true;
   }
   int64_t bestN = 0;

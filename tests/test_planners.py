@@ -34,23 +34,13 @@ def lib():
     return out
 
 
-def ladder_ceil(n):
-    best = None
-    for b in (1, 3, 5, 9):
-        x = b
-        while x < n:
-            x *= 2
-        best = x if best is None else min(best, x)
-    return best
-
-
 def staged(lib, n):
     M, q = ctypes.c_int(), ctypes.c_int()
     ok = lib["staged"](n, ctypes.byref(M), ctypes.byref(q))
     return ok, M.value, q.value
 
 
-LENGTHS = [1, 2, 100, 2047, 2048, 2049, 5000, 8191, 16383, 16384, 16385, 73729, 100000, (1 << 17) - 1, 1 << 17, (1 << 17) + 1, 200000, 262144, 262145, 500000,
+LENGTHS = [1, 2, 100, 2047, 2048, 2049, 5000, 8191, 16383, 16384, 16385, 32767, 32768, 32769, 73729, 100000, (1 << 17) - 1, 1 << 17, (1 << 17) + 1, 200000, 262144, 262145, 500000,
            524288, 1000000, 1048576, 2000000, 3000000, 4000000, 4194304, 4718592]
 
 
@@ -61,8 +51,8 @@ def test_staged_params_rule(lib, n):
     assert M in STAGE_B_M and q % 2 == 0 and 2 <= q <= 1024 and M * q >= n
     if n <= 16384:
         assert q == 4 and M == min(mm for mm in (512, 1024, 2048, 4096) if 4 * mm >= n)
-    elif n < (1 << 17):
-        assert M == 512 and q == ladder_ceil(max(16, -(-n // 512)))
+    elif n <= 32768:
+        assert (M, q) == (4096, 8)
     else:
         # the compile-time q lengths, the smallest N, the larger M on ties
         assert q in (256, 512, 1024)
