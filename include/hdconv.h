@@ -136,11 +136,13 @@ hd_status hd_conv_ext(hd_ctx* ctx, hd_algo algo, hd_prec prec, int ndim, const i
                       const float* f, const float* g, float* h, const hd_dim_params* prm, void* stream);
 
 /* `batch` independent convolutions of equal extents Ls[0..ndim) stored back to
- * back in f, g and h (item b at offset b * prod(Ls)); the same result as one
- * hd_conv1d/2d/3d call per item.  hybridRCM in FP32 runs the whole batch in
- * one pass sequence (1D: one cluster launch; 2D/3D: every outer pass and the
- * row pass over all items at once, Sec. 5); other algorithms run item by item.
- * Errors as hd_conv1d. */
+ * back in f, g and h (item b at offset b * prod(Ls)); the same convolutions as
+ * one hd_conv1d/2d/3d call per item (bit for bit where both take the same
+ * kernels).  hybridRCM in FP32 runs the whole batch in one pass sequence (1D:
+ * one cluster launch; 2D/3D: every outer pass and the row pass over all items
+ * at once, Sec. 5); hybridCS in 1D runs the three kernels of
+ * hd_conv1d_staged over the whole batch; explicitRCM in 1D one cluster
+ * launch; other cases run item by item.  Errors as hd_conv1d. */
 hd_status hd_conv_batch(hd_ctx* ctx, hd_algo algo, hd_prec prec, int ndim, const int64_t* Ls, int32_t batch,
                         const float* f, const float* g, float* h, void* stream);
 
@@ -156,8 +158,8 @@ hd_status hd_conv_batch(hd_ctx* ctx, hd_algo algo, hd_prec prec, int ndim, const
  * hd_conv1d, hd_conv_ext and hd_conv_batch take this path when prm is NULL
  * for hybridRCM lengths beyond the cluster kernel (L > 73728) and for hybridCS
  * from L = 513 in single calls (hd_conv1d, hd_conv_ext: the q/2 + 1 residue
- * CTAs beat one CTA's latency) and beyond one CTA (L > 8192) in
- * hd_conv_batch; this call runs it for any L.
+ * CTAs beat one CTA's latency) and for every L in hd_conv_batch (one pass
+ * sequence over the batch); this call runs it for any L.
  *   algo: HD_HYBRID_RCM (needs q M >= L) or HD_HYBRID_CS (needs q M >= 2L-1).
  *   `batch` items of L floats back to back in f and g, of K floats in h
  *   (K = 0 means K = L; L <= K <= 2L-1).  M in {512, 1024, 2048, 4096,

@@ -33,11 +33,12 @@ namespace hd {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// hybridCS lengths one CTA transforms with q = 2 (m <= 8192); longer ones run
-// the three-kernel path (App. A), unless the caller gives (m, q).  A single
-// call (one convolution) takes the three-kernel path from kCsSingleStaged on:
-// its q residues run on q/2 + 1 SMs instead of one (L = 4096: 39 -> 10 us).
-constexpr int64_t kCsOneCta = 8192;
+// hybridCS in 1D without (m, q) from the caller: a single call (one
+// convolution) runs the three-kernel path (App. A) from kCsSingleStaged on,
+// its q residues on q/2 + 1 SMs instead of one CTA (L = 4096: 39 -> 10 us),
+// and one CTA (q = 2) below; an equal-length batch always runs the three
+// kernels over the whole batch (2048 items of L = 4096: 29 ms one CTA after
+// another -> 1.0 ms).
 constexpr int64_t kCsSingleStaged = 512;
 
 static int64_t next_smooth_even(int64_t n) {
@@ -346,7 +347,7 @@ hd_status hd_conv_batch(hd_ctx* c, hd_algo algo, hd_prec prec, int ndim, const i
     int M, q;
     if (staged_params(Ls[0], &M, &q)) return conv1d_staged(c, f, g, h, Ls[0], Ls[0], M, q, batch, st);
   }
-  if (prec == HD_FP32 && algo == HD_HYBRID_CS && ndim == 1 && Ls[0] > kCsOneCta) {
+  if (prec == HD_FP32 && algo == HD_HYBRID_CS && ndim == 1) {
     int M, q;
     if (staged_params(2 * Ls[0] - 1, &M, &q))
       return conv1d_staged(c, f, g, h, Ls[0], Ls[0], M, q, batch, st, true);

@@ -45,3 +45,15 @@ def test_batch_matches_single_calls_bitwise_1d(hd):
     for b in range(B):
         hs = hd.conv(tf[b].contiguous(), tg[b].contiguous())
         assert torch.equal(hb[b], hs)
+
+
+@pytest.mark.parametrize("L,B", [(1, 3), (100, 40), (1000, 64), (4096, 33), (8192, 9)])
+def test_cs_batch_three_kernels(hd, L, B):
+    """A hybridCS batch of short lengths on the three kernels: every item."""
+    f, g = inputs.normal_pair((B, L), seed=7500 + L)
+    h = hd.conv_batch(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), 1, algo="hybridCS")
+    torch.cuda.synchronize()
+    hh = h.cpu().numpy()
+    for b in range(B):
+        ref = oracle.fft_conv(f[b].astype(np.float64), g[b].astype(np.float64))
+        assert rel_l2(hh[b], ref) <= TOL, (L, b)
